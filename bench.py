@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark of the Chebyshev propagation hot path on GB300.
+
+Workload (one line of output): the batched disorder ensemble -- 64 zigzag ribbons of uneven
+size (W in U{40..160}, L in U{500..4000}, 15.5 M sites), Anderson disorder W = 0.5/1/2 cycled
+over ribbons, 4 wave packets per ribbon (k0 = pi/6, pi/4, pi/3, pi/2), complex64 vectors with
+FP64 coefficients and reductions, dt = 1 (M = 19/20/21 per ribbon).  One step = one time step
+dt of the whole ensemble: M fused recurrence kernels, all ribbons in each launch.
+
+Metric: Chebyshev matvec-steps/s (one matvec-step = one application of H~ inside the
+recurrence to one vector of one ribbon), with the recurrence kernel's achieved algorithmic
+HBM bandwidth against the measured copy bandwidth, the complex128 single-vector path on the
+same ensemble for comparison, the oracle on the host as the CPU baseline, and an end-to-end
+figure through the C ABI with host buffers.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank propagates its own 64-ribbon ensemble (disorder streams offset by
+rank): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = ("Chebyshev matvec-steps/s and achieved HBM GB/s (% of GB300 peak), "
+          "complex64-batched vs FP64")
+UNIT = "matvec-steps/s"
+WORKLOAD = "ensemble of 64 uneven zigzag ribbons x 4 packets, complex64, dt=1"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--lean", action="store_true",
+                    help="timed region only: no e2e, FP64 or accuracy legs (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------------------
+# reference arm: the oracle on the host
+# ----------------------------------------------------------------------------------------
+def oracle_ensemble_sample(ens: wl.RibbonEnsemble, ribbons, nsteps: int = 1):
+    """Propagate the packets of the given ribbons by nsteps with the oracle; returns
+    (seconds, matvec-steps, site-steps)."""
+    import oracle
+
+    t = 0.0
+    mv = 0
+    ss = 0
+    for r in ribbons:
+        rb = ens.ribbon(r)
+        H = oracle.honeycomb(rb.W, rb.L, rb.hop, rb.onsite())
+        a, b = oracle.rescale(*rb.bounds(), 0.0)
+        C, M = oracle.coeffs(a, b, rb.dt)
+        for k0 in ens.k0s:
+            psi = rb.packet(k0)
+            t0 = time.perf_counter()
+            H.evolve(a, b, C, nsteps, psi)
+            t += time.perf_counter() - t0
+            mv += M * nsteps
+            ss += M * nsteps * rb.W * rb.L
+    return t, mv, ss
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    ens = wl.RibbonEnsemble()
+    # one step = one dt for 4 ribbons of the ensemble (cycling through all 64), 4 packets each
+    per_step = 4
+    for w in range(args.warmup):
+        oracle_ensemble_sample(ens, [(w * per_step + i) % ens.n_ribbons for i in range(per_step)])
+    tt, mv, ss = 0.0, 0, 0
+    for s in range(args.steps):
+        rs = [((args.warmup + s) * per_step + i) % ens.n_ribbons for i in range(per_step)]
+        t, m, x = oracle_ensemble_sample(ens, rs)
+        tt += t
+        mv += m
+        ss += x
+    value = mv / tt
+    sample = (f"{args.steps} steps, each one dt of 4 ribbons x 4 packets of the ensemble "
+              f"(cycling through the 64 ribbons), single-threaded FP64 oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "4 ribbons x 4 packets per step"},
+        "site_steps_per_s": ss / tt,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------
+def make_plan(cb, ens, prec, nvec, packets):
+    import torch
+
+    W = [w for w, _ in ens.sizes]
+    L = [l for _, l in ens.sizes]
+    eps = torch.from_numpy(ens.onsite()).to("cuda")
+    desc, keep = cb.desc_ribbons(W, L, ens.hop, eps)
+    lo, hi = ens.bounds()
+    plan = cb.Plan(desc, lo, hi, 0.0, prec, nvec, keep=keep)
+    dt = torch.complex64 if prec == cb.CHEB_C64 else torch.complex128
+    psi = torch.from_numpy(packets).to(dt).to("cuda").contiguous()
+    return plan, psi
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_0907_3022_gb300 as cb
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ens = wl.RibbonEnsemble(stream0=rank * 64)
+    packets = ens.packets()
+    plan, psi = make_plan(cb, ens, cb.CHEB_C64, ens.nvec, packets)
+    psi0 = psi.clone()
+    plan.evolve(psi, ens.dt, 0)  # coefficients for dt
+    plan.autotune()
+    Ms = [plan.block(q)["M"] for q in range(ens.n_ribbons)]
+    sites = [w * l for w, l in ens.sizes]
+    mv_per_step = ens.nvec * sum(Ms)
+    ss_per_step = ens.nvec * sum(m * s for m, s in zip(Ms, sites))
+    stream = torch.cuda.current_stream()
+
+    # warm-up (graph path)
+    plan.evolve(psi, ens.dt, args.warmup)
+    plan.sync()
+
+    # timed region: K steps; each recurrence launch bracketed by CUDA events on this stream
+    plan.set_timing(True)
+    plan.kernel_stats(reset=True)
+    clocks = Clocks(local)
+    launches0 = plan.launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.evolve(psi, ens.dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms_local = e0.elapsed_time(e1)
+    gpu_launches = plan.launches() - launches0
+    kms, kcount, kbytes = plan.kernel_stats(reset=True)
+    plan.set_timing(False)
+    ms = max_over_ranks(ms_local, world)
+    value = sum_over_ranks(mv_per_step * args.steps, world) / (ms / 1e3)
+    site_steps = sum_over_ranks(ss_per_step * args.steps, world) / (ms / 1e3)
+
+    peak, peak_kind = measured_peaks()
+    achieved = kbytes / (kms / 1e3) / 1e9  # GB/s
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_rec<float,4,StencilOp> (all launches of the step)",
+                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "launches": kcount, "kernel_ms_total": kms,
+                "alg_bytes_per_launch": kbytes / max(kcount, 1)}
+
+    out = {}
+    if not args.lean:
+        # end to end through the C ABI with host buffers: H2D of the packets, one step, D2H
+        pinned_in = torch.from_numpy(packets.astype(np.complex64)).pin_memory()
+        pinned_out = torch.empty_like(pinned_in).pin_memory()
+        plan.evolve(psi, ens.dt, 1)
+        torch.cuda.synchronize()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(args.steps):
+            psi.copy_(pinned_in, non_blocking=True)
+            plan.evolve(psi, ens.dt, 1)
+            pinned_out.copy_(psi, non_blocking=True)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(h0.elapsed_time(h1), world)
+        nbytes = pinned_in.numel() * pinned_in.element_size()
+        out["e2e"] = {"value": sum_over_ranks(mv_per_step * args.steps, world) / (e2e_ms / 1e3),
+                      "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+        # accuracy over the configuration's 200 steps: the smallest ribbon against the FP64
+        # oracle (4 packets) and the norm drift of every (ribbon, packet)
+        import oracle
+
+        nsteps_acc = ens.nsteps
+        psi.copy_(torch.from_numpy(packets.astype(np.complex64)))
+        n2_0 = torch.zeros((ens.n_ribbons, ens.nvec), dtype=torch.float64, device=dev)
+        n2 = torch.zeros_like(n2_0)
+        plan.observables(psi, cb.CHEB_OBS_NORM2, 0.0, n2_0)
+        plan.evolve(psi, ens.dt, nsteps_acc)
+        plan.observables(psi, cb.CHEB_OBS_NORM2, 0.0, n2)
+        res = psi.cpu().numpy().astype(np.complex128)
+        off = ens.offsets()
+        r = int(np.argmin(sites))
+        rb = ens.ribbon(r)
+        H = oracle.honeycomb(rb.W, rb.L, rb.hop, rb.onsite())
+        a, b = oracle.rescale(*rb.bounds(), 0.0)
+        C, M = oracle.coeffs(a, b, rb.dt)
+        errs = []
+        for v, k0 in enumerate(ens.k0s):
+            ref = H.evolve(a, b, C, nsteps_acc, rb.packet(k0))
+            errs.append(float(np.linalg.norm(res[off[r]:off[r + 1], v] - ref) / np.linalg.norm(ref)))
+        out["accuracy"] = {
+            "rel_l2_vs_fp64_oracle": max(errs),
+            "sample": f"ribbon {r} ({rb.W}x{rb.L}), 4 packets, {nsteps_acc} steps",
+            "max_norm_drift": float((n2 - n2_0).abs().max()),
+            "norm_drift_steps": nsteps_acc,
+        }
+
+        # the plain FP64 single-vector path on the same ensemble (packet k0 = pi/3)
+        plan64, psi64 = make_plan(cb, ens, cb.CHEB_C128, 1, packets[:, 2:3].copy())
+        plan64.evolve(psi64, ens.dt, 0)
+        plan64.autotune()
+        plan64.evolve(psi64, ens.dt, 2)
+        k64 = max(5, args.steps // 5)
+        plan64.set_timing(True)
+        plan64.kernel_stats(reset=True)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        plan64.evolve(psi64, ens.dt, k64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        f_ms = f0.elapsed_time(f1)
+        k64ms, k64n, k64b = plan64.kernel_stats(reset=True)
+        ss64 = sum(m * s for m, s in zip(Ms, sites)) * k64 / (f_ms / 1e3)
+        out["fp64_single_vector"] = {
+            "matvec_steps_per_s": sum(Ms) * k64 / (f_ms / 1e3),
+            "site_steps_per_s": ss64,
+            "complex64_batched_site_vector_steps_per_s": site_steps,
+            "speedup_c64_batched_over_fp64": site_steps / ss64,
+            "kernel_achieved_gbs": k64b / (k64ms / 1e3) / 1e9,
+            "steps": k64,
+            "note": "same ensemble, one packet (k0 = pi/3), complex128; FP64 is ~1.2 TFLOP/s "
+                    "on GB300, so this path is bound by FP64 arithmetic",
+        }
+        plan64.close()
+
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        # bounded sample: one dt of the first 24 ribbons x 4 packets on one host core
+        t, mv, ss = oracle_ensemble_sample(ens, list(range(24)))
+        out["cpu_baseline"] = {"value": mv / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "one dt of ribbons 0-23 x 4 packets (FP64 oracle, "
+                                         "single thread)",
+                               "site_steps_per_s": ss / t, "seconds": t}
+
+    wss = (psi.numel() * psi.element_size() * 4) / 1e9  # psi, T_a, T_b, tail
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD, "n_ribbons": ens.n_ribbons, "sites": int(sum(sites)),
+            "packets_per_ribbon": ens.nvec, "dt": ens.dt, "M_per_ribbon": sorted(set(Ms)),
+            "l2": f"inputs larger than L2 (working set {wss:.2f} GB of vectors)",
+            "launch_shape": dict(zip(("threads", "sites_per_thread", "grid"),
+                                     plan.launch_shape())),
+            "parallelism": f"replicas x{world} (one ensemble per GPU)",
+        },
+        "site_vector_steps_per_s": site_steps,
+        "roofline": roofline,
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+    }
+    line.update(out)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,238 @@
+/*
+ * cheb.h -- C ABI of the GB300 Chebyshev time-evolution library.
+ *
+ * The library propagates complex state vectors with the Chebyshev expansion of the time
+ * evolution operator (Fehske et al., "Numerical approaches to time evolution of complex
+ * quantum systems", Sec. 2.2):
+ *
+ *   U(dt) psi = e^{-i b dt} [ c_0 v_0 + 2 sum_{k=1}^{M} c_k v_k ],   c_k = (-i)^k J_k(a dt)
+ *   v_0 = psi,  v_1 = H~ v_0,  v_{k+1} = 2 H~ v_k - v_{k-1},         H~ = (H - b)/a
+ *
+ * with a = (Emax - Emin)(1 + alpha)/2 and b = (Emax + Emin)/2 (Sec. 2.2, text after Eq. U_1),
+ * and M the last order whose multiplier |(2 - delta_k0) c_k| reaches the tolerance (text after
+ * Eq. dec_Bessel).  Every recurrence step is one fused CUDA kernel: it applies H~ to v_k,
+ * forms v_{k+1}, and accumulates its weighted contribution into psi.
+ *
+ * Conventions for every entry point:
+ *   - The return value is a status: CHEB_OK (0) or a negative CHEB_ERR_* code.  Nothing
+ *     aborts or throws across this interface; cheb_last_error() gives a message for the
+ *     calling thread's most recent failure.
+ *   - "device" pointers are CUDA global-memory pointers on the plan's device, owned by the
+ *     caller, 16-byte aligned (CHEB_ERR_ALIGN otherwise).  "host" pointers are ordinary
+ *     memory, read during the call only.
+ *   - State vectors are interleaved complex numbers: double2 (re, im) for CHEB_C128 and
+ *     float2 for CHEB_C64.  With nvec vectors the layout is [site][vec]: the nvec values of
+ *     one site are contiguous.  Observables and gradients are always double.
+ *   - A plan is bound to one CUDA stream (given at creation; NULL = legacy default stream).
+ *     All work is enqueued on it asynchronously; calls that return results to host memory
+ *     synchronise that stream.  A plan is not thread-safe.
+ *   - The plan owns its workspace (two recurrence vectors, coefficients, the scaled
+ *     Hamiltonian data) and frees it in cheb_plan_destroy.
+ */
+#ifndef CHEB_H
+#define CHEB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define CHEB_OK 0
+#define CHEB_ERR_INVALID (-1)     /* bad argument (sizes, NULL, emin > emax, ...)          */
+#define CHEB_ERR_ALIGN (-2)       /* a device pointer is not 16-byte aligned               */
+#define CHEB_ERR_CUDA (-3)        /* a CUDA runtime call failed (message in last_error)    */
+#define CHEB_ERR_NOMEM (-4)       /* device or host allocation failed                      */
+#define CHEB_ERR_UNSUPPORTED (-5) /* operation not available for this operator kind        */
+#define CHEB_ERR_ORDER (-6)       /* |c_k| did not fall below tol within max_order         */
+#define CHEB_ERR_DIVERGED (-7)    /* recurrence grew: the spectral bounds do not enclose H */
+#define CHEB_ERR_STATE (-8)       /* call out of order (e.g. no time step set)             */
+
+/* ---- arithmetic of the state vectors ------------------------------------------------ */
+typedef enum { CHEB_C128 = 0, CHEB_C64 = 1 } cheb_prec;
+
+/* ---- operator kinds ----------------------------------------------------------------- */
+typedef enum {
+    /* 1D grid, Sec. 3.1: H = -(1/2) d^2/dx^2 + V(x) with the 3-point stencil (hbar = m = 1),
+       psi = 0 outside the n grid points.  onsite = V_i. */
+    CHEB_LAT1D = 0,
+    /* Zigzag honeycomb ribbons, Sec. 3.2, Eq. (model): H = -t sum_<ij>(c_i^+ c_j + h.c.)
+       + sum_j eps_j n_j.  Brick-wall indexing: site (r, c), r in [0, W) across, c in [0, L)
+       along, index r*L + c; neighbours (r, c-1), (r, c+1) and (r+1, c) if r + c is even,
+       (r-1, c) if odd; open at every border.  nblocks ribbons are stored one after another
+       (ribbon q starts at site sum_{p<q} W_p L_p); each has its own a, b, c_k and M.
+       onsite = eps_j. */
+    CHEB_HONEYCOMB_ZZ = 1,
+    /* Holstein chain, Sec. 3.3, Eq. (ghm), one spinless electron, Delta_i = 0 and
+       g_i = g: H = -t sum_i (c_i^+ c_{i+1} + h.c.) - g w0 sum_i (b_i^+ + b_i) n_i
+       + w0 sum_i b_i^+ b_i, in the basis |e; n_0..n_{L-1}> with sum_i n_i <= nph (Sec. 3.3).
+       Basis index = e * Dph + rank(n), Dph = C(nph + L, L), rank = position of n in the
+       lexicographic order of all admissible tuples (n_0 most significant) -- see
+       cheb_holstein_rank.  Stored as a SELL-C-sigma matrix built on the device. */
+    CHEB_HOLSTEIN = 2
+} cheb_kind;
+
+typedef struct cheb_ham_desc {
+    int32_t kind;            /* cheb_kind */
+    /* CHEB_LAT1D */
+    int64_t n;               /* grid points                                                */
+    double dx;               /* grid spacing                                               */
+    /* CHEB_HONEYCOMB_ZZ */
+    int32_t nblocks;         /* ribbons (>= 1); also 1 for the other kinds                */
+    const int32_t* W;        /* host [nblocks]: rows (zigzag chains) of each ribbon       */
+    const int32_t* L;        /* host [nblocks]: columns of each ribbon                     */
+    double hop;              /* transfer integral t (all kinds)                            */
+    /* CHEB_LAT1D and CHEB_HONEYCOMB_ZZ: device, on-site energies (double).  Layout [site]
+       when onsite_per_vec == 0 (shared by all nvec vectors), [site][vec] when 1 (one
+       potential per vector, e.g. independent disorder realisations).  May be NULL (zero).
+       Read once at plan creation (and by cheb_plan_set_onsite). */
+    const double* onsite;
+    int32_t onsite_per_vec;
+    /* CHEB_HOLSTEIN */
+    int32_t hol_sites;       /* L                                                          */
+    int32_t hol_nph;         /* phonon cap                                                 */
+    int32_t hol_periodic;    /* 1: bond (L-1, 0) present (needs L >= 3)                   */
+    double omega0;           /* phonon frequency w0                                        */
+    double g;                /* dimensionless coupling g                                   */
+    int32_t sell_sigma;      /* SELL sorting window in rows (0 or 1: no sorting; else a
+                                multiple of 32)                                            */
+} cheb_ham_desc;
+
+typedef struct cheb_plan cheb_plan;
+
+/* ---- error text -------------------------------------------------------------------- */
+/* Message of the calling thread's most recent failing call (static storage; never NULL). */
+const char* cheb_last_error(void);
+/* Fixed text of a status code. */
+const char* cheb_strerror(int status);
+
+/* ---- Sec. 2.2: rescaling and expansion coefficients (host, FP64) ---------------------- */
+/* b = (emax + emin)/2, a = (emax - emin)(1 + alpha)/2 (Sec. 2.2, text after Eq. U_1). */
+int cheb_rescale(double emin, double emax, double alpha, double* a, double* b);
+
+/* Multipliers C_k = e^{-i b dt} (2 - delta_k0) (-i)^k J_k(a dt), k = 0..M, of Eq. (U_1)
+   with Eq. (c_k); J_k by Miller's backward recurrence normalised with
+   J_0 + 2 sum_k J_2k = 1.  M = largest k with |C_k| >= tol; M >= 2 always (an M of 1 is
+   raised to 2).  c_re, c_im: host arrays of max_order + 1 doubles (caller-owned), filled
+   for k = 0..M.  Returns CHEB_ERR_ORDER if |C_k| >= tol still holds at k = max_order. */
+int cheb_coeffs(double a, double b, double dt, double tol, int max_order, double* c_re,
+                double* c_im, int* M_out);
+
+/* ---- plans ------------------------------------------------------------------------- */
+/* Build a plan for nvec state vectors of the operator h, in precision prec (cheb_prec).
+   emin, emax: host arrays [h->nblocks] of spectral bounds (one pair per ribbon; one pair
+   for the other kinds); alpha: the safety margin of Sec. 2.2 (the paper uses 0.01).
+   The plan scales the on-site data to d_i = 2 (H_ii - b)/a once, stores it in prec's real
+   type, and allocates two recurrence vectors.  stream: a cudaStream_t or NULL.
+   Holstein plans build the basis and the SELL matrix on the device. */
+int cheb_plan_create(cheb_plan** out, const cheb_ham_desc* h, const double* emin,
+                     const double* emax, double alpha, int prec, int nvec, void* stream);
+void cheb_plan_destroy(cheb_plan* plan);
+
+/* Tolerance and order cap used by the next cheb_step/cheb_evolve (defaults 1e-14, 100000). */
+int cheb_plan_set_tol(cheb_plan* plan, double tol, int max_order);
+/* Replace the on-site energies (device pointer, same layout as in the descriptor). */
+int cheb_plan_set_onsite(cheb_plan* plan, const double* onsite);
+/* Scalars of the plan: sites per vector (total over ribbons), number of vectors, blocks,
+   and the a, b, M of block q (M for the last dt used, 0 before the first step). */
+int cheb_plan_info(const cheb_plan* plan, int64_t* sites, int* nvec, int* nblocks);
+int cheb_plan_block(const cheb_plan* plan, int q, double* a, double* b, int* M,
+                    int64_t* offset, int* W, int* L);
+
+/* ---- propagation ------------------------------------------------------------------- */
+/* psi <- U(dt) psi for all nvec vectors (device, in place, [site][vec]).  Enqueues M fused
+   recurrence kernels (M of the largest block) on the plan's stream and returns; the
+   coefficients are recomputed on the host only when dt changes (Sec. 2.2: once per dt). */
+int cheb_step(cheb_plan* plan, void* psi, double dt);
+
+/* nsteps calls of cheb_step, replayed from one CUDA graph.  If obs_every > 0 and obs is not
+   NULL, before every obs_every-th step s (s = 0, obs_every, ...) the plan records
+   [||psi||^2, <psi|H|psi>] per (block, vec) into the device array obs (double, layout
+   [record][block][vec][2], records = ceil(nsteps / obs_every)).  The energy comes from
+   the first recurrence kernel of that step (v_1 = H~ psi), so it costs no extra matvec.
+   Synchronises the stream and returns CHEB_ERR_DIVERGED if a recurrence vector exceeded
+   the bound |v_k| <= ||psi|| that holds when the spectrum lies inside [emin, emax]. */
+int cheb_evolve(cheb_plan* plan, void* psi, double dt, int nsteps, int obs_every,
+                double* obs);
+
+/* Status of the work enqueued so far: synchronises the stream, returns CHEB_ERR_DIVERGED
+   if the growth check fired since the last call (and clears it), CHEB_ERR_CUDA on an
+   asynchronous CUDA error, else CHEB_OK. */
+int cheb_sync(cheb_plan* plan);
+
+/* ---- observables (device outputs, double) ------------------------------------------ */
+typedef enum {
+    CHEB_OBS_NORM2 = 0,     /* ||psi||^2 per (block, vec)                       [nblocks][nvec] */
+    CHEB_OBS_ENERGY = 1,    /* <psi|H|psi> per (block, vec)                     [nblocks][nvec] */
+    CHEB_OBS_PROB_COLS = 2, /* ribbons: sum_{c > param} |psi|^2 per (block,vec) [nblocks][nvec];
+                               1D grid: sum over sites i > param                                 */
+    CHEB_OBS_HOL_DENSITY = 3, /* Holstein <n_i>, Sec. 3.3 (Fig. 3)                  [L][nvec] */
+    CHEB_OBS_HOL_PHONON = 4,  /* Holstein <b_i^+ b_i>                               [L][nvec] */
+    CHEB_OBS_HOL_CHI = 5      /* Holstein chi_ii = <n_i (b_i + b_i^+)>              [L][nvec] */
+} cheb_obs_kind;
+
+/* Deterministic FP64 reductions of psi (device, plan layout) into out (device doubles). */
+int cheb_observables(cheb_plan* plan, const void* psi, int kind, double param, double* out);
+
+/* ---- gradient with respect to the on-site potential ---------------------------------- */
+/* No counterpart in the paper: reverse-mode differentiation of Eqs. (U_1) and (rec) with
+   a, b held fixed (dH~/dV_i = e_i e_i^T / a).  psi_n = U(dt)^nsteps psi0 is recomputed from
+   psi0; the forward vectors of each step are regenerated from ceil(sqrt(M)) checkpoints.
+   Objective: P = sum_{sites with column > region_col} |psi_n|^2 per vector (ribbons; for
+   the 1D grid: index > region_col) when lambda_n is NULL; otherwise the caller supplies
+   lambda_n = dP/d(conj psi_n) (device, plan layout) for an arbitrary real P.
+   Outputs (device, caller-owned, may be NULL when not wanted):
+     grad   : dP/dV_i, doubles, layout of the plan's onsite array ([site] summed over vecs
+              when onsite_per_vec == 0, [site][vec] when 1);
+     lambda0: dP/d(conj psi0), plan layout and precision;
+     P      : doubles [nvec] (only with the region objective).
+   CHEB_ERR_UNSUPPORTED for Holstein plans. */
+int cheb_adjoint_potential(cheb_plan* plan, const void* psi0, double dt, int nsteps,
+                           const void* lambda_n, int64_t region_col, double* grad,
+                           void* lambda0, double* P);
+
+/* ---- Holstein basis (Sec. 3.3), host ------------------------------------------------ */
+/* Number of phonon tuples with L sites and sum <= nph: C(nph + L, L). */
+int64_t cheb_holstein_dim_phonon(int L, int nph);
+/* rank of occ[0..L-1] (uint8) in the lexicographic order of admissible tuples, combined
+   with the electron site e into idx = e * Dph + rank.  CHEB_ERR_INVALID if sum(occ) > nph. */
+int cheb_holstein_rank(int L, int nph, const uint8_t* occ, int e, int64_t* idx);
+/* Inverse of cheb_holstein_rank. */
+int cheb_holstein_unrank(int L, int nph, int64_t idx, uint8_t* occ, int* e);
+
+/* ---- tuning --------------------------------------------------------------------------- */
+/* Times the plan's recurrence kernel over a few launch shapes (threads per block, sites
+   per thread) on the plan's own workspace and keeps the fastest; results are cached per
+   plan.  Optional: plans start from a fixed default. */
+int cheb_autotune(cheb_plan* plan);
+/* Launch shape chosen for the plan: threads per block, sites per thread, grid size. */
+int cheb_plan_launch(const cheb_plan* plan, int* threads, int* sites_per_thread, int* grid);
+
+/* ---- introspection for tests ---------------------------------------------------------- */
+/* Copies of the plan's device data to host memory, for checking the construction:
+   the SELL matrix of a Holstein plan as CSR in original row order (rowptr [n+1] int64,
+   col [nnz] int64, val [nnz] double with the unscaled H entries); nnz_out gets the count.
+   Pass col = val = NULL to query nnz only. */
+int cheb_plan_export_csr(cheb_plan* plan, int64_t* rowptr, int64_t* col, double* val,
+                         int64_t* nnz_out);
+/* Number of kernel launches the plan has enqueued since creation (graph replays count
+   every kernel node). */
+int64_t cheb_plan_launches(const cheb_plan* plan);
+
+/* ---- kernel timing ------------------------------------------------------------------- */
+/* enable != 0: cheb_step/cheb_evolve launch the recurrence kernels directly (no graph) and
+   bracket each launch with a pair of CUDA events on the plan's stream; every launch also
+   records its algorithmic DRAM bytes (each vector element read or written once, the on-site
+   and SELL data read once).  cheb_plan_kernel_stats sums, over the launches since the last
+   reset, the event times (ms), the launch count and the algorithmic bytes; it synchronises
+   the stream.  reset != 0 clears the sums afterwards. */
+int cheb_plan_set_timing(cheb_plan* plan, int enable);
+int cheb_plan_kernel_stats(cheb_plan* plan, double* ms, int64_t* launches, double* bytes,
+                           int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHEB_H */

@@ -1,0 +1,307 @@
+// Gradient of a real objective P(psi_n), psi_{s+1} = U(dt) psi_s, with respect to the on-site
+// potential V_i (the diagonal of H).  The paper has no gradient; this is reverse-mode
+// differentiation of Eqs. (U_1) and (rec) with a and b held fixed, so dH~/dV_i = e_i e_i^T/a.
+//
+// Convention: for real P, xbar = dP/d(conj x) and dP = 2 Re(xbar^+ dx).  With lambda = psibar
+// of the step's output, the adjoints w_k of the recurrence vectors v_k obey (Clenshaw form)
+//   w_M     = conj(C_M) lambda
+//   w_{M-1} = conj(C_{M-1}) lambda + 2 H~ w_M
+//   w_k     = conj(C_k) lambda + 2 H~ w_{k+1} - w_{k+2}          1 <= k <= M-2
+//   w_0     = conj(C_0) lambda +   H~ w_1     - w_2
+// and the step contributes  dP/dV_i += (4/a) sum_{k=1}^{M-1} Re(conj(w_{k+1,i}) v_{k,i})
+//                                      + (2/a) Re(conj(w_{1,i}) v_{0,i});
+// the input adjoint is psibar_s = w_0.  The forward vectors v_k of a step are needed in
+// reverse order: the forward pass keeps ceil(sqrt(M+1)) checkpoint pairs (v_{jS}, v_{jS+1})
+// and each segment is recomputed into a buffer of S vectors just before it is reversed.
+// The step inputs psi_s are stored for every step of the trajectory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "cheb_internal.cuh"
+
+namespace cheb {
+
+template <typename R> struct AV2;
+template <> struct AV2<double> {
+    using C = double2;
+    static __device__ __forceinline__ C make(double x, double y) { return make_double2(x, y); }
+};
+template <> struct AV2<float> {
+    using C = float2;
+    static __device__ __forceinline__ C make(float x, float y) { return make_float2(x, y); }
+};
+
+// 2 H~ x at site gs of vector v (stencil geometry of block B)
+template <typename R>
+__device__ __forceinline__ typename AV2<R>::C stencil_2h(const typename AV2<R>::C* x,
+                                                         const DevBlock& B, int64_t sl, int64_t gs,
+                                                         int nv, int v, R d)
+{
+    const int r = (int)(sl / B.L);
+    const int c = (int)(sl - (int64_t)r * B.L);
+    const int vr = ((r + c) & 1) ? r - 1 : r + 1;
+    R sx = 0, sy = 0;
+    if (c > 0) { auto y = x[(gs - 1) * nv + v]; sx += y.x; sy += y.y; }
+    if (c + 1 < B.L) { auto y = x[(gs + 1) * nv + v]; sx += y.x; sy += y.y; }
+    if (vr >= 0 && vr < B.W) {
+        auto y = x[(gs + (int64_t)(vr - r) * B.L) * nv + v];
+        sx += y.x;
+        sy += y.y;
+    }
+    const auto o = x[gs * nv + v];
+    const R beta = (R)B.beta;
+    return AV2<R>::make(fma(d, o.x, beta * sx), fma(d, o.y, beta * sy));
+}
+
+struct AdjArgs {
+    const WorkItem* items;
+    int nitems;
+    int nvec;
+    const DevBlock* blocks;
+    const void* diag;
+    int diag_per_vec;
+};
+
+// forward recurrence without accumulation: out = H~ cur (first) or 2 H~ cur - prev
+template <typename R>
+__global__ void k_adj_forward(AdjArgs a, const void* cur_, const void* prev_, void* out_, int first)
+{
+    using C = typename AV2<R>::C;
+    const C* cur = static_cast<const C*>(cur_);
+    const C* prev = static_cast<const C*>(prev_);
+    C* out = static_cast<C*>(out_);
+    const R* diag = static_cast<const R*>(a.diag);
+    for (int w = blockIdx.x; w < a.nitems; w += gridDim.x) {
+        const WorkItem it = a.items[w];
+        const DevBlock B = a.blocks[it.block];
+        for (int64_t u = threadIdx.x; u < it.count * a.nvec; u += blockDim.x) {
+            const int64_t sl = it.first + u / a.nvec;
+            const int v = (int)(u % a.nvec);
+            const int64_t gs = B.offset + sl;
+            const R d = a.diag_per_vec ? diag[gs * a.nvec + v] : diag[gs];
+            C h = stencil_2h<R>(cur, B, sl, gs, a.nvec, v, d);
+            if (first) {
+                h.x *= (R)0.5;
+                h.y *= (R)0.5;
+            } else {
+                const C p = prev[gs * a.nvec + v];
+                h.x -= p.x;
+                h.y -= p.y;
+            }
+            out[gs * a.nvec + v] = h;
+        }
+    }
+}
+
+// reverse step k: wk_out = conj(C_k) lam + f H~ w1 - w2 (f = 2, or 1 at k = 0; no matvec at
+// k = M; no w2 for k >= M-1), grad += g Re(conj(w1) v_k) for k < M (g = 4/a, or 2/a at k = 0)
+template <typename R>
+__global__ void k_adj_reverse(AdjArgs a, int k, int M, const void* lam_, const void* w1_,
+                              void* w2out_, const void* vk_, const void* qcoef_, double* grad)
+{
+    using C = typename AV2<R>::C;
+    const C* lam = static_cast<const C*>(lam_);
+    const C* w1 = static_cast<const C*>(w1_);
+    C* w2out = static_cast<C*>(w2out_);
+    const C* vk = static_cast<const C*>(vk_);
+    using CC = typename AV2<R>::C;
+    const CC* qc = static_cast<const CC*>(qcoef_);  // (hi, lo) pairs
+    const R* diag = static_cast<const R*>(a.diag);
+    for (int w = blockIdx.x; w < a.nitems; w += gridDim.x) {
+        const WorkItem it = a.items[w];
+        const DevBlock B = a.blocks[it.block];
+        const CC qq = qc[B.coef_off + k];
+        // conj(C_k) = conj(ph) q_k (1 for even k, +i for odd k)
+        const R pr = (R)B.ph_re, pim = -(R)B.ph_im;
+        const double gfac = (k == 0 ? 2.0 : 4.0) / B.a;
+        for (int64_t sl = it.first + threadIdx.x; sl < it.first + it.count; sl += blockDim.x) {
+            const int64_t gs = B.offset + sl;
+            double gsum = 0.0;
+            for (int v = 0; v < a.nvec; ++v) {
+                const int64_t idx = gs * a.nvec + v;
+                const C l = lam[idx];
+                C lp = AV2<R>::make(pr * l.x - pim * l.y, pr * l.y + pim * l.x);
+                if (k & 1) lp = AV2<R>::make(-lp.y, lp.x);  // i * lp
+                C wk = AV2<R>::make(fma(qq.x, lp.x, qq.y * lp.x), fma(qq.x, lp.y, qq.y * lp.y));
+                if (k < M) {
+                    const R d = a.diag_per_vec ? diag[idx] : diag[gs];
+                    C h = stencil_2h<R>(w1, B, sl, gs, a.nvec, v, d);
+                    const R f = (k == 0) ? (R)0.5 : (R)1.0;
+                    wk.x += f * h.x;
+                    wk.y += f * h.y;
+                    if (k < M - 1) {
+                        const C w2 = w2out[idx];
+                        wk.x -= w2.x;
+                        wk.y -= w2.y;
+                    }
+                    const C wn = w1[idx];
+                    const C vv = vk[idx];
+                    const double gv = gfac * ((double)wn.x * vv.x + (double)wn.y * vv.y);
+                    if (a.diag_per_vec) grad[idx] += gv;
+                    else gsum += gv;
+                }
+                w2out[idx] = wk;
+            }
+            if (!a.diag_per_vec && k < M) grad[gs] += gsum;
+        }
+    }
+}
+
+// lambda_n = Pi psi_n for the region of columns > region_col
+template <typename R>
+__global__ void k_adj_region_seed(AdjArgs a, const void* psi_, void* lam_, int64_t region_col)
+{
+    using C = typename AV2<R>::C;
+    const C* psi = static_cast<const C*>(psi_);
+    C* lam = static_cast<C*>(lam_);
+    for (int w = blockIdx.x; w < a.nitems; w += gridDim.x) {
+        const WorkItem it = a.items[w];
+        const DevBlock B = a.blocks[it.block];
+        for (int64_t u = threadIdx.x; u < it.count * a.nvec; u += blockDim.x) {
+            const int64_t sl = it.first + u / a.nvec;
+            const int v = (int)(u % a.nvec);
+            const int64_t gs = B.offset + sl;
+            const int r = (int)(sl / B.L);
+            const int64_t c = sl - (int64_t)r * B.L;
+            lam[gs * a.nvec + v] = (c > region_col) ? psi[gs * a.nvec + v] : AV2<R>::make(0, 0);
+        }
+    }
+}
+
+template <typename R>
+static int adjoint_impl(Plan* p, const void* psi0, int nsteps, const void* lambda_n,
+                        int64_t region_col, double* grad, void* lambda0, double* P)
+{
+    cudaStream_t s = p->stream;
+    const size_t vb = p->vec_bytes();
+    const DevBlock B = p->hblocks[0];
+    const int M = B.M;
+    const int S = (int)std::ceil(std::sqrt((double)(M + 1)));
+    const int nseg = (M + 1 + S - 1) / S;
+    AdjArgs a{p->d_items, (int)p->hitems.size(), p->nvec, p->d_blocks, p->d_diag,
+              p->desc.onsite_per_vec};
+    const int grid = std::min<int>(a.nitems, 65535);
+    const int th = 256;
+
+    // workspace: trajectory, checkpoints, segment, two adjoint buffers, lambda
+    char* ws = nullptr;
+    const size_t nvecs = (size_t)(nsteps + 1) + 2 * (size_t)nseg + (size_t)S + 3;
+    CHEB_CUDA(cudaMalloc(&ws, nvecs * vb));
+    auto V = [&](size_t i) { return static_cast<void*>(ws + i * vb); };
+    const size_t o_traj = 0, o_ck = nsteps + 1, o_seg = o_ck + 2 * nseg, o_w = o_seg + S,
+                 o_lam = o_w + 2;
+    int rc = CHEB_OK;
+    auto done = [&](int code) {
+        cudaStreamSynchronize(s);
+        cudaFree(ws);
+        return code;
+    };
+    // forward trajectory with the fused propagator
+    if (cudaMemcpyAsync(V(o_traj), psi0, vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return done(fail(CHEB_ERR_CUDA, "adjoint: copy psi0"));
+    for (int st = 0; st < nsteps; ++st) {
+        if (cudaMemcpyAsync(V(o_traj + st + 1), V(o_traj + st), vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return done(fail(CHEB_ERR_CUDA, "adjoint: copy step"));
+        rc = cheb_step(reinterpret_cast<cheb_plan*>(p), V(o_traj + st + 1), p->dt);
+        if (rc) return done(rc);
+    }
+    // seed
+    void* lam = V(o_lam);
+    if (lambda_n) {
+        if (cudaMemcpyAsync(lam, lambda_n, vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return done(fail(CHEB_ERR_CUDA, "adjoint: copy lambda_n"));
+    } else {
+        k_adj_region_seed<R><<<grid, th, 0, s>>>(a, V(o_traj + nsteps), lam, region_col);
+        p->launches++;
+        if (P) {
+            rc = launch_observable(p, V(o_traj + nsteps), CHEB_OBS_PROB_COLS, (double)region_col, P, s);
+            if (rc) return done(rc);
+        }
+    }
+    const size_t gbytes = (size_t)p->n_sites * (p->desc.onsite_per_vec ? p->nvec : 1) * sizeof(double);
+    double* g = grad;
+    double* gtmp = nullptr;
+    if (!g) {
+        if (cudaMalloc(&gtmp, gbytes) != cudaSuccess) return done(fail(CHEB_ERR_NOMEM, "adjoint grad"));
+        g = gtmp;
+    }
+    cudaMemsetAsync(g, 0, gbytes, s);
+    auto fwd = [&](const void* cur, const void* prev, void* out, int first) {
+        k_adj_forward<R><<<grid, th, 0, s>>>(a, cur, prev, out, first);
+        p->launches++;
+    };
+    for (int st = nsteps - 1; st >= 0; --st) {
+        // checkpoints of this step: pairs (v_{jS}, v_{jS+1})
+        void* P0 = V(o_seg);
+        void* P1 = V(o_seg + 1);
+        cudaMemcpyAsync(P0, V(o_traj + st), vb, cudaMemcpyDeviceToDevice, s);  // v_0
+        fwd(P0, nullptr, P1, 1);                                                // v_1
+        // P0 holds v_k, P1 holds v_{k+1}
+        for (int k = 0; k <= M; ++k) {
+            if (k % S == 0) {
+                const int j = k / S;
+                cudaMemcpyAsync(V(o_ck + 2 * j), P0, vb, cudaMemcpyDeviceToDevice, s);
+                if (k + 1 <= M) cudaMemcpyAsync(V(o_ck + 2 * j + 1), P1, vb, cudaMemcpyDeviceToDevice, s);
+            }
+            if (k + 2 <= M) {
+                fwd(P1, P0, P0, 0);  // v_{k+2} over v_k
+                std::swap(P0, P1);
+            } else if (k + 1 <= M) {
+                std::swap(P0, P1);   // P0 = v_M for a checkpoint that starts at k = M
+            } else {
+                break;
+            }
+        }
+        // reverse over segments
+        for (int j = nseg - 1; j >= 0; --j) {
+            const int k0 = j * S, k1 = std::min(k0 + S - 1, M);
+            cudaMemcpyAsync(V(o_seg), V(o_ck + 2 * j), vb, cudaMemcpyDeviceToDevice, s);
+            if (k1 > k0) cudaMemcpyAsync(V(o_seg + 1), V(o_ck + 2 * j + 1), vb, cudaMemcpyDeviceToDevice, s);
+            for (int k = k0 + 2; k <= k1; ++k)
+                fwd(V(o_seg + (k - 1 - k0)), V(o_seg + (k - 2 - k0)), V(o_seg + (k - k0)), 0);
+            for (int k = k1; k >= k0; --k) {
+                void* wk = V(o_w + (k & 1));            // w_k overwrites w_{k+2}
+                const void* w1 = V(o_w + ((k + 1) & 1)); // w_{k+1}
+                k_adj_reverse<R><<<grid, th, 0, s>>>(a, k, M, lam, w1, wk, V(o_seg + (k - k0)),
+                                                     p->d_qcoef, g);
+                p->launches++;
+            }
+        }
+        // lambda_s = w_0
+        cudaMemcpyAsync(lam, V(o_w + 0), vb, cudaMemcpyDeviceToDevice, s);
+    }
+    if (lambda0) cudaMemcpyAsync(lambda0, lam, vb, cudaMemcpyDeviceToDevice, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (gtmp) cudaFree(gtmp);
+    if (e != cudaSuccess) return done(cuda_fail(e, "adjoint kernels"));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return done(cuda_fail(e, "adjoint launch"));
+    return done(CHEB_OK);
+}
+
+}  // namespace cheb
+
+using namespace cheb;
+
+extern "C" int cheb_adjoint_potential(cheb_plan* plan, const void* psi0, double dt, int nsteps,
+                                      const void* lambda_n, int64_t region_col, double* grad,
+                                      void* lambda0, double* P)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p || !psi0) return fail(CHEB_ERR_INVALID, "cheb_adjoint_potential: NULL argument");
+    if (p->op != OP_STENCIL) return fail(CHEB_ERR_UNSUPPORTED, "adjoint needs a lattice plan");
+    if (p->nblocks != 1) return fail(CHEB_ERR_UNSUPPORTED, "adjoint needs a single block");
+    if (nsteps < 0) return fail(CHEB_ERR_INVALID, "nsteps < 0");
+    const void* ptrs[] = {psi0, lambda_n, grad, lambda0, P};
+    for (const void* q : ptrs)
+        if (q && !aligned16(q)) return fail(CHEB_ERR_ALIGN, "adjoint: pointers must be 16-byte aligned");
+    // a zero-step evolve sets dt (and the coefficients) without propagating
+    int rc = cheb_evolve(plan, const_cast<void*>(psi0), dt, 0, 0, nullptr);
+    if (rc) return rc;
+    if (p->prec == CHEB_C128)
+        return adjoint_impl<double>(p, psi0, nsteps, lambda_n, region_col, grad, lambda0, P);
+    return adjoint_impl<float>(p, psi0, nsteps, lambda_n, region_col, grad, lambda0, P);
+}

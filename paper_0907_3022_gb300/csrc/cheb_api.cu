@@ -1,0 +1,762 @@
+// Plan lifecycle, propagation (Sec. 2.2), observables and tuning behind the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cheb_internal.cuh"
+
+namespace cheb {
+
+static thread_local std::string g_last_error = "no error";
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return CHEB_ERR_CUDA;
+}
+
+int vpt_for(int prec, int nvec);
+
+// Split every block into tiles of `tile` sites; Holstein tiles also never straddle two
+// electron sites (blocks of Dph rows), so per-tile observables have a single slot.
+int plan_build_items(Plan* p)
+{
+    const int nvg = p->nvec / vpt_for(p->prec, p->nvec);
+    int64_t tile = (int64_t)p->threads * p->spt / nvg;
+    if (tile < 1) tile = 1;
+    p->tile = tile;
+    p->hitems.clear();
+    p->hblock_item_begin.assign(p->nblocks + 1, 0);
+    for (int q = 0; q < p->nblocks; ++q) {
+        p->hblock_item_begin[q] = (int32_t)p->hitems.size();
+        const DevBlock& B = p->hblocks[q];
+        const int64_t n = (p->desc.kind == CHEB_HOLSTEIN) ? p->n_sites : (int64_t)B.W * B.L;
+        const int64_t seg = (p->desc.kind == CHEB_HOLSTEIN) ? p->hol_dph : n;
+        for (int64_t s0 = 0; s0 < n; s0 += seg) {
+            const int64_t s1 = std::min(n, s0 + seg);
+            for (int64_t f = s0; f < s1; f += tile) {
+                WorkItem it;
+                it.block = q;
+                it.pad = 0;
+                it.first = f;
+                it.count = std::min(tile, s1 - f);
+                p->hitems.push_back(it);
+            }
+        }
+    }
+    p->hblock_item_begin[p->nblocks] = (int32_t)p->hitems.size();
+    if (p->hitems.size() >= (size_t)INT32_MAX) return fail(CHEB_ERR_INVALID, "too many work items");
+    if (p->d_items) cudaFree(p->d_items);
+    if (p->d_block_item_begin) cudaFree(p->d_block_item_begin);
+    if (p->d_partials) cudaFree(p->d_partials);
+    p->d_items = nullptr;
+    p->d_block_item_begin = nullptr;
+    p->d_partials = nullptr;
+    CHEB_CUDA(cudaMalloc(&p->d_items, p->hitems.size() * sizeof(WorkItem)));
+    CHEB_CUDA(cudaMemcpy(p->d_items, p->hitems.data(), p->hitems.size() * sizeof(WorkItem),
+                         cudaMemcpyHostToDevice));
+    CHEB_CUDA(cudaMalloc(&p->d_block_item_begin, (p->nblocks + 1) * sizeof(int32_t)));
+    CHEB_CUDA(cudaMemcpy(p->d_block_item_begin, p->hblock_item_begin.data(),
+                         (p->nblocks + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CHEB_CUDA(cudaMalloc(&p->d_partials, p->hitems.size() * p->nvec * 2 * sizeof(double)));
+    p->shape_epoch++;
+    return CHEB_OK;
+}
+
+static int upload_blocks(Plan* p)
+{
+    CHEB_CUDA(cudaMemcpy(p->d_blocks, p->hblocks.data(), p->hblocks.size() * sizeof(DevBlock),
+                         cudaMemcpyHostToDevice));
+    return CHEB_OK;
+}
+
+// Coefficients for a new dt: q_k = sign_k (2 - delta_k0) J_k(a dt) with sign_k = +1 for
+// k mod 4 in {0, 1} and -1 for {2, 3}, so that (-i)^k (2 - delta_k0) J_k = q_k (1 or -i).
+static int set_dt(Plan* p, double dt)
+{
+    if (p->have_dt && dt == p->dt) return CHEB_OK;
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(CHEB_ERR_INVALID, "dt must be >= 0");
+    std::vector<double> table;
+    int maxM = 0;
+    for (int q = 0; q < p->nblocks; ++q) {
+        DevBlock& B = p->hblocks[q];
+        std::vector<double> cre((size_t)p->max_order + 1), cim((size_t)p->max_order + 1);
+        int M = 0;
+        int rc = cheb_coeffs(B.a, B.b, dt, p->tol, p->max_order, cre.data(), cim.data(), &M);
+        if (rc) return rc;
+        // recover q_k from C_k = e^{-i b dt} (-i)^k g_k: use the Bessel values directly
+        std::vector<double> J;
+        const long natural = (long)std::ceil(B.a * dt + 60.0 + 20.0 * std::cbrt(B.a * dt));
+        const int kmax = (int)std::min<long>((long)p->max_order, std::max<long>(natural, M));
+        if (bessel_j_seq(B.a * dt, kmax, J) != 0) return fail(CHEB_ERR_INVALID, "Bessel failed");
+        B.M = M;
+        B.coef_off = (int32_t)table.size();
+        int ksplit = 2;
+        for (int k = 0; k <= M; ++k) {
+            const double g = (k == 0 ? 1.0 : 2.0) * J[(size_t)k];
+            table.push_back(((k & 3) >= 2) ? -g : g);
+            if (std::fabs(g) >= 1.0 / 256.0) ksplit = std::max(ksplit, k);
+        }
+        // complex64: orders with |q_k| < 2^-8 go to the tail accumulator
+        B.ksplit = (p->prec == CHEB_C64) ? ksplit : M;
+        B.ph_re = std::cos(B.b * dt);
+        B.ph_im = -std::sin(B.b * dt);
+        maxM = std::max(maxM, M);
+    }
+    // device table: (hi, lo) pairs in the plan's real type, q = hi + lo (lo = 0 for double)
+    const size_t bytes = table.size() * 2 * p->real_size();
+    if (p->qcoef_cap < bytes) {
+        if (p->d_qcoef) cudaFree(p->d_qcoef);
+        p->d_qcoef = nullptr;
+        p->qcoef_cap = 0;
+        CHEB_CUDA(cudaMalloc(&p->d_qcoef, bytes));
+        p->qcoef_cap = bytes;
+    }
+    if (p->prec == CHEB_C128) {
+        std::vector<double> t2(2 * table.size(), 0.0);
+        for (size_t i = 0; i < table.size(); ++i) t2[2 * i] = table[i];
+        CHEB_CUDA(cudaMemcpy(p->d_qcoef, t2.data(), bytes, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> t2(2 * table.size());
+        for (size_t i = 0; i < table.size(); ++i) {
+            const float hi = (float)table[i];
+            t2[2 * i] = hi;
+            t2[2 * i + 1] = (float)(table[i] - (double)hi);
+        }
+        CHEB_CUDA(cudaMemcpy(p->d_qcoef, t2.data(), bytes, cudaMemcpyHostToDevice));
+    }
+    int rc = upload_blocks(p);
+    if (rc) return rc;
+    p->max_M = maxM;
+    p->dt = dt;
+    p->have_dt = true;
+    p->shape_epoch++;
+    return CHEB_OK;
+}
+
+static RecArgs base_args(Plan* p)
+{
+    RecArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.items = p->d_items;
+    a.nitems = (int32_t)p->hitems.size();
+    a.nvec = p->nvec;
+    a.blocks = p->d_blocks;
+    a.diag = p->d_diag;
+    a.diag_per_vec = p->desc.onsite_per_vec;
+    a.qcoef = p->d_qcoef;
+    a.sell_col = p->d_sell_col;
+    a.sell_val = p->d_sell_val;
+    a.sell_chunk_off = p->d_sell_chunk_off;
+    a.sell_chunk_len = p->d_sell_chunk_len;
+    a.partials = p->d_partials;
+    a.done_counter = p->d_counter;
+    a.red_out = p->d_red;
+    a.nblocks = p->nblocks;
+    a.block_item_begin = p->d_block_item_begin;
+    a.norm2 = p->d_red;
+    a.errflag = p->d_err;
+    a.tail = p->d_tail;
+    return a;
+}
+
+// Algorithmic DRAM bytes of the launch forming T_k: every vector element the launch touches
+// read or written once, the on-site data (and SELL entries) read once, for the sites of the
+// blocks whose order reaches k.
+static double launch_bytes(const Plan* p, int k)
+{
+    const double cs = (double)p->cplx_size() * p->nvec;
+    const double ds = (double)p->real_size() * (p->desc.onsite_per_vec ? p->nvec : 1);
+    double total = 0.0;
+    for (const DevBlock& B : p->hblocks) {
+        if (k > B.M) continue;
+        const double sites = (p->op == OP_SELL) ? (double)p->n_sites : (double)B.W * B.L;
+        double vecs;  // vectors read + written per site
+        if (k == 1) vecs = 3;            // read psi; write T_0, T_1
+        else if (k == 2) vecs = 4;       // read T_1, T_0; write T_2, psi
+        else {
+            const bool to_tail = k > B.ksplit;
+            vecs = 5;                    // read T_k, T_{k-1}, acc; write T_{k+1}, acc
+            if (to_tail && k == B.ksplit + 1) vecs -= 1;      // tail starts: not read
+            if (to_tail && k == B.M && k > B.ksplit + 1) vecs += 1;  // last: tail and psi read
+        }
+        total += sites * (vecs * cs + ds);
+    }
+    if (p->op == OP_SELL) total += (double)p->sell_nnz_stored * (4.0 + (double)p->real_size());
+    return total;
+}
+
+static int timed_launch(Plan* p, const RecArgs& a, cudaStream_t s)
+{
+    if (!p->timing) return launch_recurrence(p, a, p->op, p->prec, s);
+    if (p->ev_used + 2 > p->ev_pool.size()) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t e;
+            CHEB_CUDA(cudaEventCreate(&e));
+            p->ev_pool.push_back(e);
+        }
+    }
+    CHEB_CUDA(cudaEventRecord(p->ev_pool[p->ev_used], s));
+    int rc = launch_recurrence(p, a, p->op, p->prec, s);
+    if (rc) return rc;
+    CHEB_CUDA(cudaEventRecord(p->ev_pool[p->ev_used + 1], s));
+    p->ev_used += 2;
+    p->ev_bytes.push_back(launch_bytes(p, a.j + 1));
+    return CHEB_OK;
+}
+
+// fold the recorded event pairs into the sums (synchronises)
+static int collect_timing(Plan* p)
+{
+    if (p->ev_used == 0) return CHEB_OK;
+    CHEB_CUDA(cudaEventSynchronize(p->ev_pool[p->ev_used - 1]));
+    for (size_t i = 0; i < p->ev_used; i += 2) {
+        float ms = 0.0f;
+        CHEB_CUDA(cudaEventElapsedTime(&ms, p->ev_pool[i], p->ev_pool[i + 1]));
+        p->t_ms += ms;
+        p->t_bytes += p->ev_bytes[i / 2];
+        p->t_launches++;
+    }
+    p->ev_used = 0;
+    p->ev_bytes.clear();
+    return CHEB_OK;
+}
+
+// Enqueue the M_max fused kernels of one step on stream s.
+static int enqueue_step(Plan* p, void* psi, cudaStream_t s)
+{
+    RecArgs a = base_args(p);
+    if (p->timing && p->ev_used > 4096) {  // keep the event pool bounded
+        int rc = collect_timing(p);
+        if (rc) return rc;
+    }
+    for (int j = 0; j < p->max_M; ++j) {
+        a.j = j;
+        if (j == 0) {
+            a.mode = REC_FIRST;
+            a.cur = psi;
+            a.prev = p->d_A;
+            a.out1 = p->d_B;
+            a.psi = nullptr;
+        } else {
+            a.mode = (j == 1) ? REC_SECOND : REC_GENERAL;
+            a.cur = (j & 1) ? p->d_B : p->d_A;
+            a.prev = (j & 1) ? p->d_A : p->d_B;
+            a.out1 = nullptr;
+            a.psi = psi;
+        }
+        int rc = timed_launch(p, a, s);
+        if (rc) return rc;
+    }
+    return CHEB_OK;
+}
+
+static int check_psi(const Plan* p, const void* psi)
+{
+    if (!psi) return fail(CHEB_ERR_INVALID, "psi is NULL");
+    if (!aligned16(psi)) return fail(CHEB_ERR_ALIGN, "psi must be 16-byte aligned");
+    return CHEB_OK;
+}
+
+static int ensure_graph(Plan* p, void* psi)
+{
+    if (p->graph && p->graph_psi == psi && p->graph_epoch == p->shape_epoch) return CHEB_OK;
+    if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CHEB_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = p->launches;
+    int rc = enqueue_step(p, psi, p->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+    const int64_t captured = p->launches - before;
+    p->launches = before;  // captured launches are counted when the graph is replayed
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&p->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+    p->graph_psi = psi;
+    p->graph_epoch = p->shape_epoch;
+    p->graph_kernels = (int)captured;
+    return CHEB_OK;
+}
+
+static void free_plan(Plan* p)
+{
+    if (!p) return;
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    void* ptrs[] = {p->d_blocks, p->d_items, p->d_block_item_begin, p->d_diag, p->d_A, p->d_B,
+                    p->d_tail,
+                    p->d_qcoef, p->d_partials, p->d_counter, p->d_red, p->d_err,
+                    p->d_obs_scratch, p->d_sell_col, p->d_sell_val, p->d_sell_chunk_off,
+                    p->d_sell_chunk_len, p->d_hol_diag_raw, p->d_sell_val_raw, p->d_binom,
+                    p->d_hol_rowlen};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    delete p;
+}
+
+}  // namespace cheb
+
+using namespace cheb;
+
+extern "C" const char* cheb_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* cheb_strerror(int status)
+{
+    switch (status) {
+        case CHEB_OK: return "ok";
+        case CHEB_ERR_INVALID: return "invalid argument";
+        case CHEB_ERR_ALIGN: return "device pointer not 16-byte aligned";
+        case CHEB_ERR_CUDA: return "CUDA runtime error";
+        case CHEB_ERR_NOMEM: return "out of memory";
+        case CHEB_ERR_UNSUPPORTED: return "unsupported for this operator";
+        case CHEB_ERR_ORDER: return "expansion order limit reached";
+        case CHEB_ERR_DIVERGED: return "recurrence diverged (spectral bounds too tight)";
+        case CHEB_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int cheb_plan_create(cheb_plan** out, const cheb_ham_desc* h, const double* emin,
+                                const double* emax, double alpha, int prec, int nvec,
+                                void* stream)
+{
+    if (!out || !h || !emin || !emax) return fail(CHEB_ERR_INVALID, "cheb_plan_create: NULL argument");
+    *out = nullptr;
+    if (prec != CHEB_C128 && prec != CHEB_C64) return fail(CHEB_ERR_INVALID, "bad precision");
+    if (nvec < 1 || nvec > 32 || (nvec & (nvec - 1)) != 0)
+        return fail(CHEB_ERR_INVALID, "nvec must be a power of two in [1, 32]");
+    if (!(alpha >= 0.0)) return fail(CHEB_ERR_INVALID, "alpha must be >= 0");
+    Plan* p = new Plan();
+    p->desc = *h;
+    p->prec = prec;
+    p->nvec = nvec;
+    p->alpha = alpha;
+    p->stream = static_cast<cudaStream_t>(stream);
+    int rc = CHEB_OK;
+    auto bail = [&](int code) {
+        free_plan(p);
+        return code;
+    };
+    if (cudaGetDevice(&p->device) != cudaSuccess) return bail(fail(CHEB_ERR_CUDA, "no CUDA device"));
+    cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(CHEB_ERR_CUDA, "stream creation failed"));
+
+    if (h->onsite && !aligned16(h->onsite))
+        return bail(fail(CHEB_ERR_ALIGN, "onsite must be 16-byte aligned"));
+    if (h->onsite_per_vec && h->kind == CHEB_HOLSTEIN)
+        return bail(fail(CHEB_ERR_UNSUPPORTED, "per-vector on-site data needs a lattice kind"));
+    switch (h->kind) {
+        case CHEB_LAT1D: {
+            if (h->n < 1 || h->n > INT32_MAX || !(h->dx > 0.0))
+                return bail(fail(CHEB_ERR_INVALID, "LAT1D needs 1 <= n < 2^31 and dx > 0"));
+            p->nblocks = 1;
+            p->op = OP_STENCIL;
+            DevBlock B{};
+            B.offset = 0;
+            B.W = 1;
+            B.L = (int32_t)h->n;
+            p->hblocks.push_back(B);
+            p->n_sites = h->n;
+            break;
+        }
+        case CHEB_HONEYCOMB_ZZ: {
+            if (h->nblocks < 1 || !h->W || !h->L)
+                return bail(fail(CHEB_ERR_INVALID, "HONEYCOMB_ZZ needs nblocks >= 1 and W, L arrays"));
+            p->nblocks = h->nblocks;
+            p->op = OP_STENCIL;
+            int64_t off = 0;
+            for (int q = 0; q < h->nblocks; ++q) {
+                if (h->W[q] < 1 || h->L[q] < 1 || (int64_t)h->W[q] * h->L[q] > INT32_MAX)
+                    return bail(fail(CHEB_ERR_INVALID, "ribbon sizes must be >= 1 and W*L < 2^31"));
+                DevBlock B{};
+                B.offset = off;
+                B.W = h->W[q];
+                B.L = h->L[q];
+                p->hblocks.push_back(B);
+                off += (int64_t)h->W[q] * h->L[q];
+            }
+            p->n_sites = off;
+            break;
+        }
+        case CHEB_HOLSTEIN: {
+            if (h->hol_sites < 1 || h->hol_sites > 64 || h->hol_nph < 0 || h->hol_nph > 255 ||
+                (h->hol_periodic && h->hol_sites < 3))
+                return bail(fail(CHEB_ERR_INVALID, "HOLSTEIN needs 1 <= L <= 64 (L >= 3 periodic), 0 <= nph <= 255"));
+            p->nblocks = 1;
+            p->op = OP_SELL;
+            const int64_t dph = cheb_holstein_dim_phonon(h->hol_sites, h->hol_nph);
+            if (dph < 1) return bail(fail(CHEB_ERR_INVALID, "Holstein basis too large"));
+            p->hol_dph = dph;
+            DevBlock B{};
+            B.offset = 0;
+            B.W = 1;
+            B.L = 1;
+            p->hblocks.push_back(B);
+            p->n_sites = (int64_t)h->hol_sites * dph;
+            if (p->n_sites >= ((int64_t)1 << 31) - 64)
+                return bail(fail(CHEB_ERR_INVALID, "Holstein dimension >= 2^31"));
+            break;
+        }
+        default:
+            return bail(fail(CHEB_ERR_INVALID, "unknown operator kind"));
+    }
+    // rescaling per block (Sec. 2.2)
+    for (int q = 0; q < p->nblocks; ++q) {
+        double a = 0, b = 0;
+        rc = cheb_rescale(emin[q], emax[q], alpha, &a, &b);
+        if (rc) return bail(rc);
+        DevBlock& B = p->hblocks[q];
+        B.a = a;
+        B.b = b;
+        B.M = 0;
+        B.ph_re = 1.0;
+        B.ph_im = 0.0;
+        // scaled off-diagonal: 1D grid -1/(2 dx^2); ribbons -t
+        const double off = (h->kind == CHEB_LAT1D) ? -0.5 / (h->dx * h->dx) : -h->hop;
+        B.beta = 2.0 * off / a;
+        p->emin.push_back(emin[q]);
+        p->emax.push_back(emax[q]);
+    }
+    // device allocations
+    if (cudaMalloc(&p->d_blocks, p->hblocks.size() * sizeof(DevBlock)) != cudaSuccess)
+        return bail(fail(CHEB_ERR_NOMEM, "cudaMalloc blocks"));
+    rc = upload_blocks(p);
+    if (rc) return bail(rc);
+    const size_t per = (h->onsite_per_vec ? (size_t)nvec : 1);
+    if (cudaMalloc(&p->d_diag, (size_t)p->n_sites * per * p->real_size()) != cudaSuccess ||
+        cudaMalloc(&p->d_A, p->vec_bytes()) != cudaSuccess ||
+        cudaMalloc(&p->d_B, p->vec_bytes()) != cudaSuccess ||
+        (prec == CHEB_C64 && cudaMalloc(&p->d_tail, p->vec_bytes()) != cudaSuccess) ||
+        cudaMalloc(&p->d_counter, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc(&p->d_red, (size_t)p->nblocks * nvec * 2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess)
+        return bail(fail(CHEB_ERR_NOMEM, "cudaMalloc workspace"));
+    if (cudaMemset(p->d_counter, 0, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(p->d_red, 0, (size_t)p->nblocks * nvec * 2 * sizeof(double)) != cudaSuccess)
+        return bail(fail(CHEB_ERR_CUDA, "cudaMemset workspace"));
+    rc = plan_build_items(p);
+    if (rc) return bail(rc);
+    if (h->kind == CHEB_HOLSTEIN) {
+        rc = holstein_build(p);
+        if (rc) return bail(rc);
+    } else {
+        rc = launch_scale_diag(p, h->onsite, p->stream);
+        if (rc) return bail(rc);
+    }
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess)
+        return bail(fail(CHEB_ERR_CUDA, "plan setup kernels failed"));
+    // the descriptor's host arrays are not kept
+    p->desc.W = nullptr;
+    p->desc.L = nullptr;
+    *out = reinterpret_cast<cheb_plan*>(p);
+    return CHEB_OK;
+}
+
+extern "C" void cheb_plan_destroy(cheb_plan* plan)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return;
+    cudaStreamSynchronize(p->stream);
+    free_plan(p);
+}
+
+extern "C" int cheb_plan_set_tol(cheb_plan* plan, double tol, int max_order)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p || !(tol > 0.0) || max_order < 2) return fail(CHEB_ERR_INVALID, "cheb_plan_set_tol");
+    p->tol = tol;
+    p->max_order = max_order;
+    p->have_dt = false;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_set_onsite(cheb_plan* plan, const double* onsite)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    if (p->desc.kind == CHEB_HOLSTEIN)
+        return fail(CHEB_ERR_UNSUPPORTED, "on-site data of a Holstein plan is fixed at creation");
+    if (onsite && !aligned16(onsite)) return fail(CHEB_ERR_ALIGN, "onsite must be 16-byte aligned");
+    return launch_scale_diag(p, onsite, p->stream);
+}
+
+extern "C" int cheb_plan_info(const cheb_plan* plan, int64_t* sites, int* nvec, int* nblocks)
+{
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    if (sites) *sites = p->n_sites;
+    if (nvec) *nvec = p->nvec;
+    if (nblocks) *nblocks = p->nblocks;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_block(const cheb_plan* plan, int q, double* a, double* b, int* M,
+                               int64_t* offset, int* W, int* L)
+{
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    if (!p || q < 0 || q >= p->nblocks) return fail(CHEB_ERR_INVALID, "cheb_plan_block");
+    const DevBlock& B = p->hblocks[q];
+    if (a) *a = B.a;
+    if (b) *b = B.b;
+    if (M) *M = p->have_dt ? B.M : 0;
+    if (offset) *offset = B.offset;
+    if (W) *W = B.W;
+    if (L) *L = B.L;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_step(cheb_plan* plan, void* psi, double dt)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    int rc = check_psi(p, psi);
+    if (rc) return rc;
+    rc = set_dt(p, dt);
+    if (rc) return rc;
+    return enqueue_step(p, psi, p->stream);
+}
+
+extern "C" int cheb_sync(cheb_plan* plan)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    int flag = 0;
+    CHEB_CUDA(cudaMemcpyAsync(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CHEB_CUDA(cudaStreamSynchronize(p->stream));
+    if (flag) {
+        CHEB_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream));
+        CHEB_CUDA(cudaStreamSynchronize(p->stream));
+        return fail(CHEB_ERR_DIVERGED, "a recurrence vector exceeded ||psi||: spectral bounds too tight");
+    }
+    return CHEB_OK;
+}
+
+extern "C" int cheb_evolve(cheb_plan* plan, void* psi, double dt, int nsteps, int obs_every,
+                           double* obs)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    if (nsteps < 0) return fail(CHEB_ERR_INVALID, "nsteps < 0");
+    int rc = check_psi(p, psi);
+    if (rc) return rc;
+    if (obs && !aligned16(obs)) return fail(CHEB_ERR_ALIGN, "obs must be 16-byte aligned");
+    rc = set_dt(p, dt);
+    if (rc) return rc;
+    if (nsteps == 0) return CHEB_OK;
+    if (!p->timing) {
+        rc = ensure_graph(p, psi);
+        if (rc) return rc;
+    }
+    const size_t rec_bytes = (size_t)p->nblocks * p->nvec * 2 * sizeof(double);
+    for (int s = 0; s < nsteps; ++s) {
+        if (p->timing) {
+            rc = enqueue_step(p, psi, p->stream);
+            if (rc) return rc;
+        } else {
+            CHEB_CUDA(cudaGraphLaunch(p->graph, p->stream));
+            p->launches += p->graph_kernels;
+        }
+        if (obs && obs_every > 0 && s % obs_every == 0) {
+            CHEB_CUDA(cudaMemcpyAsync(obs + (size_t)(s / obs_every) * p->nblocks * p->nvec * 2,
+                                      p->d_red, rec_bytes, cudaMemcpyDeviceToDevice, p->stream));
+        }
+    }
+    return cheb_sync(plan);
+}
+
+extern "C" int cheb_observables(cheb_plan* plan, const void* psi, int kind, double param,
+                                double* out)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p || !out) return fail(CHEB_ERR_INVALID, "cheb_observables: NULL argument");
+    int rc = check_psi(p, psi);
+    if (rc) return rc;
+    if (!aligned16(out)) return fail(CHEB_ERR_ALIGN, "out must be 16-byte aligned");
+    if (kind < CHEB_OBS_NORM2 || kind > CHEB_OBS_HOL_CHI) return fail(CHEB_ERR_INVALID, "bad kind");
+    return launch_observable(p, psi, kind, param, out, p->stream);
+}
+
+extern "C" int cheb_plan_launch(const cheb_plan* plan, int* threads, int* spt, int* grid)
+{
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    if (threads) *threads = p->threads;
+    if (spt) *spt = p->spt;
+    if (grid) *grid = p->grid_cap > 0 ? std::min<int>(p->grid_cap, (int)p->hitems.size())
+                                      : (int)p->hitems.size();
+    return CHEB_OK;
+}
+
+extern "C" int64_t cheb_plan_launches(const cheb_plan* plan)
+{
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    return p ? p->launches : -1;
+}
+
+// Autotuner: time one GENERAL-order launch per candidate (threads, sites/thread, grid cap)
+// on the plan's own vectors and keep the fastest.
+extern "C" int cheb_autotune(cheb_plan* plan)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    if (!p->have_dt) return fail(CHEB_ERR_STATE, "cheb_autotune: run a step (set dt) first");
+    if (p->max_M < 3) return CHEB_OK;
+    void* scratch = nullptr;
+    CHEB_CUDA(cudaMalloc(&scratch, p->vec_bytes()));
+    CHEB_CUDA(cudaMemsetAsync(scratch, 0, p->vec_bytes(), p->stream));
+    CHEB_CUDA(cudaMemsetAsync(p->d_A, 0, p->vec_bytes(), p->stream));
+    CHEB_CUDA(cudaMemsetAsync(p->d_B, 0, p->vec_bytes(), p->stream));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int th_c[] = {128, 256, 512};
+    const int spt_c[] = {1, 2, 4};
+    const int cap_c[] = {0, 4, 8, 16};
+    float best = 1e30f;
+    int bt = p->threads, bs = p->spt, bc = p->grid_cap;
+    int rc = CHEB_OK;
+    const int64_t launches0 = p->launches;
+    for (int th : th_c) {
+        for (int spt : spt_c) {
+            p->threads = th;
+            p->spt = spt;
+            rc = plan_build_items(p);
+            if (rc) break;
+            for (int capm : cap_c) {
+                p->grid_cap = capm ? capm * p->num_sms : 0;
+                RecArgs a = base_args(p);
+                a.mode = REC_GENERAL;
+                a.j = 2;
+                a.cur = p->d_A;
+                a.prev = p->d_B;
+                a.psi = scratch;
+                float tot = 0.0f;
+                for (int rep = 0; rep < 4; ++rep) {
+                    cudaEventRecord(e0, p->stream);
+                    rc = launch_recurrence(p, a, p->op, p->prec, p->stream);
+                    cudaEventRecord(e1, p->stream);
+                    if (rc) break;
+                    cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) tot += ms;  // first launch is warm-up
+                }
+                if (rc) break;
+                if (tot < best) {
+                    best = tot;
+                    bt = th;
+                    bs = spt;
+                    bc = p->grid_cap;
+                }
+            }
+            if (rc) break;
+        }
+        if (rc) break;
+    }
+    p->launches = launches0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    p->threads = bt;
+    p->spt = bs;
+    p->grid_cap = bc;
+    int rc2 = plan_build_items(p);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    p->tuned = true;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_export_csr(cheb_plan* plan, int64_t* rowptr, int64_t* col, double* val,
+                                    int64_t* nnz_out)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p || !nnz_out) return fail(CHEB_ERR_INVALID, "cheb_plan_export_csr: NULL argument");
+    if (p->op != OP_SELL) return fail(CHEB_ERR_UNSUPPORTED, "export needs a SELL (Holstein) plan");
+    const int64_t n = p->n_sites;
+    std::vector<uint8_t> rl(n);
+    std::vector<double> diag(n);
+    std::vector<int32_t> clen(p->sell_nchunks);
+    std::vector<int64_t> coff(p->sell_nchunks + 1);
+    CHEB_CUDA(cudaStreamSynchronize(p->stream));
+    CHEB_CUDA(cudaMemcpy(rl.data(), p->d_hol_rowlen, n, cudaMemcpyDeviceToHost));
+    CHEB_CUDA(cudaMemcpy(diag.data(), p->d_hol_diag_raw, n * sizeof(double), cudaMemcpyDeviceToHost));
+    CHEB_CUDA(cudaMemcpy(clen.data(), p->d_sell_chunk_len, clen.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CHEB_CUDA(cudaMemcpy(coff.data(), p->d_sell_chunk_off, coff.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    int64_t nnz = n;
+    for (int64_t i = 0; i < n; ++i) nnz += rl[i];
+    *nnz_out = nnz;
+    if (!rowptr || !col || !val) return CHEB_OK;
+    std::vector<int32_t> scol(std::max<int64_t>(p->sell_nnz_stored, 1));
+    std::vector<double> sval(std::max<int64_t>(p->sell_nnz_stored, 1));
+    CHEB_CUDA(cudaMemcpy(scol.data(), p->d_sell_col, p->sell_nnz_stored * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CHEB_CUDA(cudaMemcpy(sval.data(), p->d_sell_val_raw, p->sell_nnz_stored * sizeof(double), cudaMemcpyDeviceToHost));
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        rowptr[i] = k;
+        col[k] = i;
+        val[k] = diag[i];
+        ++k;
+        const int64_t off = coff[i >> 5] + (i & 31);
+        for (int e = 0; e < rl[i]; ++e) {
+            col[k] = scol[off + (int64_t)e * 32];
+            val[k] = sval[off + (int64_t)e * 32];
+            ++k;
+        }
+    }
+    rowptr[n] = k;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_set_timing(cheb_plan* plan, int enable)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    if (!enable) {
+        int rc = collect_timing(p);
+        if (rc) return rc;
+    }
+    p->timing = enable != 0;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_kernel_stats(cheb_plan* plan, double* ms, int64_t* launches,
+                                      double* bytes, int reset)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    int rc = collect_timing(p);
+    if (rc) return rc;
+    if (ms) *ms = p->t_ms;
+    if (launches) *launches = p->t_launches;
+    if (bytes) *bytes = p->t_bytes;
+    if (reset) {
+        p->t_ms = 0.0;
+        p->t_bytes = 0.0;
+        p->t_launches = 0;
+    }
+    return CHEB_OK;
+}

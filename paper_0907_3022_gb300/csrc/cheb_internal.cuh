@@ -1,0 +1,191 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cheb.h"
+
+namespace cheb {
+
+// ---- status plumbing -------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define CHEB_CUDA(call)                                        \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return ::cheb::cuda_fail(e_, #call); \
+    } while (0)
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// ---- complex types ---------------------------------------------------------------------
+template <typename R> struct CT;
+template <> struct CT<double> { using type = double2; };
+template <> struct CT<float> { using type = float2; };
+
+// ---- operator geometry -------------------------------------------------------------------
+enum OpKind : int { OP_STENCIL = 0, OP_SELL = 1 };
+
+// One independent Hamiltonian block: a ribbon (W x L brick wall), the 1D grid (W = 1), or
+// the whole Holstein matrix.  Device copy of the per-block scalars used by the kernels.
+struct DevBlock {
+    int64_t offset;   // first site of the block in the vector
+    int32_t W, L;     // brick-wall rows/columns (1D grid: W = 1, L = n)
+    int32_t M;        // truncation order for the current dt (>= 2)
+    int32_t coef_off; // index of q_0 of this block in the coefficient table
+    int32_t ksplit;   // orders k > ksplit accumulate into the tail vector (complex64 only)
+    int32_t pad0;
+    double beta;      // scaled off-diagonal 2 * h_offdiag / a (stencil kinds)
+    double a, b;      // rescaling of Sec. 2.2
+    double ph_re, ph_im; // e^{-i b dt}
+};
+
+// A tile of consecutive sites inside one block (work items never straddle blocks).
+struct WorkItem {
+    int32_t block;
+    int32_t pad;
+    int64_t first;  // first site, relative to the block
+    int64_t count;  // sites in the tile
+};
+
+// Recurrence launch arguments (one launch = one order j, producing T_{j+1}).
+enum RecMode : int { REC_FIRST = 0, REC_SECOND = 1, REC_GENERAL = 2 };
+
+struct RecArgs {
+    const WorkItem* items;
+    int32_t nitems;
+    int32_t nvec;
+    const DevBlock* blocks;
+    const void* diag;       // d_i = 2 (H_ii - b)/a in R; [site] or [site][vec]
+    int32_t diag_per_vec;
+    int32_t mode;
+    int32_t j;              // this launch forms T_{j+1}
+    const void* cur;        // T_j  (FIRST: psi)
+    void* prev;             // T_{j-1} in, T_{j+1} out (FIRST: receives T_0)
+    void* out1;             // FIRST only: receives T_1
+    void* psi;              // accumulator (SECOND: written; GENERAL: read-modify-write)
+    void* tail;             // accumulator of the small high orders (complex64 plans)
+    const void* qcoef;      // R table: q_k = sign_k (2 - delta_k0) J_k(a dt), per block
+    // SELL data (OP_SELL)
+    const int32_t* sell_col;
+    const void* sell_val;   // R, already multiplied by 2/a
+    const int64_t* sell_chunk_off;
+    const int32_t* sell_chunk_len;
+    // reductions (FIRST): per work item [nvec][2] partial (norm2, <x|2H~x>/2)
+    double* partials;
+    unsigned int* done_counter;
+    double* red_out;        // [nblocks][nvec][2]: norm2, <psi|H|psi>
+    int32_t nblocks;
+    const int32_t* block_item_begin; // [nblocks + 1]: items of block q are [begin_q, begin_{q+1})
+    // growth check (last order of a block): |T_M,i|^2 <= 4 ||psi||^2 + tiny
+    const double* norm2;    // [nblocks][nvec], from the FIRST launch of this step
+    int* errflag;
+};
+
+struct Plan;
+
+// kernel launchers (cheb_kernels.cu)
+int launch_recurrence(Plan* p, const RecArgs& a, int op, int prec, cudaStream_t s);
+int launch_observable(Plan* p, const void* psi, int kind, double param, double* out,
+                      cudaStream_t s);
+int launch_scale_diag(Plan* p, const double* onsite, cudaStream_t s);
+
+// Holstein (cheb_holstein.cu)
+int holstein_build(Plan* p);
+
+// host Bessel (cheb_coeffs.cpp)
+int bessel_j_seq(double z, int kmax, std::vector<double>& J);
+
+// ---- the plan ----------------------------------------------------------------------------
+struct Plan {
+    cheb_ham_desc desc{};
+    int prec = CHEB_C128;
+    int nvec = 1;
+    int op = OP_STENCIL;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    double alpha = 0.0;
+    double tol = 1e-14;
+    int max_order = 100000;
+    double dt = 0.0;
+    bool have_dt = false;
+
+    int64_t n_sites = 0;
+    int nblocks = 1;
+    std::vector<double> emin, emax;
+    std::vector<DevBlock> hblocks;
+    std::vector<WorkItem> hitems;
+    std::vector<int32_t> hblock_item_begin;
+    int max_M = 0;
+
+    // device data
+    DevBlock* d_blocks = nullptr;
+    WorkItem* d_items = nullptr;
+    int32_t* d_block_item_begin = nullptr;
+    void* d_diag = nullptr;     // R [site] or [site][vec]
+    void* d_A = nullptr;        // recurrence vectors
+    void* d_B = nullptr;
+    void* d_tail = nullptr;     // second accumulator (complex64 plans)
+    void* d_qcoef = nullptr;    // R
+    size_t qcoef_cap = 0;
+    double* d_partials = nullptr;
+    unsigned int* d_counter = nullptr;
+    double* d_red = nullptr;    // [nblocks][nvec][2]
+    int* d_err = nullptr;
+    double* d_obs_scratch = nullptr; // observable partials
+    size_t obs_scratch_cap = 0;
+
+    // SELL (Holstein)
+    int64_t sell_nnz_stored = 0;
+    int64_t sell_nchunks = 0;
+    int32_t* d_sell_col = nullptr;
+    void* d_sell_val = nullptr;
+    int64_t* d_sell_chunk_off = nullptr;
+    int32_t* d_sell_chunk_len = nullptr;
+    double* d_hol_diag_raw = nullptr; // unscaled H_ii (double)
+    double* d_sell_val_raw = nullptr; // unscaled off-diagonals (double), same layout
+    int64_t hol_dph = 0;
+    int64_t* d_binom = nullptr;       // binomial table for on-device ranking
+    uint8_t* d_hol_rowlen = nullptr;  // true off-diagonal count per row (export, energy)
+
+    // launch shape
+    int threads = 256;
+    int spt = 1;         // sites per thread
+    int grid_cap = 0;    // 0: one CTA per work item
+    int64_t tile = 256;
+    bool tuned = false;
+
+    // graph of one step (rebuilt when the psi pointer, dt or the launch shape change)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    const void* graph_psi = nullptr;
+    double graph_dt = 0.0;
+    int graph_kernels = 0;
+    int64_t graph_epoch = -1;
+    int64_t shape_epoch = 0;  // bumped whenever items / launch shape / coefficients change
+
+    int64_t launches = 0;
+
+    // kernel timing (cheb_plan_set_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;               // events used since the last collection (pairs)
+    std::vector<double> ev_bytes;     // algorithmic bytes of each timed launch
+    double t_ms = 0.0, t_bytes = 0.0;
+    int64_t t_launches = 0;
+
+    size_t real_size() const { return prec == CHEB_C128 ? sizeof(double) : sizeof(float); }
+    size_t cplx_size() const { return 2 * real_size(); }
+    size_t vec_bytes() const { return (size_t)n_sites * (size_t)nvec * cplx_size(); }
+};
+
+int plan_build_items(Plan* p);
+
+}  // namespace cheb

@@ -1,0 +1,568 @@
+// Fused Chebyshev recurrence kernel (Sec. 2.2, Eqs. U_1 and rec) and FP64 reductions.
+//
+// One launch forms T_{j+1} for every block whose order M reaches j+1:
+//   FIRST   (j = 0):  T_1 = H~ psi                    -> A = psi, B = T_1
+//                     and per (block, vec) ||psi||^2, <psi|H~ psi>   (deterministic FP64)
+//   SECOND  (j = 1):  T_2 = 2 H~ T_1 - T_0            -> A = T_2,
+//                     psi = q_0 T_0 + q_1' T_1 + q_2 T_2          (psi written, not read)
+//   GENERAL (j >= 2): T_{j+1} = 2 H~ T_j - T_{j-1}     -> over T_{j-1},
+//                     psi += q'_{j+1} T_{j+1};  at j+1 = M: psi *= e^{-i b dt}
+// complex64 plans send the orders with |q_k| < 2^-8 (k > ksplit) to a second accumulator
+// "tail" and add it to psi at the last order: added straight into psi, terms smaller than
+// half an ulp of psi would be rounded away every time, which truncates the series early
+// and makes the norm decay linearly in time (~1e-8 per step at M = 20).
+// where q_k = sign (2 - delta_k0) J_k(a dt) is real and the factor (-i)^k is applied by the
+// parity of k (even k: +/- real, odd k: +/- imaginary), so the accumulation costs two FMAs
+// per complex value.  2 H~ x at a site is d_i x_i + beta * (sum of neighbour values) with
+// d_i = 2 (H_ii - b)/a stored per site and beta = 2 h_offdiag / a per block (stencils), or
+// d_i x_i + sum_j v_ij x_j with v_ij = 2 H_ij / a stored in SELL-C order (Holstein).
+//
+// Memory per site and order (GENERAL, one vector): read T_j (+ neighbours, from cache),
+// T_{j-1}, d_i, psi; write T_{j+1}, psi.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "cheb_internal.cuh"
+
+namespace cheb {
+
+// ---- small complex helpers ---------------------------------------------------------------
+template <typename R> struct V2;
+template <> struct V2<double> {
+    using C = double2;
+    static __device__ __forceinline__ C make(double x, double y) { return make_double2(x, y); }
+};
+template <> struct V2<float> {
+    using C = float2;
+    static __device__ __forceinline__ C make(float x, float y) { return make_float2(x, y); }
+};
+
+// Load / store VPT consecutive complex values with the widest aligned accesses.
+template <typename R, int VPT> struct VecIO {
+    using C = typename V2<R>::C;
+    static __device__ __forceinline__ void load(const C* __restrict__ p, C (&o)[VPT]) {
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) o[v] = p[v];
+    }
+    static __device__ __forceinline__ void store(C* __restrict__ p, const C (&o)[VPT]) {
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) p[v] = o[v];
+    }
+};
+template <> struct VecIO<float, 2> {
+    static __device__ __forceinline__ void load(const float2* __restrict__ p, float2 (&o)[2]) {
+        float4 t = *reinterpret_cast<const float4*>(p);
+        o[0] = make_float2(t.x, t.y);
+        o[1] = make_float2(t.z, t.w);
+    }
+    static __device__ __forceinline__ void store(float2* __restrict__ p, const float2 (&o)[2]) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+    }
+};
+template <> struct VecIO<float, 4> {
+    static __device__ __forceinline__ void load(const float2* __restrict__ p, float2 (&o)[4]) {
+        float4 t0 = reinterpret_cast<const float4*>(p)[0];
+        float4 t1 = reinterpret_cast<const float4*>(p)[1];
+        o[0] = make_float2(t0.x, t0.y);
+        o[1] = make_float2(t0.z, t0.w);
+        o[2] = make_float2(t1.x, t1.y);
+        o[3] = make_float2(t1.z, t1.w);
+    }
+    static __device__ __forceinline__ void store(float2* __restrict__ p, const float2 (&o)[4]) {
+        reinterpret_cast<float4*>(p)[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+        reinterpret_cast<float4*>(p)[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+    }
+};
+
+// ---- deterministic block reduction of NSUM values per thread, grouped by vector group -------
+// Threads with the same (threadIdx.x % nvg) hold partials of the same vector group (nvg is a
+// power of two <= 32).  Thread t < nvg * NSUM writes the block total of value t % NSUM of
+// group t / NSUM to gout[t].  The tree order is fixed, so results are bitwise reproducible.
+template <int NSUM>
+__device__ __forceinline__ void block_reduce_groups(double (&val)[NSUM], int nvg, double* smem,
+                                                    double* gout)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int s = 0; s < NSUM; ++s) {
+        double x = val[s];
+        for (int off = 16; off >= nvg; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        val[s] = x;
+    }
+    if (lane < nvg) {
+#pragma unroll
+        for (int s = 0; s < NSUM; ++s) smem[(warp * nvg + lane) * NSUM + s] = val[s];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nvg * NSUM) {
+        const int g = threadIdx.x / NSUM, s = threadIdx.x % NSUM;
+        double acc = 0.0;
+        for (int w = 0; w < nwarps; ++w) acc += smem[(w * nvg + g) * NSUM + s];
+        gout[threadIdx.x] = acc;
+    }
+    __syncthreads();
+}
+
+// ---- the fused recurrence: shared per-site update ----------------------------------------
+// complex64 plans carry the per-block constants (q_k, beta, e^{-i b dt}) as unevaluated sums
+// hi + lo of two floats: rounding each to one float would make every step's propagator
+// non-unitary by ~1e-7 in the same direction, and the norm would drift linearly in time.
+template <typename R> struct Split { static constexpr bool on = false; };
+template <> struct Split<float> { static constexpr bool on = true; };
+
+template <typename R>
+__device__ __forceinline__ void split_const(double v, R& hi, R& lo)
+{
+    hi = (R)v;
+    lo = Split<R>::on ? (R)(v - (double)hi) : (R)0;
+}
+
+template <typename R>
+struct SiteUpdate {
+    using C = typename V2<R>::C;
+    static constexpr bool SP = Split<R>::on;
+
+    // acc += (-i)^k q T  with the sign of (-i)^k folded into q = qh + ql
+    static __device__ __forceinline__ void accum(C& acc, const C q, const C t, const int k) {
+        if ((k & 1) == 0) {
+            if (SP) {
+                acc.x = fma(q.y, t.x, acc.x);
+                acc.y = fma(q.y, t.y, acc.y);
+            }
+            acc.x = fma(q.x, t.x, acc.x);
+            acc.y = fma(q.x, t.y, acc.y);
+        } else {  // -i q t = (q t.y, -q t.x)
+            if (SP) {
+                acc.x = fma(q.y, t.y, acc.x);
+                acc.y = fma(-q.y, t.x, acc.y);
+            }
+            acc.x = fma(q.x, t.y, acc.x);
+            acc.y = fma(-q.x, t.x, acc.y);
+        }
+    }
+    // acc * (ph + pl), ph and pl complex with e^{-i b dt} = ph + pl
+    static __device__ __forceinline__ C phase(const C acc, const C ph, const C pl) {
+        R rx = 0, ry = 0;
+        if (SP) {
+            rx = fma(pl.x, acc.x, -pl.y * acc.y);
+            ry = fma(pl.x, acc.y, pl.y * acc.x);
+        }
+        rx = fma(ph.x, acc.x, fma(-ph.y, acc.y, rx));
+        ry = fma(ph.x, acc.y, fma(ph.y, acc.x, ry));
+        return V2<R>::make(rx, ry);
+    }
+};
+
+// Finalize FIRST-mode reductions: the last CTA to finish sums the per-item partials of each
+// block in item order and writes (||psi||^2, <psi|H|psi>) per (block, vec).
+__device__ void finalize_first(const RecArgs& a)
+{
+    __shared__ unsigned int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(a.done_counter, 1u);
+        s_last = (t == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int nv = a.nvec;
+    for (int slot = threadIdx.x; slot < a.nblocks * nv; slot += blockDim.x) {
+        const int q = slot / nv, v = slot % nv;
+        double n2 = 0.0, eh = 0.0;
+        for (int it = a.block_item_begin[q]; it < a.block_item_begin[q + 1]; ++it) {
+            n2 += __ldcg(a.partials + ((size_t)it * nv + v) * 2 + 0);
+            eh += __ldcg(a.partials + ((size_t)it * nv + v) * 2 + 1);
+        }
+        const DevBlock B = a.blocks[q];
+        a.red_out[(size_t)slot * 2 + 0] = n2;
+        a.red_out[(size_t)slot * 2 + 1] = B.a * eh + B.b * n2;  // <H> = a <H~> + b ||psi||^2
+    }
+    if (threadIdx.x == 0) *a.done_counter = 0u;  // ready for the next FIRST launch
+}
+
+// ---- operators: off-diagonal part of 2 H~ x at one (site, vector group) --------------------
+// Stencil: beta * (sum of the brick-wall neighbours); 1D grid = one ribbon with W = 1.
+template <typename R, int VPT>
+struct StencilOp {
+    using C = typename V2<R>::C;
+    using IO = VecIO<R, VPT>;
+    R bh, bl;
+    int32_t W, L;
+    __device__ __forceinline__ void init(const RecArgs&, const DevBlock& B) {
+        split_const<R>(B.beta, bh, bl);
+        W = B.W;
+        L = B.L;
+    }
+    // adds beta * s to acc (acc holds -T_{j-1} or 0)
+    __device__ __forceinline__ void offdiag(const RecArgs&, const C* __restrict__ cur, int64_t sl,
+                                            int64_t, int64_t base, int, int nv,
+                                            C (&acc)[VPT]) const {
+        const int r = (int)(sl / L);
+        const int c = (int)(sl - (int64_t)r * L);
+        const int vr = ((r + c) & 1) ? r - 1 : r + 1;
+        const bool hl = c > 0, hr = c + 1 < L, hv = (vr >= 0) && (vr < W);
+        C nl[VPT], nr[VPT], nvv[VPT];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) nl[v] = nr[v] = nvv[v] = V2<R>::make(0, 0);
+        if (hl) IO::load(cur + base - nv, nl);
+        if (hr) IO::load(cur + base + nv, nr);
+        if (hv) IO::load(cur + base + (int64_t)(vr - r) * L * nv, nvv);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const R sx = nl[v].x + nr[v].x + nvv[v].x;
+            const R sy = nl[v].y + nr[v].y + nvv[v].y;
+            if (Split<R>::on) {
+                acc[v].x = fma(bl, sx, acc[v].x);
+                acc[v].y = fma(bl, sy, acc[v].y);
+            }
+            acc[v].x = fma(bh, sx, acc[v].x);
+            acc[v].y = fma(bh, sy, acc[v].y);
+        }
+    }
+};
+
+// SELL-C (C = 32): entries v_ij = 2 H_ij / a stored column-major per chunk of 32 rows.
+template <typename R, int VPT>
+struct SellOp {
+    using C = typename V2<R>::C;
+    using IO = VecIO<R, VPT>;
+    __device__ __forceinline__ void init(const RecArgs&, const DevBlock&) {}
+    __device__ __forceinline__ void offdiag(const RecArgs& a, const C* __restrict__ cur, int64_t,
+                                            int64_t row, int64_t, int g, int nv,
+                                            C (&acc)[VPT]) const {
+        const R* __restrict__ sval = static_cast<const R*>(a.sell_val);
+        const int64_t chunk = row >> 5;
+        const int64_t off = a.sell_chunk_off[chunk] + (row & 31);
+        const int len = a.sell_chunk_len[chunk];
+        for (int e = 0; e < len; ++e) {
+            const int col = a.sell_col[off + (int64_t)e * 32];
+            const R val = sval[off + (int64_t)e * 32];
+            C y[VPT];
+            IO::load(cur + (int64_t)col * nv + (int64_t)g * VPT, y);
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                acc[v].x = fma(val, y[v].x, acc[v].x);
+                acc[v].y = fma(val, y[v].y, acc[v].y);
+            }
+        }
+    }
+};
+
+// ---- the fused recurrence kernel -------------------------------------------------------------
+template <typename R, int VPT, template <typename, int> class Op>
+__global__ void __launch_bounds__(512) k_rec(RecArgs a)
+{
+    using C = typename V2<R>::C;
+    using U = SiteUpdate<R>;
+    using IO = VecIO<R, VPT>;
+    __shared__ double s_red[16 * 32 * 2];  // [warps][nvg][2 VPT]
+    const int nv = a.nvec;
+    const int nvg = nv / VPT;
+    const C* __restrict__ cur = static_cast<const C*>(a.cur);
+    C* __restrict__ prev = static_cast<C*>(a.prev);
+    C* __restrict__ out1 = static_cast<C*>(a.out1);
+    C* __restrict__ psi = static_cast<C*>(a.psi);
+    C* __restrict__ tail = static_cast<C*>(a.tail);
+    const R* __restrict__ diag = static_cast<const R*>(a.diag);
+    const C* __restrict__ qc = static_cast<const C*>(a.qcoef);  // (hi, lo) per k
+    const int k = a.j + 1;  // order formed by this launch
+    const bool first = (a.mode == REC_FIRST);
+
+    for (int w = blockIdx.x; w < a.nitems; w += gridDim.x) {
+        const WorkItem it = a.items[w];
+        const DevBlock B = a.blocks[it.block];
+        double part[2 * VPT];
+#pragma unroll
+        for (int s = 0; s < 2 * VPT; ++s) part[s] = 0.0;
+        if (k <= B.M) {
+            Op<R, VPT> op;
+            op.init(a, B);
+            const int64_t units = it.count * nvg;  // (site, vector group) pairs in the tile
+            const C qk = qc[B.coef_off + k];
+            C q0 = V2<R>::make(0, 0), q1 = V2<R>::make(0, 0);
+            if (a.mode == REC_SECOND) {
+                q0 = qc[B.coef_off + 0];
+                q1 = qc[B.coef_off + 1];
+            }
+            const bool last = (k == B.M);
+            C ph, pl;
+            split_const<R>(B.ph_re, ph.x, pl.x);
+            split_const<R>(B.ph_im, ph.y, pl.y);
+            for (int64_t u = threadIdx.x; u < units; u += blockDim.x) {
+                const int64_t sl = it.first + u / nvg;  // site (row) within the block
+                const int g = (int)(u % nvg);
+                const int64_t gs = B.offset + sl;
+                const int64_t base = gs * nv + (int64_t)g * VPT;
+                C x[VPT], p[VPT];
+                IO::load(cur + base, x);
+                if (first) {
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) p[v] = V2<R>::make(0, 0);
+                } else {
+                    IO::load(prev + base, p);
+                }
+                // h = 2 H~ x - p  (FIRST: p = 0)
+                C h[VPT];
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) h[v] = V2<R>::make(-p[v].x, -p[v].y);
+                op.offdiag(a, cur, sl, gs, base, g, nv, h);
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const R d = a.diag_per_vec ? diag[base + v] : diag[gs];
+                    h[v].x = fma(d, x[v].x, h[v].x);
+                    h[v].y = fma(d, x[v].y, h[v].y);
+                }
+                if (first) {
+                    C t1[VPT];
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) {
+                        t1[v] = V2<R>::make((R)0.5 * h[v].x, (R)0.5 * h[v].y);
+                        part[2 * v + 0] += (double)x[v].x * (double)x[v].x + (double)x[v].y * (double)x[v].y;
+                        part[2 * v + 1] += (double)x[v].x * (double)t1[v].x + (double)x[v].y * (double)t1[v].y;
+                    }
+                    IO::store(prev + base, x);
+                    IO::store(out1 + base, t1);
+                } else {
+                    C acc[VPT];
+                    IO::store(prev + base, h);  // T_{j+1} over T_{j-1}
+                    const bool to_tail = k > B.ksplit;
+                    if (a.mode == REC_SECOND) {  // k = 2 <= ksplit
+#pragma unroll
+                        for (int v = 0; v < VPT; ++v) {
+                            acc[v] = V2<R>::make(0, 0);
+                            U::accum(acc[v], q0, p[v], 0);  // T_0
+                            U::accum(acc[v], q1, x[v], 1);  // T_1
+                            U::accum(acc[v], qk, h[v], 2);  // T_2
+                        }
+                    } else {
+                        if (!to_tail) {
+                            IO::load(psi + base, acc);
+                        } else if (k == B.ksplit + 1) {
+#pragma unroll
+                            for (int v = 0; v < VPT; ++v) acc[v] = V2<R>::make(0, 0);
+                        } else {
+                            IO::load(tail + base, acc);
+                        }
+#pragma unroll
+                        for (int v = 0; v < VPT; ++v) U::accum(acc[v], qk, h[v], k);
+                    }
+                    if (last) {
+                        if (to_tail) {  // psi + (tail + q_M T_M)
+                            C ps[VPT];
+                            IO::load(psi + base, ps);
+#pragma unroll
+                            for (int v = 0; v < VPT; ++v)
+                                acc[v] = V2<R>::make(ps[v].x + acc[v].x, ps[v].y + acc[v].y);
+                        }
+#pragma unroll
+                        for (int v = 0; v < VPT; ++v) {
+                            acc[v] = U::phase(acc[v], ph, pl);
+                            const double t2 = (double)h[v].x * h[v].x + (double)h[v].y * h[v].y;
+                            const double lim = 4.0 * a.norm2[((size_t)it.block * nv + g * VPT + v) * 2];
+                            if (!(t2 <= lim)) atomicOr(a.errflag, 1);
+                        }
+                        IO::store(psi + base, acc);
+                    } else {
+                        IO::store((to_tail ? tail : psi) + base, acc);
+                    }
+                }
+            }
+        }
+        if (first) {
+            // partials[w][vec][2] = (||x||^2, <x|H~x>) of this tile; (g, v, comp) -> g*2VPT + 2v + comp
+            block_reduce_groups<2 * VPT>(part, nvg, s_red, a.partials + (size_t)w * nv * 2);
+        }
+    }
+    if (first) finalize_first(a);
+}
+
+// ---- dispatch ---------------------------------------------------------------------------
+template <typename R, int VPT>
+static void launch_t(const RecArgs& a, int op, int grid, int threads, cudaStream_t s)
+{
+    if (op == OP_STENCIL)
+        k_rec<R, VPT, StencilOp><<<grid, threads, 0, s>>>(a);
+    else
+        k_rec<R, VPT, SellOp><<<grid, threads, 0, s>>>(a);
+}
+
+int vpt_for(int prec, int nvec)
+{
+    // widest group that keeps 16-byte accesses: c128 one value (16 B); c64 up to 4 (32 B)
+    if (prec == CHEB_C128) return 1;
+    if (nvec % 4 == 0) return 4;
+    if (nvec % 2 == 0) return 2;
+    return 1;
+}
+
+int launch_recurrence(Plan* p, const RecArgs& a, int op, int prec, cudaStream_t s)
+{
+    const int vpt = vpt_for(prec, p->nvec);
+    int grid = a.nitems;
+    if (p->grid_cap > 0 && grid > p->grid_cap) grid = p->grid_cap;
+    if (grid < 1) return CHEB_OK;
+    const int th = p->threads;
+    if (prec == CHEB_C128) {
+        launch_t<double, 1>(a, op, grid, th, s);
+    } else {
+        if (vpt == 4) launch_t<float, 4>(a, op, grid, th, s);
+        else if (vpt == 2) launch_t<float, 2>(a, op, grid, th, s);
+        else launch_t<float, 1>(a, op, grid, th, s);
+    }
+    p->launches++;
+    CHEB_CUDA(cudaGetLastError());
+    return CHEB_OK;
+}
+
+// ---- diagonal scaling: d_i = 2 (H_ii - b)/a -------------------------------------------------
+template <typename R>
+__global__ void k_scale_diag(const WorkItem* items, int nitems, const DevBlock* blocks,
+                             const double* onsite, int per_vec, int nvec, double diag_shift,
+                             R* d)
+{
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const WorkItem it = items[w];
+        const DevBlock B = blocks[it.block];
+        const int per = per_vec ? nvec : 1;
+        const int64_t n = it.count * per;
+        for (int64_t u = threadIdx.x; u < n; u += blockDim.x) {
+            const int64_t idx = (B.offset + it.first) * per + u;
+            const double hii = diag_shift + (onsite ? onsite[idx] : 0.0);
+            d[idx] = (R)(2.0 * (hii - B.b) / B.a);
+        }
+    }
+}
+
+int launch_scale_diag(Plan* p, const double* onsite, cudaStream_t s)
+{
+    // 1D grid: H_ii = 1/dx^2 + V_i; ribbons: H_ii = eps_i
+    const double shift = (p->desc.kind == CHEB_LAT1D) ? 1.0 / (p->desc.dx * p->desc.dx) : 0.0;
+    const int grid = (int)std::min<int64_t>((int64_t)p->hitems.size(), 65535);
+    if (p->prec == CHEB_C128)
+        k_scale_diag<double><<<grid, 256, 0, s>>>(p->d_items, (int)p->hitems.size(), p->d_blocks,
+                                                  onsite, p->desc.onsite_per_vec, p->nvec, shift,
+                                                  static_cast<double*>(p->d_diag));
+    else
+        k_scale_diag<float><<<grid, 256, 0, s>>>(p->d_items, (int)p->hitems.size(), p->d_blocks,
+                                                 onsite, p->desc.onsite_per_vec, p->nvec, shift,
+                                                 static_cast<float*>(p->d_diag));
+    p->launches++;
+    CHEB_CUDA(cudaGetLastError());
+    return CHEB_OK;
+}
+
+// ---- observables for the stencil kinds ------------------------------------------------------
+// Per work item partials [nvec] of  norm2 | energy (<x|H x>) | probability of columns > param;
+// then one CTA per (block) sums item partials in order.
+template <typename R>
+__global__ void k_obs_stencil(const WorkItem* items, int nitems, const DevBlock* blocks,
+                              const void* psi_, const void* diag_, int diag_per_vec, int nvec,
+                              int kind, double param, double* partials)
+{
+    using C = typename V2<R>::C;
+    const C* psi = static_cast<const C*>(psi_);
+    const R* diag = static_cast<const R*>(diag_);
+    __shared__ double s_red[32];
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const WorkItem it = items[w];
+        const DevBlock B = blocks[it.block];
+        for (int v = 0; v < nvec; ++v) {
+            double acc = 0.0;
+            for (int64_t u = threadIdx.x; u < it.count; u += blockDim.x) {
+                const int64_t sl = it.first + u;
+                const int r = (int)(sl / B.L);
+                const int c = (int)(sl - (int64_t)r * B.L);
+                const int64_t gs = B.offset + sl;
+                const C x = psi[gs * nvec + v];
+                const double n2 = (double)x.x * x.x + (double)x.y * x.y;
+                if (kind == CHEB_OBS_NORM2) {
+                    acc += n2;
+                } else if (kind == CHEB_OBS_PROB_COLS) {
+                    if ((double)c > param) acc += n2;
+                } else {  // energy: <x| 2H~ x>/2 * a + b |x|^2, with 2H~x from the stencil
+                    const int vr = ((r + c) & 1) ? r - 1 : r + 1;
+                    double sx = 0.0, sy = 0.0;
+                    if (c > 0) { C y = psi[(gs - 1) * nvec + v]; sx += y.x; sy += y.y; }
+                    if (c + 1 < B.L) { C y = psi[(gs + 1) * nvec + v]; sx += y.x; sy += y.y; }
+                    if (vr >= 0 && vr < B.W) {
+                        C y = psi[(gs + (int64_t)(vr - r) * B.L) * nvec + v];
+                        sx += y.x;
+                        sy += y.y;
+                    }
+                    const double d = (double)(diag_per_vec ? diag[gs * nvec + v] : diag[gs]);
+                    const double hx = d * x.x + B.beta * sx, hy = d * x.y + B.beta * sy;
+                    acc += 0.5 * B.a * ((double)x.x * hx + (double)x.y * hy) + B.b * n2;
+                }
+            }
+            // block reduce (fixed order)
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = 0.0;
+                for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s_red[q];
+                partials[(size_t)w * nvec + v] = t;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void k_obs_finalize(const double* partials, const int32_t* block_item_begin,
+                               int nblocks, int nvec, double* out)
+{
+    for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < nblocks * nvec;
+         slot += gridDim.x * blockDim.x) {
+        const int q = slot / nvec, v = slot % nvec;
+        double t = 0.0;
+        for (int it = block_item_begin[q]; it < block_item_begin[q + 1]; ++it)
+            t += partials[(size_t)it * nvec + v];
+        out[slot] = t;
+    }
+}
+
+int launch_holstein_observable(Plan* p, const void* psi, int kind, double* out, cudaStream_t s);
+int launch_holstein_energy(Plan* p, const void* psi, double* out, cudaStream_t s);
+
+int launch_observable(Plan* p, const void* psi, int kind, double param, double* out,
+                      cudaStream_t s)
+{
+    if (kind >= CHEB_OBS_HOL_DENSITY) {
+        if (p->desc.kind != CHEB_HOLSTEIN)
+            return fail(CHEB_ERR_UNSUPPORTED, "Holstein observable on a lattice plan");
+        return launch_holstein_observable(p, psi, kind, out, s);
+    }
+    if (p->op == OP_SELL) {
+        if (kind == CHEB_OBS_PROB_COLS)
+            return fail(CHEB_ERR_UNSUPPORTED, "column probability needs a lattice plan");
+        if (kind == CHEB_OBS_ENERGY) return launch_holstein_energy(p, psi, out, s);
+    }
+    const int nitems = (int)p->hitems.size();
+    const size_t need = (size_t)nitems * p->nvec;
+    if (p->obs_scratch_cap < need) {
+        if (p->d_obs_scratch) cudaFree(p->d_obs_scratch);
+        p->d_obs_scratch = nullptr;
+        p->obs_scratch_cap = 0;
+        CHEB_CUDA(cudaMalloc(&p->d_obs_scratch, need * sizeof(double)));
+        p->obs_scratch_cap = need;
+    }
+    const int grid = std::min(nitems, 65535);
+    if (p->prec == CHEB_C128)
+        k_obs_stencil<double><<<grid, 256, 0, s>>>(p->d_items, nitems, p->d_blocks, psi, p->d_diag,
+                                                   p->desc.onsite_per_vec, p->nvec, kind, param,
+                                                   p->d_obs_scratch);
+    else
+        k_obs_stencil<float><<<grid, 256, 0, s>>>(p->d_items, nitems, p->d_blocks, psi, p->d_diag,
+                                                  p->desc.onsite_per_vec, p->nvec, kind, param,
+                                                  p->d_obs_scratch);
+    k_obs_finalize<<<1, 256, 0, s>>>(p->d_obs_scratch, p->d_block_item_begin, p->nblocks, p->nvec,
+                                     out);
+    p->launches += 2;
+    CHEB_CUDA(cudaGetLastError());
+    return CHEB_OK;
+}
+
+}  // namespace cheb

@@ -168,6 +168,7 @@ class RibbonEnsemble:
     dt: float = 1.0
     nsteps: int = 200
     hop: float = 1.0
+    stream0: int = 0        # ribbon r draws its disorder from stream stream0 + r
     sizes: list = field(default_factory=list)
 
     def __post_init__(self):
@@ -189,7 +190,7 @@ class RibbonEnsemble:
     def ribbon(self, r: int) -> Ribbon:
         W, L = self.sizes[r]
         return Ribbon(W=W, L=L, hop=self.hop, disorder=self.disorder(r), seed=self.seed,
-                      stream=r, sigma=self.sigma, dt=self.dt, nsteps=self.nsteps)
+                      stream=self.stream0 + r, sigma=self.sigma, dt=self.dt, nsteps=self.nsteps)
 
     def offsets(self) -> np.ndarray:
         n = np.array([W * L for W, L in self.sizes], dtype=np.int64)
