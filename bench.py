@@ -389,7 +389,7 @@ def run_ours(args, world, rank, local):
             "workload": WORKLOAD, "n_ribbons": ens.n_ribbons, "sites": int(sum(sites)),
             "packets_per_ribbon": ens.nvec, "dt": ens.dt, "M_per_ribbon": sorted(set(Ms)),
             "l2": f"inputs larger than L2 (working set {wss:.2f} GB of vectors)",
-            "launch_shape": dict(zip(("threads", "sites_per_thread", "grid"),
+            "launch_shape": dict(zip(("threads", "sites_per_thread", "grid", "vecs_per_thread"),
                                      plan.launch_shape())),
             "parallelism": f"replicas x{world} (one ensemble per GPU)",
         },

@@ -203,12 +203,15 @@ int cheb_holstein_rank(int L, int nph, const uint8_t* occ, int e, int64_t* idx);
 int cheb_holstein_unrank(int L, int nph, int64_t idx, uint8_t* occ, int* e);
 
 /* ---- tuning --------------------------------------------------------------------------- */
-/* Times the plan's recurrence kernel over a few launch shapes (threads per block, sites
-   per thread) on the plan's own workspace and keeps the fastest; results are cached per
-   plan.  Optional: plans start from a fixed default. */
+/* Times the plan's recurrence kernel over launch shapes (threads per block, sites per
+   thread, vectors per thread, grid size) on the plan's own workspace and keeps the fastest;
+   the choice is kept in the plan.  Needs a time step set (CHEB_ERR_STATE otherwise).
+   Optional: plans start from a fixed default. */
 int cheb_autotune(cheb_plan* plan);
-/* Launch shape chosen for the plan: threads per block, sites per thread, grid size. */
-int cheb_plan_launch(const cheb_plan* plan, int* threads, int* sites_per_thread, int* grid);
+/* Launch shape chosen for the plan: threads per block, sites per thread, grid size, and
+   vectors handled per thread (of the nvec at each site). */
+int cheb_plan_launch(const cheb_plan* plan, int* threads, int* sites_per_thread, int* grid,
+                     int* vecs_per_thread);
 
 /* ---- introspection for tests ---------------------------------------------------------- */
 /* Copies of the plan's device data to host memory, for checking the construction:

@@ -88,7 +88,7 @@ _SIGS = {
     "cheb_holstein_rank": ([_c.c_int, _c.c_int, _u8p, _c.c_int, _i64p], _c.c_int),
     "cheb_holstein_unrank": ([_c.c_int, _c.c_int, _c.c_int64, _u8p, _ip], _c.c_int),
     "cheb_autotune": ([_vp], _c.c_int),
-    "cheb_plan_launch": ([_vp, _ip, _ip, _ip], _c.c_int),
+    "cheb_plan_launch": ([_vp, _ip, _ip, _ip, _ip], _c.c_int),
     "cheb_plan_export_csr": ([_vp, _i64p, _i64p, _dp, _i64p], _c.c_int),
     "cheb_plan_launches": ([_vp], _c.c_int64),
     "cheb_plan_set_timing": ([_vp, _c.c_int], _c.c_int),
@@ -268,10 +268,11 @@ class Plan:
         check(lib().cheb_autotune(self.handle), "cheb_autotune")
 
     def launch_shape(self):
-        t, s, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        """(threads per block, sites per thread, grid, vectors per thread)."""
+        t, s, g, v = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(lib().cheb_plan_launch(self.handle, ctypes.byref(t), ctypes.byref(s),
-                                     ctypes.byref(g)), "cheb_plan_launch")
-        return t.value, s.value, g.value
+                                     ctypes.byref(g), ctypes.byref(v)), "cheb_plan_launch")
+        return t.value, s.value, g.value, v.value
 
     def launches(self) -> int:
         return int(lib().cheb_plan_launches(self.handle))

@@ -27,13 +27,11 @@ int cuda_fail(cudaError_t e, const char* what)
     return CHEB_ERR_CUDA;
 }
 
-int vpt_for(int prec, int nvec);
-
 // Split every block into tiles of `tile` sites; Holstein tiles also never straddle two
 // electron sites (blocks of Dph rows), so per-tile observables have a single slot.
 int plan_build_items(Plan* p)
 {
-    const int nvg = p->nvec / vpt_for(p->prec, p->nvec);
+    const int nvg = p->nvec / vpt_for(p->prec, p->nvec, p->vpt);
     int64_t tile = (int64_t)p->threads * p->spt / nvg;
     if (tile < 1) tile = 1;
     p->tile = tile;
@@ -599,12 +597,14 @@ extern "C" int cheb_observables(cheb_plan* plan, const void* psi, int kind, doub
     return launch_observable(p, psi, kind, param, out, p->stream);
 }
 
-extern "C" int cheb_plan_launch(const cheb_plan* plan, int* threads, int* spt, int* grid)
+extern "C" int cheb_plan_launch(const cheb_plan* plan, int* threads, int* spt, int* grid,
+                                int* vpt)
 {
     const Plan* p = reinterpret_cast<const Plan*>(plan);
     if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
     if (threads) *threads = p->threads;
     if (spt) *spt = p->spt;
+    if (vpt) *vpt = vpt_for(p->prec, p->nvec, p->vpt);
     if (grid) *grid = p->grid_cap > 0 ? std::min<int>(p->grid_cap, (int)p->hitems.size())
                                       : (int)p->hitems.size();
     return CHEB_OK;
@@ -635,42 +635,50 @@ extern "C" int cheb_autotune(cheb_plan* plan)
     const int th_c[] = {128, 256, 512};
     const int spt_c[] = {1, 2, 4};
     const int cap_c[] = {0, 4, 8, 16};
+    std::vector<int> vpt_c;
+    for (int v : {1, 2, 4})
+        if (vpt_for(p->prec, p->nvec, v) == v) vpt_c.push_back(v);
     float best = 1e30f;
-    int bt = p->threads, bs = p->spt, bc = p->grid_cap;
+    int bt = p->threads, bs = p->spt, bc = p->grid_cap, bv = p->vpt;
     int rc = CHEB_OK;
     const int64_t launches0 = p->launches;
-    for (int th : th_c) {
-        for (int spt : spt_c) {
-            p->threads = th;
-            p->spt = spt;
-            rc = plan_build_items(p);
-            if (rc) break;
-            for (int capm : cap_c) {
-                p->grid_cap = capm ? capm * p->num_sms : 0;
-                RecArgs a = base_args(p);
-                a.mode = REC_GENERAL;
-                a.j = 2;
-                a.cur = p->d_A;
-                a.prev = p->d_B;
-                a.psi = scratch;
-                float tot = 0.0f;
-                for (int rep = 0; rep < 4; ++rep) {
-                    cudaEventRecord(e0, p->stream);
-                    rc = launch_recurrence(p, a, p->op, p->prec, p->stream);
-                    cudaEventRecord(e1, p->stream);
+    for (int vpt : vpt_c) {
+        for (int th : th_c) {
+            for (int spt : spt_c) {
+                p->vpt = vpt;
+                p->threads = th;
+                p->spt = spt;
+                rc = plan_build_items(p);
+                if (rc) break;
+                for (int capm : cap_c) {
+                    p->grid_cap = capm ? capm * p->num_sms : 0;
+                    RecArgs a = base_args(p);
+                    a.mode = REC_GENERAL;
+                    a.j = 2;
+                    a.cur = p->d_A;
+                    a.prev = p->d_B;
+                    a.psi = scratch;
+                    float tot = 0.0f;
+                    for (int rep = 0; rep < 4; ++rep) {
+                        cudaEventRecord(e0, p->stream);
+                        rc = launch_recurrence(p, a, p->op, p->prec, p->stream);
+                        cudaEventRecord(e1, p->stream);
+                        if (rc) break;
+                        cudaEventSynchronize(e1);
+                        float ms = 0.0f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (rep > 0) tot += ms;  // first launch is warm-up
+                    }
                     if (rc) break;
-                    cudaEventSynchronize(e1);
-                    float ms = 0.0f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep > 0) tot += ms;  // first launch is warm-up
+                    if (tot < best) {
+                        best = tot;
+                        bt = th;
+                        bs = spt;
+                        bc = p->grid_cap;
+                        bv = vpt;
+                    }
                 }
                 if (rc) break;
-                if (tot < best) {
-                    best = tot;
-                    bt = th;
-                    bs = spt;
-                    bc = p->grid_cap;
-                }
             }
             if (rc) break;
         }
@@ -683,6 +691,7 @@ extern "C" int cheb_autotune(cheb_plan* plan)
     p->threads = bt;
     p->spt = bs;
     p->grid_cap = bc;
+    p->vpt = bv;
     int rc2 = plan_build_items(p);
     if (rc) return rc;
     if (rc2) return rc2;

@@ -159,6 +159,7 @@ struct Plan {
     int threads = 256;
     int spt = 1;         // sites per thread
     int grid_cap = 0;    // 0: one CTA per work item
+    int vpt = 0;         // vectors per thread (0: default for the precision)
     int64_t tile = 256;
     bool tuned = false;
 
@@ -187,5 +188,6 @@ struct Plan {
 };
 
 int plan_build_items(Plan* p);
+int vpt_for(int prec, int nvec, int want);
 
 }  // namespace cheb

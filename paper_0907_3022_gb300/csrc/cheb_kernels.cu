@@ -291,12 +291,20 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
             C ph, pl;
             split_const<R>(B.ph_re, ph.x, pl.x);
             split_const<R>(B.ph_im, ph.y, pl.y);
+            const bool to_tail = k > B.ksplit;
+            const bool gen = (a.mode == REC_GENERAL);
+            // accumulator read by this launch: psi (k <= ksplit), tail (k > ksplit + 1), none
+            const bool read_psi = gen && !to_tail;
+            const bool read_tail = gen && to_tail && (k > B.ksplit + 1);
+            const bool read_psi_last = last && to_tail;  // last order: psi + tail
             for (int64_t u = threadIdx.x; u < units; u += blockDim.x) {
                 const int64_t sl = it.first + u / nvg;  // site (row) within the block
                 const int g = (int)(u % nvg);
                 const int64_t gs = B.offset + sl;
                 const int64_t base = gs * nv + (int64_t)g * VPT;
-                C x[VPT], p[VPT];
+                // every load of this site first, then arithmetic and stores
+                C x[VPT], p[VPT], acc[VPT], ps[VPT];
+                R d[VPT];
                 IO::load(cur + base, x);
                 if (first) {
 #pragma unroll
@@ -304,6 +312,17 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
                 } else {
                     IO::load(prev + base, p);
                 }
+                if (read_psi) {
+                    IO::load(psi + base, acc);
+                } else if (read_tail) {
+                    IO::load(tail + base, acc);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) acc[v] = V2<R>::make(0, 0);
+                }
+                if (read_psi_last) IO::load(psi + base, ps);
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) d[v] = a.diag_per_vec ? diag[base + v] : diag[gs];
                 // h = 2 H~ x - p  (FIRST: p = 0)
                 C h[VPT];
 #pragma unroll
@@ -311,9 +330,8 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
                 op.offdiag(a, cur, sl, gs, base, g, nv, h);
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
-                    const R d = a.diag_per_vec ? diag[base + v] : diag[gs];
-                    h[v].x = fma(d, x[v].x, h[v].x);
-                    h[v].y = fma(d, x[v].y, h[v].y);
+                    h[v].x = fma(d[v], x[v].x, h[v].x);
+                    h[v].y = fma(d[v], x[v].y, h[v].y);
                 }
                 if (first) {
                     C t1[VPT];
@@ -326,33 +344,20 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
                     IO::store(prev + base, x);
                     IO::store(out1 + base, t1);
                 } else {
-                    C acc[VPT];
                     IO::store(prev + base, h);  // T_{j+1} over T_{j-1}
-                    const bool to_tail = k > B.ksplit;
                     if (a.mode == REC_SECOND) {  // k = 2 <= ksplit
 #pragma unroll
                         for (int v = 0; v < VPT; ++v) {
-                            acc[v] = V2<R>::make(0, 0);
                             U::accum(acc[v], q0, p[v], 0);  // T_0
                             U::accum(acc[v], q1, x[v], 1);  // T_1
                             U::accum(acc[v], qk, h[v], 2);  // T_2
                         }
                     } else {
-                        if (!to_tail) {
-                            IO::load(psi + base, acc);
-                        } else if (k == B.ksplit + 1) {
-#pragma unroll
-                            for (int v = 0; v < VPT; ++v) acc[v] = V2<R>::make(0, 0);
-                        } else {
-                            IO::load(tail + base, acc);
-                        }
 #pragma unroll
                         for (int v = 0; v < VPT; ++v) U::accum(acc[v], qk, h[v], k);
                     }
                     if (last) {
-                        if (to_tail) {  // psi + (tail + q_M T_M)
-                            C ps[VPT];
-                            IO::load(psi + base, ps);
+                        if (read_psi_last) {  // psi + (tail + q_M T_M)
 #pragma unroll
                             for (int v = 0; v < VPT; ++v)
                                 acc[v] = V2<R>::make(ps[v].x + acc[v].x, ps[v].y + acc[v].y);
@@ -389,9 +394,12 @@ static void launch_t(const RecArgs& a, int op, int grid, int threads, cudaStream
         k_rec<R, VPT, SellOp><<<grid, threads, 0, s>>>(a);
 }
 
-int vpt_for(int prec, int nvec)
+// vectors per thread: the plan's tuned value when it divides nvec, else the widest group
+// that keeps 16-byte accesses (complex128: 1 value; complex64: up to 4 values)
+int vpt_for(int prec, int nvec, int want)
 {
-    // widest group that keeps 16-byte accesses: c128 one value (16 B); c64 up to 4 (32 B)
+    if (want > 0 && nvec % want == 0 && (want == 1 || want == 2 || (want == 4 && prec == CHEB_C64)))
+        return want;
     if (prec == CHEB_C128) return 1;
     if (nvec % 4 == 0) return 4;
     if (nvec % 2 == 0) return 2;
@@ -400,13 +408,14 @@ int vpt_for(int prec, int nvec)
 
 int launch_recurrence(Plan* p, const RecArgs& a, int op, int prec, cudaStream_t s)
 {
-    const int vpt = vpt_for(prec, p->nvec);
+    const int vpt = vpt_for(prec, p->nvec, p->vpt);
     int grid = a.nitems;
     if (p->grid_cap > 0 && grid > p->grid_cap) grid = p->grid_cap;
     if (grid < 1) return CHEB_OK;
     const int th = p->threads;
     if (prec == CHEB_C128) {
-        launch_t<double, 1>(a, op, grid, th, s);
+        if (vpt == 2) launch_t<double, 2>(a, op, grid, th, s);
+        else launch_t<double, 1>(a, op, grid, th, s);
     } else {
         if (vpt == 4) launch_t<float, 4>(a, op, grid, th, s);
         else if (vpt == 2) launch_t<float, 2>(a, op, grid, th, s);

@@ -344,8 +344,8 @@ def test_graph_replay_equals_single_steps_and_tuning_keeps_results():
     c = x0.clone()
     plan.evolve(c, 1.0, 5)
     assert bool((a == c).all())
-    t, s, g = plan.launch_shape()
-    assert t in (128, 256, 512) and s in (1, 2, 4) and g >= 1
+    t, s, g, v = plan.launch_shape()
+    assert t in (128, 256, 512) and s in (1, 2, 4) and g >= 1 and v in (1, 2, 4)
     n0 = plan.launches()
     plan.evolve(c, 1.0, 2)
     assert plan.launches() - n0 == 2 * max(plan.block(q)["M"] for q in range(6))
