@@ -176,6 +176,25 @@ typedef enum {
 /* Deterministic FP64 reductions of psi (device, plan layout) into out (device doubles). */
 int cheb_observables(cheb_plan* plan, const void* psi, int kind, double param, double* out);
 
+/* ---- plan-free region norm that allocates no device memory -------------------------- */
+/* The paper has no counterpart: this serves callers that may not allocate device memory
+   where they need a norm -- code running while a stream is captured in global mode (no
+   cudaMalloc allowed), latency-critical loops that cannot take the device-wide
+   synchronisation of cudaMalloc/cudaFree, and host programs whose own pool owns all device
+   memory.  For one zigzag ribbon (or the 1D grid, L = n) held as psi (device, [site][vec],
+   complex128 or complex64 by prec, n_sites = W * L), out[v] (device, nvec doubles) =
+   sum over sites with column (site % L) > col_min of |psi_v|^2; col_min = -1 gives ||psi_v||^2.
+   Same per-tile FP64 reduction as cheb_observables; its tile partials live in a static
+   device array of CHEB_NOALLOC_MAX_PARTIALS doubles (512 KiB, held by every GPU that loads
+   the library until exit), so ceil(n_sites / 1024) * nvec must not exceed that
+   (CHEB_ERR_INVALID otherwise).  The array's device address is looked up on the first call
+   made on each device, so make that first call before any stream capture.  Calls share the
+   array: calls whose kernels may overlap on the GPU race.  Enqueued on stream (NULL =
+   legacy default stream); no allocation of any kind. */
+#define CHEB_NOALLOC_MAX_PARTIALS 65536
+int cheb_region_norm_noalloc(const void* psi, int prec, int64_t n_sites, int32_t L, int nvec,
+                             int64_t col_min, double* out, void* stream);
+
 /* ---- gradient with respect to the on-site potential ---------------------------------- */
 /* No counterpart in the paper: reverse-mode differentiation of Eqs. (U_1) and (rec) with
    a, b held fixed (dH~/dV_i = e_i e_i^T / a).  psi_n = U(dt)^nsteps psi0 is recomputed from

@@ -93,6 +93,8 @@ _SIGS = {
     "cheb_plan_launches": ([_vp], _c.c_int64),
     "cheb_plan_set_timing": ([_vp, _c.c_int], _c.c_int),
     "cheb_plan_kernel_stats": ([_vp, _dp, _i64p, _dp, _c.c_int], _c.c_int),
+    "cheb_region_norm_noalloc": ([_vp, _c.c_int, _c.c_int64, _c.c_int32, _c.c_int, _c.c_int64, _vp,
+                                  _vp], _c.c_int),
 }
 
 
@@ -300,6 +302,13 @@ class Plan:
                                          col.ctypes.data_as(_i64p), val.ctypes.data_as(_dp),
                                          ctypes.byref(nnz)), "cheb_plan_export_csr")
         return rp, col, val
+
+
+def cheb_region_norm_noalloc(psi, prec: int, n_sites: int, L: int, nvec: int, col_min: int, out,
+                             stream=None):
+    """Plan-free region norm into out (device doubles [nvec]); allocates nothing."""
+    check(lib().cheb_region_norm_noalloc(_ptr(psi), prec, n_sites, L, nvec, col_min, _ptr(out),
+                                         _stream_handle(stream)), "cheb_region_norm_noalloc")
 
 
 # ---- descriptor helpers ----------------------------------------------------------------------
