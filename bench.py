@@ -53,6 +53,9 @@ def parse():
                     help="skip the oracle timing (profiling runs)")
     ap.add_argument("--lean", action="store_true",
                     help="timed region only: no e2e, FP64 or accuracy legs (profiling runs)")
+    ap.add_argument("--blocking", default=None,
+                    help="S:SPT -- force S orders per launch with SPT sites per thread and skip "
+                         "the autotuner (profiling runs); 0:0 forces single-order launches")
     return ap.parse_args()
 
 
@@ -249,7 +252,11 @@ def run_ours(args, world, rank, local):
     plan, psi = make_plan(cb, ens, cb.CHEB_C64, ens.nvec, packets)
     psi0 = psi.clone()
     plan.evolve(psi, ens.dt, 0)  # coefficients for dt
-    plan.autotune()
+    if args.blocking is None:
+        plan.autotune()
+    else:
+        bs, bspt = (int(x) for x in args.blocking.split(":"))
+        plan.set_blocking(bs, bspt if bs else 4)
     Ms = [plan.block(q)["M"] for q in range(ens.n_ribbons)]
     sites = [w * l for w, l in ens.sizes]
     mv_per_step = ens.nvec * sum(Ms)
@@ -288,7 +295,10 @@ def run_ours(args, world, rank, local):
     achieved = kbytes / (kms / 1e3) / 1e9  # GB/s
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "k_rec<float,4,StencilOp> (all launches of the step)",
+                "kernel": ("k_rec_tb<4,%d> (all launches of the step)" % plan.blocking()[1]
+                           if plan.blocking()[0] else
+                           "k_rec<float,%d,StencilOp> (all launches of the step)"
+                           % plan.launch_shape()[3]),
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "launches": kcount, "kernel_ms_total": kms,
                 "alg_bytes_per_launch": kbytes / max(kcount, 1)}
@@ -346,7 +356,8 @@ def run_ours(args, world, rank, local):
         # the plain FP64 single-vector path on the same ensemble (packet k0 = pi/3)
         plan64, psi64 = make_plan(cb, ens, cb.CHEB_C128, 1, packets[:, 2:3].copy())
         plan64.evolve(psi64, ens.dt, 0)
-        plan64.autotune()
+        if args.blocking is None:
+            plan64.autotune()
         plan64.evolve(psi64, ens.dt, 2)
         k64 = max(5, args.steps // 5)
         plan64.set_timing(True)
@@ -391,6 +402,8 @@ def run_ours(args, world, rank, local):
             "l2": f"inputs larger than L2 (working set {wss:.2f} GB of vectors)",
             "launch_shape": dict(zip(("threads", "sites_per_thread", "grid", "vecs_per_thread"),
                                      plan.launch_shape())),
+            "temporal_blocking": dict(zip(("orders_per_launch", "sites_per_thread"),
+                                          plan.blocking())),
             "parallelism": f"replicas x{world} (one ensemble per GPU)",
         },
         "site_vector_steps_per_s": site_steps,

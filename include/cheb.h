@@ -227,10 +227,19 @@ int cheb_holstein_unrank(int L, int nph, int64_t idx, uint8_t* occ, int* e);
    the choice is kept in the plan.  Needs a time step set (CHEB_ERR_STATE otherwise).
    Optional: plans start from a fixed default. */
 int cheb_autotune(cheb_plan* plan);
+/* Temporal blocking (complex64 lattice plans with nvec 1, 2 or 4 and a shared on-site
+   array): orders_per_launch s > 0 makes each launch run s recurrence orders out of shared
+   memory on 2-D tiles of each ribbon with an s-site halo (sites_per_thread 4, 6 or 8 sets the
+   tile budget, 256 threads x sites_per_thread region sites); s = 0 returns to one order per
+   launch.  CHEB_ERR_UNSUPPORTED for other plans.  cheb_autotune also chooses these. */
+int cheb_plan_set_blocking(cheb_plan* plan, int orders_per_launch, int sites_per_thread);
+
 /* Launch shape chosen for the plan: threads per block, sites per thread, grid size, and
    vectors handled per thread (of the nvec at each site). */
 int cheb_plan_launch(const cheb_plan* plan, int* threads, int* sites_per_thread, int* grid,
                      int* vecs_per_thread);
+/* Orders per launch and sites per thread of the temporal blocking in use (0, 0: off). */
+int cheb_plan_blocking(const cheb_plan* plan, int* orders_per_launch, int* sites_per_thread);
 
 /* ---- introspection for tests ---------------------------------------------------------- */
 /* Copies of the plan's device data to host memory, for checking the construction:

@@ -80,6 +80,8 @@ static int upload_blocks(Plan* p)
     return CHEB_OK;
 }
 
+static int tb_prepare(Plan* p);
+
 // Coefficients for a new dt: q_k = sign_k (2 - delta_k0) J_k(a dt) with sign_k = +1 for
 // k mod 4 in {0, 1} and -1 for {2, 3}, so that (-i)^k (2 - delta_k0) J_k = q_k (1 or -i).
 static int set_dt(Plan* p, double dt)
@@ -141,7 +143,7 @@ static int set_dt(Plan* p, double dt)
     p->dt = dt;
     p->have_dt = true;
     p->shape_epoch++;
-    return CHEB_OK;
+    return tb_prepare(p);
 }
 
 static RecArgs base_args(Plan* p)
@@ -232,9 +234,112 @@ static int collect_timing(Plan* p)
     return CHEB_OK;
 }
 
+// ---- temporal blocking ---------------------------------------------------------------------
+static bool tb_eligible(const Plan* p)
+{
+    return p->op == OP_STENCIL && p->prec == CHEB_C64 && !p->desc.onsite_per_vec &&
+           (p->nvec == 1 || p->nvec == 2 || p->nvec == 4);
+}
+
+static int tb_set_for(Plan* p, int s)
+{
+    for (size_t i = 0; i < p->tb_sets.size(); ++i)
+        if (p->tb_sets[i].s == s) return (int)i;
+    std::vector<TBTile> tiles;
+    std::vector<int32_t> begin;
+    if (!tb_build_tiles(p, s, tiles, begin)) return -1;
+    TBSet set;
+    set.s = s;
+    set.ntiles = (int)tiles.size();
+    if (cudaMalloc(&set.d_tiles, tiles.size() * sizeof(TBTile)) != cudaSuccess) return -2;
+    if (cudaMalloc(&set.d_begin, begin.size() * sizeof(int32_t)) != cudaSuccess) {
+        cudaFree(set.d_tiles);
+        return -2;
+    }
+    cudaMemcpy(set.d_tiles, tiles.data(), tiles.size() * sizeof(TBTile), cudaMemcpyHostToDevice);
+    cudaMemcpy(set.d_begin, begin.data(), begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    p->tb_sets.push_back(set);
+    return (int)p->tb_sets.size() - 1;
+}
+
+// Launch schedule of one step with temporal blocking: orders 1..s0 (s0 < min M, so the first
+// launch, which reads psi as T_0, never writes psi), then blocks of tb_s orders up to max M.
+// Builds the tile sets and buffers it needs (outside any stream capture).  On failure the
+// plan falls back to single-order launches (tb_s = 0).
+static int tb_prepare(Plan* p)
+{
+    p->tb_sched.clear();
+    if (p->tb_s <= 0 || !tb_eligible(p) || !p->have_dt) return CHEB_OK;
+    int minM = 1 << 30, maxM = 0;
+    for (const DevBlock& B : p->hblocks) {
+        minM = std::min(minM, (int)B.M);
+        maxM = std::max(maxM, (int)B.M);
+    }
+    int rc0 = tb_configure(p->nvec, p->tb_spt);
+    if (rc0) {
+        p->tb_s = 0;
+        return rc0;
+    }
+    const int s0 = std::max(1, std::min(p->tb_s, minM - 1));
+    std::vector<Plan::TBLaunch> sched;
+    int ka = 1, kb = s0, prev = 0;
+    while (ka <= maxM) {
+        const int set = tb_set_for(p, kb - ka + 1);
+        if (set < 0) {
+            p->tb_s = 0;
+            return set == -2 ? fail(CHEB_ERR_NOMEM, "temporal blocking tiles") : CHEB_OK;
+        }
+        sched.push_back({ka, kb, prev, set});
+        prev = ka;
+        ka = kb + 1;
+        kb = std::min(ka + p->tb_s - 1, maxM);
+    }
+    const size_t vb = p->vec_bytes();
+    for (void** b : {&p->d_C, &p->d_D, &p->d_E}) {
+        if (!*b && cudaMalloc(b, vb) != cudaSuccess) return fail(CHEB_ERR_NOMEM, "temporal blocking buffers");
+    }
+    const size_t need = (size_t)p->tb_sets[sched[0].set].ntiles * p->nvec * 2;
+    if (p->tb_partials_cap < need) {
+        if (p->d_tb_partials) cudaFree(p->d_tb_partials);
+        p->d_tb_partials = nullptr;
+        p->tb_partials_cap = 0;
+        if (cudaMalloc(&p->d_tb_partials, need * sizeof(double)) != cudaSuccess)
+            return fail(CHEB_ERR_NOMEM, "temporal blocking partials");
+        p->tb_partials_cap = need;
+    }
+    p->tb_sched = sched;
+    p->shape_epoch++;
+    return CHEB_OK;
+}
+
+// algorithmic bytes of one blocked launch: region inputs counted once per interior site
+static double tb_launch_bytes(const Plan* p, const Plan::TBLaunch& L)
+{
+    const double cs = (double)p->cplx_size() * p->nvec;
+    const double ds = (double)p->real_size();
+    double total = 0.0;
+    for (const DevBlock& B : p->hblocks) {
+        if (L.ka > B.M) continue;
+        const double sites = (double)B.W * B.L;
+        const bool first = L.ka == 1;
+        const bool done = std::min(L.kb, (int)B.M) == B.M;
+        const bool to_main = first || L.ka <= B.ksplit;
+        const bool tail_has = L.prev_ka > B.ksplit;
+        double v = (first ? 1 : 2);                  // T_{ka-1}, T_{ka-2}
+        v += done ? 0 : 2;                           // T_{ke-1}, T_{ke} out
+        if (!done) v += (to_main ? (first ? 0 : 1) : (tail_has ? 1 : 0)) + 1;  // acc in/out
+        else v += (to_main ? 1 : (tail_has ? 2 : 1)) + 1;                    // E (+tail), psi
+        total += sites * (v * cs + ds);
+    }
+    return total;
+}
+
+static int enqueue_step_tb(Plan* p, void* psi, cudaStream_t st);
+
 // Enqueue the M_max fused kernels of one step on stream s.
 static int enqueue_step(Plan* p, void* psi, cudaStream_t s)
 {
+    if (!p->tb_sched.empty()) return enqueue_step_tb(p, psi, s);
     RecArgs a = base_args(p);
     if (p->timing && p->ev_used > 4096) {  // keep the event pool bounded
         int rc = collect_timing(p);
@@ -257,6 +362,62 @@ static int enqueue_step(Plan* p, void* psi, cudaStream_t s)
         }
         int rc = timed_launch(p, a, s);
         if (rc) return rc;
+    }
+    return CHEB_OK;
+}
+
+static int enqueue_step_tb(Plan* p, void* psi, cudaStream_t st)
+{
+    void* pairs[2][2] = {{p->d_A, p->d_B}, {p->d_C, p->d_D}};
+    for (size_t i = 0; i < p->tb_sched.size(); ++i) {
+        const Plan::TBLaunch& L = p->tb_sched[i];
+        const TBSet& set = p->tb_sets[L.set];
+        TBArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.tiles = set.d_tiles;
+        a.ntiles = set.ntiles;
+        a.ka = L.ka;
+        a.kb = L.kb;
+        a.prev_ka = L.prev_ka;
+        a.blocks = p->d_blocks;
+        a.diag = p->d_diag;
+        if (i == 0) {
+            a.in_prev = nullptr;
+            a.in_cur = psi;
+        } else {
+            a.in_prev = pairs[(i - 1) & 1][0];
+            a.in_cur = pairs[(i - 1) & 1][1];
+        }
+        a.out_prev = pairs[i & 1][0];
+        a.out_cur = pairs[i & 1][1];
+        a.acc_main = p->d_E;
+        a.tail = p->d_tail;
+        a.psi = psi;
+        a.qcoef = p->d_qcoef;
+        a.partials = p->d_tb_partials;
+        a.done_counter = p->d_counter;
+        a.red_out = p->d_red;
+        a.nblocks = p->nblocks;
+        a.block_tile_begin = set.d_begin;
+        a.norm2 = p->d_red;
+        a.errflag = p->d_err;
+        if (p->timing) {
+            if (p->ev_used + 2 > p->ev_pool.size()) {
+                for (int e = 0; e < 64; ++e) {
+                    cudaEvent_t ev;
+                    CHEB_CUDA(cudaEventCreate(&ev));
+                    p->ev_pool.push_back(ev);
+                }
+            }
+            CHEB_CUDA(cudaEventRecord(p->ev_pool[p->ev_used], st));
+        }
+        int rc = tb_launch(p, a, st);
+        if (rc) return rc;
+        if (p->timing) {
+            CHEB_CUDA(cudaEventRecord(p->ev_pool[p->ev_used + 1], st));
+            p->ev_used += 2;
+            p->ev_bytes.push_back(tb_launch_bytes(p, L));
+        }
     }
     return CHEB_OK;
 }
@@ -301,6 +462,12 @@ static void free_plan(Plan* p)
     if (!p) return;
     if (p->graph) cudaGraphExecDestroy(p->graph);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    for (TBSet& t : p->tb_sets) {
+        if (t.d_tiles) cudaFree(t.d_tiles);
+        if (t.d_begin) cudaFree(t.d_begin);
+    }
+    for (void* q : {p->d_C, p->d_D, p->d_E, (void*)p->d_tb_partials})
+        if (q) cudaFree(q);
     void* ptrs[] = {p->d_blocks, p->d_items, p->d_block_item_begin, p->d_diag, p->d_A, p->d_B,
                     p->d_tail,
                     p->d_qcoef, p->d_partials, p->d_counter, p->d_red, p->d_err,
@@ -684,17 +851,81 @@ extern "C" int cheb_autotune(cheb_plan* plan)
         }
         if (rc) break;
     }
-    p->launches = launches0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(scratch);
     p->threads = bt;
     p->spt = bs;
     p->grid_cap = bc;
     p->vpt = bv;
     int rc2 = plan_build_items(p);
+    if (rc) {
+        cudaFree(scratch);
+        return rc;
+    }
+    if (rc2) {
+        cudaFree(scratch);
+        return rc2;
+    }
+    // whole steps: single-order launches against temporal blocking (complex64 stencils)
+    if (tb_eligible(p)) {
+        auto time_steps = [&](float* out_ms) -> int {
+            cudaEvent_t t0, t1;
+            cudaEventCreate(&t0);
+            cudaEventCreate(&t1);
+            int r = enqueue_step(p, scratch, p->stream);  // warm-up
+            cudaEventRecord(t0, p->stream);
+            for (int rep = 0; rep < 2 && !r; ++rep) r = enqueue_step(p, scratch, p->stream);
+            cudaEventRecord(t1, p->stream);
+            cudaEventSynchronize(t1);
+            cudaEventElapsedTime(out_ms, t0, t1);
+            cudaEventDestroy(t0);
+            cudaEventDestroy(t1);
+            return r;
+        };
+        p->tb_s = 0;
+        p->tb_sched.clear();
+        float best_ms = 0.0f;
+        rc = time_steps(&best_ms);
+        int best_s = 0, best_spt = p->tb_spt;
+        const int spts[] = {4, 6, 8};
+        for (int spt : spts) {
+            if (rc) break;
+            if (spt == 8 && p->nvec == 4) continue;
+            for (int s_try : {2, 3, 4, 5, 6, 8}) {
+                p->tb_s = s_try;
+                p->tb_spt = spt;
+                for (TBSet& t : p->tb_sets) {  // tiles depend on the region budget (spt)
+                    cudaFree(t.d_tiles);
+                    cudaFree(t.d_begin);
+                }
+                p->tb_sets.clear();
+                rc = tb_prepare(p);
+                if (rc) break;
+                if (p->tb_sched.empty()) continue;
+                float ms = 0.0f;
+                rc = time_steps(&ms);
+                if (rc) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_s = s_try;
+                    best_spt = spt;
+                }
+            }
+        }
+        for (TBSet& t : p->tb_sets) {
+            cudaFree(t.d_tiles);
+            cudaFree(t.d_begin);
+        }
+        p->tb_sets.clear();
+        p->tb_s = best_s;
+        p->tb_spt = best_spt;
+        int rc3 = tb_prepare(p);
+        if (!rc) rc = rc3;
+        CHEB_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream));
+    }
+    p->launches = launches0;
+    cudaFree(scratch);
     if (rc) return rc;
-    if (rc2) return rc2;
     p->tuned = true;
     return CHEB_OK;
 }
@@ -767,5 +998,43 @@ extern "C" int cheb_plan_kernel_stats(cheb_plan* plan, double* ms, int64_t* laun
         p->t_bytes = 0.0;
         p->t_launches = 0;
     }
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_set_blocking(cheb_plan* plan, int s, int spt)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    if (s < 0 || s > 16) return fail(CHEB_ERR_INVALID, "orders_per_launch must be in [0, 16]");
+    if (s > 0 && !tb_eligible(p))
+        return fail(CHEB_ERR_UNSUPPORTED, "temporal blocking needs a complex64 lattice plan with "
+                                          "nvec 1, 2 or 4 and a shared on-site array");
+    if (s > 0 && spt != 4 && spt != 6 && spt != 8)
+        return fail(CHEB_ERR_INVALID, "sites_per_thread must be 4, 6 or 8");
+    if (s > 0 && spt == 8 && p->nvec == 4)
+        return fail(CHEB_ERR_INVALID, "sites_per_thread 8 needs nvec <= 2");
+    for (TBSet& t : p->tb_sets) {
+        cudaFree(t.d_tiles);
+        cudaFree(t.d_begin);
+    }
+    p->tb_sets.clear();
+    p->tb_s = s;
+    if (s > 0) p->tb_spt = spt;
+    p->tb_sched.clear();
+    p->shape_epoch++;
+    int rc = tb_prepare(p);
+    if (rc) return rc;
+    if (s > 0 && p->have_dt && p->tb_sched.empty())
+        return fail(CHEB_ERR_INVALID, "temporal blocking: a ribbon does not fit the tile budget");
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_blocking(const cheb_plan* plan, int* s, int* spt)
+{
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    const bool on = p->tb_s > 0 && tb_eligible(p);
+    if (s) *s = on ? p->tb_s : 0;
+    if (spt) *spt = on ? p->tb_spt : 0;
     return CHEB_OK;
 }

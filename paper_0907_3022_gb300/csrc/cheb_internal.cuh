@@ -88,7 +88,51 @@ struct RecArgs {
     int* errflag;
 };
 
+// Temporal blocking (cheb_tb.cu): a tile of one ribbon with its halo region.
+struct TBTile {
+    int32_t block;
+    int32_t R0, R1, C0, C1;  // region (ribbon rows/columns, half-open)
+    int32_t r0, r1, c0, c1;  // interior
+};
+
+struct TBArgs {
+    const TBTile* tiles;
+    int32_t ntiles;
+    int32_t ka, kb;          // orders formed by this launch
+    int32_t prev_ka;         // first order of the previous launch of the step (0: none)
+    const DevBlock* blocks;
+    const void* diag;        // float d_i
+    const void* in_prev;     // T_{ka-2} (unused when ka = 1)
+    const void* in_cur;      // T_{ka-1} (psi when ka = 1)
+    void* out_prev;          // T_{ke-1}
+    void* out_cur;           // T_{ke}
+    void* acc_main;          // E
+    void* tail;
+    void* psi;
+    const void* qcoef;       // float2 (hi, lo) per order
+    double* partials;        // first launch: [tile][nvec][2]
+    unsigned int* done_counter;
+    double* red_out;
+    int32_t nblocks;
+    const int32_t* block_tile_begin;
+    const double* norm2;
+    int* errflag;
+};
+
+struct TBSet {
+    int s = 0;
+    TBTile* d_tiles = nullptr;
+    int32_t* d_begin = nullptr;
+    int ntiles = 0;
+};
+
 struct Plan;
+
+// temporal blocking (cheb_tb.cu)
+size_t tb_smem_bytes(int nv, int spt);
+int tb_launch(Plan* p, const TBArgs& a, cudaStream_t s);
+int tb_configure(int nv, int spt);
+bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vector<int32_t>& begin);
 
 // kernel launchers (cheb_kernels.cu)
 int launch_recurrence(Plan* p, const RecArgs& a, int op, int prec, cudaStream_t s);
@@ -173,6 +217,21 @@ struct Plan {
     int64_t shape_epoch = 0;  // bumped whenever items / launch shape / coefficients change
 
     int64_t launches = 0;
+
+    // temporal blocking (complex64 stencils): orders per launch (0: off), sites per thread
+    int tb_s = 0;
+    int tb_spt = 4;
+    int tb_grid_cap = 0;
+    void* d_C = nullptr;      // second recurrence pair and the main accumulator
+    void* d_D = nullptr;
+    void* d_E = nullptr;
+    std::vector<TBSet> tb_sets;
+    struct TBLaunch {
+        int ka, kb, prev_ka, set;
+    };
+    std::vector<TBLaunch> tb_sched;   // launches of one step (rebuilt with dt / tb_s)
+    double* d_tb_partials = nullptr;
+    size_t tb_partials_cap = 0;
 
     // kernel timing (cheb_plan_set_timing)
     bool timing = false;

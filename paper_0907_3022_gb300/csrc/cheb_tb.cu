@@ -1,0 +1,442 @@
+// Temporally blocked Chebyshev recurrence for complex64 brick-wall stencils (Sec. 2.2,
+// Eqs. U_1 and rec; ribbons of Sec. 3.2, the 1D grid as W = 1).
+//
+// One launch forms s consecutive orders k = ka .. kb for every ribbon.  A CTA owns a tile
+// of one ribbon: the interior [r0, r1) x [c0, c1) plus a halo of s sites on every side that
+// is not a ribbon edge (the region [R0, R1) x [C0, C1)).  It loads T_{ka-2}, T_{ka-1} and
+// the on-site data d of the region into shared memory once, then runs the s recurrence
+// orders there: order i is computed on the region shrunk by i+1 on its open sides, which is
+// exactly where its inputs are still valid, and the interior is the region shrunk by s.  The
+// weighted sum of the s new orders for the interior sites stays in registers.  At the end
+// the interior's last two vectors go to the other global buffer pair (the neighbouring CTAs
+// are still reading this pair as their halo) and the partial sum goes to an accumulator:
+//   E   (main accumulator)  for launches that start at an order <= ksplit,
+//   tail                    for launches that start later (|q_k| < 2^-8, see cheb_kernels.cu),
+// and psi = e^{-i b dt} (E + tail + partial) at the launch holding the ribbon's last order M.
+// psi itself is read only by the first launch (as T_0) and written only at order M; the
+// first launch never holds order M (the host keeps s_0 < min M).
+//
+// Per site and s orders the launch moves 2 vectors + d of the region in and 2 vectors of
+// the interior out, plus the accumulator: about (2 nv 8 + 4) * halo + 3 nv 8 bytes instead
+// of s * (5 nv 8 + 4) for s single-order launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "cheb_internal.cuh"
+
+namespace cheb {
+
+static constexpr int TB_THREADS = 256;
+
+template <int NV>
+struct TBCplx {
+    float2 v[NV];
+};
+
+// split of a double into hi + lo floats
+__device__ __forceinline__ void tb_split(double x, float& hi, float& lo)
+{
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+// acc += (-i)^k q T with the sign of (-i)^k folded into q = (hi, lo)
+__device__ __forceinline__ void tb_accum(float2& acc, const float2 q, const float2 t, const int k)
+{
+    if ((k & 1) == 0) {
+        acc.x = fmaf(q.y, t.x, acc.x);
+        acc.y = fmaf(q.y, t.y, acc.y);
+        acc.x = fmaf(q.x, t.x, acc.x);
+        acc.y = fmaf(q.x, t.y, acc.y);
+    } else {
+        acc.x = fmaf(q.y, t.y, acc.x);
+        acc.y = fmaf(-q.y, t.x, acc.y);
+        acc.x = fmaf(q.x, t.y, acc.x);
+        acc.y = fmaf(-q.x, t.x, acc.y);
+    }
+}
+
+__device__ __forceinline__ float2 tb_phase(const float2 a, const float2 ph, const float2 pl)
+{
+    float rx = fmaf(pl.x, a.x, -pl.y * a.y);
+    float ry = fmaf(pl.x, a.y, pl.y * a.x);
+    rx = fmaf(ph.x, a.x, fmaf(-ph.y, a.y, rx));
+    ry = fmaf(ph.x, a.y, fmaf(ph.y, a.x, ry));
+    return make_float2(rx, ry);
+}
+
+// asynchronous global -> shared copies (no registers in between)
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int NV, int SPT>
+__global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArgs a)
+{
+    constexpr int RMAX = TB_THREADS * SPT;
+    extern __shared__ float4 tb_smem_raw[];
+    float2* const sP0 = reinterpret_cast<float2*>(tb_smem_raw);  // [NV][RMAX]
+    float2* const sQ0 = sP0 + NV * RMAX;                          // [NV][RMAX]
+    float* const sD = reinterpret_cast<float*>(sQ0 + NV * RMAX);  // [RMAX]
+    __shared__ double s_red[(TB_THREADS / 32) * 2 * NV];
+
+    const float2* __restrict__ in_prev = static_cast<const float2*>(a.in_prev);
+    const float2* __restrict__ in_cur = static_cast<const float2*>(a.in_cur);
+    float2* __restrict__ out_prev = static_cast<float2*>(a.out_prev);
+    float2* __restrict__ out_cur = static_cast<float2*>(a.out_cur);
+    float2* __restrict__ accE = static_cast<float2*>(a.acc_main);
+    float2* __restrict__ tail = static_cast<float2*>(a.tail);
+    float2* __restrict__ psi = static_cast<float2*>(a.psi);
+    const float* __restrict__ diag = static_cast<const float*>(a.diag);
+    const float2* __restrict__ qc = static_cast<const float2*>(a.qcoef);
+    const int tid = threadIdx.x;
+    const bool first = (a.ka == 1);
+
+    for (int w = blockIdx.x; w < a.ntiles; w += gridDim.x) {
+        const TBTile T = a.tiles[w];
+        const DevBlock B = a.blocks[T.block];
+        double part[2 * NV];
+#pragma unroll
+        for (int s = 0; s < 2 * NV; ++s) part[s] = 0.0;
+        if (a.ka <= B.M) {
+            const int ke = min(a.kb, B.M);
+            const int RW = T.C1 - T.C0, RH = T.R1 - T.R0;
+            const int nreg = RW * RH;
+            // region coordinates of this thread's sites, computed once per tile
+            int srr[SPT], scc[SPT];
+#pragma unroll
+            for (int j = 0; j < SPT; ++j) {
+                const int idx = tid + j * TB_THREADS;
+                srr[j] = idx / RW;
+                scc[j] = idx - srr[j] * RW;
+                if (idx >= nreg) srr[j] = 1 << 20;  // never inside a rectangle
+            }
+            // ---- load the region: asynchronous copies straight into shared memory ---------
+#pragma unroll
+            for (int j = 0; j < SPT; ++j) {
+                const int idx = tid + j * TB_THREADS;
+                if (idx < nreg) {
+                    const int64_t g = B.offset + (int64_t)(T.R0 + srr[j]) * B.L + (T.C0 + scc[j]);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        cp_async8(&sQ0[v * RMAX + idx], &in_cur[g * NV + v]);
+                        if (first) sP0[v * RMAX + idx] = make_float2(0.f, 0.f);
+                        else cp_async8(&sP0[v * RMAX + idx], &in_prev[g * NV + v]);
+                    }
+                    cp_async4(&sD[idx], &diag[g]);
+                }
+            }
+            float bh, bl;
+            tb_split(B.beta, bh, bl);
+            float2 acc[SPT][NV];
+            bool inter[SPT];
+#pragma unroll
+            for (int j = 0; j < SPT; ++j) {
+                const int r = T.R0 + srr[j], c = T.C0 + scc[j];
+                inter[j] = (r >= T.r0) && (r < T.r1) && (c >= T.c0) && (c < T.c1);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) acc[j][v] = make_float2(0.f, 0.f);
+            }
+            cp_async_wait_all();
+            __syncthreads();
+            if (first) {  // q_0 T_0
+                const float2 q0 = qc[B.coef_off + 0];
+#pragma unroll
+                for (int j = 0; j < SPT; ++j) {
+                    if (!inter[j]) continue;
+                    const int idx = tid + j * TB_THREADS;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) tb_accum(acc[j][v], q0, sQ0[v * RMAX + idx], 0);
+                }
+            }
+            // ---- s recurrence orders in shared memory -------------------------------------
+            float2* sP = sP0;
+            float2* sQ = sQ0;
+            const bool open_t = T.R0 > 0, open_b = T.R1 < B.W, open_l = T.C0 > 0, open_r = T.C1 < B.L;
+            for (int k = a.ka; k <= ke; ++k) {
+                const int sh = k - a.ka + 1;
+                const int rlo = open_t ? sh : 0, rhi = RH - (open_b ? sh : 0);
+                const int clo = open_l ? sh : 0, chi = RW - (open_r ? sh : 0);
+                const float2 qk = qc[B.coef_off + k];
+                float2* __restrict__ Pw = sP;        // T_{k-2} in, T_k out (own site only)
+                const float2* __restrict__ Qr = sQ;  // T_{k-1}, read at the site and neighbours
+#pragma unroll
+                for (int j = 0; j < SPT; ++j) {
+                    const int rr = srr[j], cc = scc[j];
+                    if (rr < rlo || rr >= rhi || cc < clo || cc >= chi) continue;
+                    const int idx = tid + j * TB_THREADS;
+                    const int r = T.R0 + rr, c = T.C0 + cc;
+                    const bool up = (r + c) & 1;  // vertical neighbour r-1 (else r+1)
+                    const bool hl = c > 0, hr = c + 1 < B.L;
+                    const bool hv = up ? (r > 0) : (r + 1 < B.W);
+                    const int vidx = up ? idx - RW : idx + RW;
+                    const float d = sD[idx];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const float2* Q = Qr + v * RMAX;
+                        const float2 x = Q[idx];
+                        const float2 yl = hl ? Q[idx - 1] : make_float2(0.f, 0.f);
+                        const float2 yr = hr ? Q[idx + 1] : make_float2(0.f, 0.f);
+                        const float2 yv = hv ? Q[vidx] : make_float2(0.f, 0.f);
+                        const float2 p = Pw[v * RMAX + idx];
+                        const float sx = (yl.x + yr.x) + yv.x;
+                        const float sy = (yl.y + yr.y) + yv.y;
+                        float hx = fmaf(bl, sx, -p.x), hy = fmaf(bl, sy, -p.y);
+                        hx = fmaf(bh, sx, hx);
+                        hy = fmaf(bh, sy, hy);
+                        hx = fmaf(d, x.x, hx);
+                        hy = fmaf(d, x.y, hy);
+                        if (k == 1) {  // T_1 = H~ T_0 (p = 0)
+                            hx *= 0.5f;
+                            hy *= 0.5f;
+                        }
+                        const float2 h = make_float2(hx, hy);
+                        Pw[v * RMAX + idx] = h;
+                        if (inter[j]) {
+                            tb_accum(acc[j][v], qk, h, k);
+                            if (k == 1) {
+                                part[2 * v + 0] += (double)x.x * x.x + (double)x.y * x.y;
+                                part[2 * v + 1] += (double)x.x * h.x + (double)x.y * h.y;
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                float2* tmp = sP;
+                sP = sQ;
+                sQ = tmp;
+            }
+            // ---- write back: sQ = T_ke, sP = T_{ke-1} --------------------------------------
+            const bool done = (ke == B.M);
+            float2 ph, pl;
+            tb_split(B.ph_re, ph.x, pl.x);
+            tb_split(B.ph_im, ph.y, pl.y);
+            const bool to_main = first || (a.ka <= B.ksplit);
+            const bool tail_has = a.prev_ka > B.ksplit;  // an earlier launch wrote the tail
+#pragma unroll
+            for (int j = 0; j < SPT; ++j) {
+                if (!inter[j]) continue;
+                const int idx = tid + j * TB_THREADS;
+                const int64_t g = B.offset + (int64_t)(T.R0 + srr[j]) * B.L + (T.C0 + scc[j]);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const float2 tk = sQ[v * RMAX + idx];
+                    float2 val = acc[j][v];
+                    if (!done) {
+                        out_cur[g * NV + v] = tk;
+                        out_prev[g * NV + v] = sP[v * RMAX + idx];
+                        if (to_main) {
+                            if (!first) {
+                                const float2 e = accE[g * NV + v];
+                                val = make_float2(e.x + val.x, e.y + val.y);
+                            }
+                            accE[g * NV + v] = val;
+                        } else {
+                            if (tail_has) {
+                                const float2 e = tail[g * NV + v];
+                                val = make_float2(e.x + val.x, e.y + val.y);
+                            }
+                            tail[g * NV + v] = val;
+                        }
+                    } else {
+                        // psi = e^{-i b dt} (E + tail + partial)
+                        if (to_main) {
+                            const float2 e = accE[g * NV + v];
+                            val = make_float2(e.x + val.x, e.y + val.y);
+                        } else {
+                            if (tail_has) {
+                                const float2 e = tail[g * NV + v];
+                                val = make_float2(e.x + val.x, e.y + val.y);
+                            }
+                            const float2 e = accE[g * NV + v];
+                            val = make_float2(e.x + val.x, e.y + val.y);
+                        }
+                        psi[g * NV + v] = tb_phase(val, ph, pl);
+                        const double t2 = (double)tk.x * tk.x + (double)tk.y * tk.y;
+                        const double lim = 4.0 * a.norm2[((size_t)T.block * NV + v) * 2];
+                        if (!(t2 <= lim)) atomicOr(a.errflag, 1);
+                    }
+                }
+            }
+        }
+        if (first) {
+            // per-tile partials of ||T_0||^2 and <T_0|H~ T_0>, fixed-order block reduction
+            const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+            for (int s = 0; s < 2 * NV; ++s) {
+                double x = part[s];
+                for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+                if (lane == 0) s_red[warp * 2 * NV + s] = x;
+            }
+            __syncthreads();
+            if (tid < 2 * NV) {
+                double t = 0.0;
+                for (int q = 0; q < TB_THREADS / 32; ++q) t += s_red[q * 2 * NV + tid];
+                a.partials[(size_t)w * NV * 2 + tid] = t;
+            }
+        }
+        __syncthreads();  // shared memory is reused by the next tile
+    }
+    if (first) {
+        __shared__ unsigned int s_last;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_last = (atomicAdd(a.done_counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            for (int slot = tid; slot < a.nblocks * NV; slot += blockDim.x) {
+                const int q = slot / NV, v = slot % NV;
+                double n2 = 0.0, eh = 0.0;
+                for (int it = a.block_tile_begin[q]; it < a.block_tile_begin[q + 1]; ++it) {
+                    n2 += __ldcg(a.partials + ((size_t)it * NV + v) * 2 + 0);
+                    eh += __ldcg(a.partials + ((size_t)it * NV + v) * 2 + 1);
+                }
+                const DevBlock Bq = a.blocks[q];
+                a.red_out[(size_t)slot * 2 + 0] = n2;
+                a.red_out[(size_t)slot * 2 + 1] = Bq.a * eh + Bq.b * n2;
+            }
+            if (tid == 0) *a.done_counter = 0u;
+        }
+    }
+}
+
+size_t tb_smem_bytes(int nv, int spt)
+{
+    const size_t rmax = (size_t)TB_THREADS * spt;
+    return 2 * (size_t)nv * rmax * sizeof(float2) + rmax * sizeof(float);
+}
+
+template <int NV, int SPT>
+static int tb_launch_t(const TBArgs& a, int grid, cudaStream_t s)
+{
+    k_rec_tb<NV, SPT><<<grid, TB_THREADS, tb_smem_bytes(NV, SPT), s>>>(a);
+    CHEB_CUDA(cudaGetLastError());
+    return CHEB_OK;
+}
+
+template <int NV, int SPT>
+static int tb_attr_t()
+{
+    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tb<NV, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)tb_smem_bytes(NV, SPT)));
+    return CHEB_OK;
+}
+
+// Allow the dynamic shared memory of the (nv, spt) instantiation; called while the schedule
+// is prepared, outside any stream capture.
+int tb_configure(int nv, int spt)
+{
+    if (spt == 4) {
+        if (nv == 4) return tb_attr_t<4, 4>();
+        if (nv == 2) return tb_attr_t<2, 4>();
+        if (nv == 1) return tb_attr_t<1, 4>();
+    } else if (spt == 6) {
+        if (nv == 4) return tb_attr_t<4, 6>();
+        if (nv == 2) return tb_attr_t<2, 6>();
+        if (nv == 1) return tb_attr_t<1, 6>();
+    } else if (spt == 8) {
+        if (nv == 2) return tb_attr_t<2, 8>();
+        if (nv == 1) return tb_attr_t<1, 8>();
+    }
+    return fail(CHEB_ERR_UNSUPPORTED, "temporal blocking: unsupported nvec / sites per thread");
+}
+
+int tb_launch(Plan* p, const TBArgs& a, cudaStream_t s)
+{
+    int grid = a.ntiles;
+    if (p->tb_grid_cap > 0 && grid > p->tb_grid_cap) grid = p->tb_grid_cap;
+    if (grid < 1) return CHEB_OK;
+    int rc = CHEB_ERR_UNSUPPORTED;
+    const int nv = p->nvec;
+    if (p->tb_spt == 4) {
+        if (nv == 4) rc = tb_launch_t<4, 4>(a, grid, s);
+        else if (nv == 2) rc = tb_launch_t<2, 4>(a, grid, s);
+        else if (nv == 1) rc = tb_launch_t<1, 4>(a, grid, s);
+    } else if (p->tb_spt == 6) {
+        if (nv == 4) rc = tb_launch_t<4, 6>(a, grid, s);
+        else if (nv == 2) rc = tb_launch_t<2, 6>(a, grid, s);
+        else if (nv == 1) rc = tb_launch_t<1, 6>(a, grid, s);
+    } else if (p->tb_spt == 8) {
+        if (nv == 2) rc = tb_launch_t<2, 8>(a, grid, s);
+        else if (nv == 1) rc = tb_launch_t<1, 8>(a, grid, s);
+    }
+    if (rc == CHEB_ERR_UNSUPPORTED) return fail(rc, "temporal blocking: unsupported nvec / sites per thread");
+    p->launches++;
+    return rc;
+}
+
+// Tiles for a halo of s: row bands of at most 48 interior rows, then as many interior columns
+// as the region budget (TB_THREADS * spt sites) allows.  Returns false if a ribbon cannot be
+// tiled (the region of one interior column would not fit).
+bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vector<int32_t>& begin)
+{
+    const int rmax = TB_THREADS * p->tb_spt;
+    tiles.clear();
+    begin.assign(p->nblocks + 1, 0);
+    for (int q = 0; q < p->nblocks; ++q) {
+        begin[q] = (int32_t)tiles.size();
+        const DevBlock& B = p->hblocks[q];
+        // row bands: pick the band count whose tiles waste the least region on halos
+        int best_nbr = -1;
+        double best_eff = 0.0;
+        for (int nbr = 1; nbr <= B.W; ++nbr) {
+            const int tr = (B.W + nbr - 1) / nbr;
+            const int rh = std::min(B.W, tr + (nbr > 1 ? 2 * s : 0));  // worst band
+            const int tcmax = rmax / rh - (B.L > rmax / rh ? 2 * s : 0);
+            if (tcmax < 1) continue;
+            const int tc = std::min(tcmax, B.L);
+            const double eff = (double)tr * tc / ((double)rh * (tc + (B.L > tc ? 2 * s : 0)));
+            if (eff > best_eff * 1.02) {
+                best_eff = eff;
+                best_nbr = nbr;
+            }
+            if (tr <= 2 * s) break;
+        }
+        if (best_nbr < 0) return false;
+        const int tr = (B.W + best_nbr - 1) / best_nbr;
+        for (int r0 = 0; r0 < B.W; r0 += tr) {
+            const int r1 = std::min(B.W, r0 + tr);
+            const int R0 = std::max(0, r0 - s), R1 = std::min(B.W, r1 + s);
+            const int rh = R1 - R0;
+            int tc = rmax / rh;
+            if (tc < B.L) tc -= 2 * s;  // halo on both column sides
+            if (tc < 1) return false;
+            const int nbc = (B.L + tc - 1) / tc;
+            tc = (B.L + nbc - 1) / nbc;
+            for (int c0 = 0; c0 < B.L; c0 += tc) {
+                const int c1 = std::min(B.L, c0 + tc);
+                TBTile t{};
+                t.block = q;
+                t.R0 = R0;
+                t.R1 = R1;
+                t.C0 = std::max(0, c0 - s);
+                t.C1 = std::min(B.L, c1 + s);
+                t.r0 = r0;
+                t.r1 = r1;
+                t.c0 = c0;
+                t.c1 = c1;
+                if ((int64_t)(t.R1 - t.R0) * (t.C1 - t.C0) > rmax) return false;
+                tiles.push_back(t);
+            }
+        }
+    }
+    begin[p->nblocks] = (int32_t)tiles.size();
+    return true;
+}
+
+}  // namespace cheb

@@ -41,9 +41,10 @@ def oracle_1d(n, nsteps=None):
 
 
 @functools.lru_cache(maxsize=None)
-def oracle_ribbon(W, L, disorder, seed, stream, k0, nsteps, sigma=20.0, r0=None, c0=None):
+def oracle_ribbon(W, L, disorder, seed, stream, k0, nsteps, sigma=20.0, r0=None, c0=None,
+                  dt=1.0):
     rb = wl.Ribbon(W=W, L=L, disorder=disorder, seed=seed, stream=stream, sigma=sigma, r0=r0,
-                   c0=c0)
+                   c0=c0, dt=dt)
     H = oracle.honeycomb(W, L, rb.hop, rb.onsite())
     a, b = oracle.rescale(*rb.bounds(), 0.0)
     C, M = oracle.coeffs(a, b, rb.dt)

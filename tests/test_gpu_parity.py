@@ -343,12 +343,22 @@ def test_graph_replay_equals_single_steps_and_tuning_keeps_results():
     plan.autotune()
     c = x0.clone()
     plan.evolve(c, 1.0, 5)
-    assert bool((a == c).all())
+    blk, _ = plan.blocking()
+    if blk == 0:  # single-order launches: the launch shape does not change any result bit
+        assert bool((a == c).all())
+    else:  # temporal blocking: same recurrence vectors, partial sums added in another order
+        assert rel(host(c), host(a)) <= 2e-6
     t, s, g, v = plan.launch_shape()
     assert t in (128, 256, 512) and s in (1, 2, 4) and g >= 1 and v in (1, 2, 4)
     n0 = plan.launches()
     plan.evolve(c, 1.0, 2)
-    assert plan.launches() - n0 == 2 * max(plan.block(q)["M"] for q in range(6))
+    Ms = [plan.block(q)["M"] for q in range(6)]
+    if blk == 0:
+        expect = max(Ms)
+    else:
+        s0 = min(blk, min(Ms) - 1)
+        expect = 1 + -(-(max(Ms) - s0) // blk)
+    assert plan.launches() - n0 == 2 * expect
 
 
 # ---------------------------------------------------------------------------------------
