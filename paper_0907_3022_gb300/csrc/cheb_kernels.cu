@@ -274,9 +274,12 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
     for (int w = blockIdx.x; w < a.nitems; w += gridDim.x) {
         const WorkItem it = a.items[w];
         const DevBlock B = a.blocks[it.block];
-        double part[2 * VPT];
+        // per-thread norm / energy terms (FIRST): in the vector precision, since a thread sums
+        // only its few sites (FP64 arithmetic is ~1/32 the FP32 rate on this GPU); the block
+        // and grid reductions that follow are FP64
+        R part[2 * VPT];
 #pragma unroll
-        for (int s = 0; s < 2 * VPT; ++s) part[s] = 0.0;
+        for (int s = 0; s < 2 * VPT; ++s) part[s] = (R)0;
         if (k <= B.M) {
             Op<R, VPT> op;
             op.init(a, B);
@@ -338,8 +341,8 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
 #pragma unroll
                     for (int v = 0; v < VPT; ++v) {
                         t1[v] = V2<R>::make((R)0.5 * h[v].x, (R)0.5 * h[v].y);
-                        part[2 * v + 0] += (double)x[v].x * (double)x[v].x + (double)x[v].y * (double)x[v].y;
-                        part[2 * v + 1] += (double)x[v].x * (double)t1[v].x + (double)x[v].y * (double)t1[v].y;
+                        part[2 * v + 0] = fma(x[v].x, x[v].x, fma(x[v].y, x[v].y, part[2 * v + 0]));
+                        part[2 * v + 1] = fma(x[v].x, t1[v].x, fma(x[v].y, t1[v].y, part[2 * v + 1]));
                     }
                     IO::store(prev + base, x);
                     IO::store(out1 + base, t1);
@@ -378,7 +381,10 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
         }
         if (first) {
             // partials[w][vec][2] = (||x||^2, <x|H~x>) of this tile; (g, v, comp) -> g*2VPT + 2v + comp
-            block_reduce_groups<2 * VPT>(part, nvg, s_red, a.partials + (size_t)w * nv * 2);
+            double dpart[2 * VPT];
+#pragma unroll
+            for (int s = 0; s < 2 * VPT; ++s) dpart[s] = (double)part[s];
+            block_reduce_groups<2 * VPT>(dpart, nvg, s_red, a.partials + (size_t)w * nv * 2);
         }
     }
     if (first) finalize_first(a);

@@ -84,7 +84,7 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <int NV, int SPT>
+template <int NV, int SPT, bool FIRST>
 __global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArgs a)
 {
     constexpr int RMAX = TB_THREADS * SPT;
@@ -104,19 +104,23 @@ __global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArg
     const float* __restrict__ diag = static_cast<const float*>(a.diag);
     const float2* __restrict__ qc = static_cast<const float2*>(a.qcoef);
     const int tid = threadIdx.x;
-    const bool first = (a.ka == 1);
+    constexpr bool first = FIRST;  // ka == 1: T_0 = psi, no T_{-1}; norm and energy partials
 
     for (int w = blockIdx.x; w < a.ntiles; w += gridDim.x) {
         const TBTile T = a.tiles[w];
         const DevBlock B = a.blocks[T.block];
-        double part[2 * NV];
+        // per-thread norm / energy terms of the first launch: a thread sums only its SPT
+        // sites, in FP32 (FP64 arithmetic is ~1/32 the FP32 rate on this GPU); the block and
+        // grid reductions that follow are FP64
+        float part[FIRST ? 2 * NV : 1];
 #pragma unroll
-        for (int s = 0; s < 2 * NV; ++s) part[s] = 0.0;
+        for (int s = 0; s < (FIRST ? 2 * NV : 1); ++s) part[s] = 0.f;
         if (a.ka <= B.M) {
             const int ke = min(a.kb, B.M);
+            const bool done = (ke == B.M);
             const int RW = T.C1 - T.C0, RH = T.R1 - T.R0;
             const int nreg = RW * RH;
-            // region coordinates of this thread's sites, computed once per tile
+            // region coordinates of this thread's positions tid + j * 256 (row-major region)
             int srr[SPT], scc[SPT];
 #pragma unroll
             for (int j = 0; j < SPT; ++j) {
@@ -140,10 +144,10 @@ __global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArg
                     cp_async4(&sD[idx], &diag[g]);
                 }
             }
-            float bh, bl;
-            tb_split(B.beta, bh, bl);
-            float2 acc[SPT][NV];
             bool inter[SPT];
+            float2 acc[SPT][NV];
+            const bool to_main = first || (a.ka <= B.ksplit);
+            const bool tail_has = a.prev_ka > B.ksplit;  // an earlier launch wrote the tail
 #pragma unroll
             for (int j = 0; j < SPT; ++j) {
                 const int r = T.R0 + srr[j], c = T.C0 + scc[j];
@@ -151,6 +155,8 @@ __global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArg
 #pragma unroll
                 for (int v = 0; v < NV; ++v) acc[j][v] = make_float2(0.f, 0.f);
             }
+            float bh, bl;
+            tb_split(B.beta, bh, bl);
             cp_async_wait_all();
             __syncthreads();
             if (first) {  // q_0 T_0
@@ -183,14 +189,15 @@ __global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArg
                     const bool up = (r + c) & 1;  // vertical neighbour r-1 (else r+1)
                     const bool hl = c > 0, hr = c + 1 < B.L;
                     const bool hv = up ? (r > 0) : (r + 1 < B.W);
+                    const int il = idx - 1, ir = idx + 1;
                     const int vidx = up ? idx - RW : idx + RW;
                     const float d = sD[idx];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         const float2* Q = Qr + v * RMAX;
                         const float2 x = Q[idx];
-                        const float2 yl = hl ? Q[idx - 1] : make_float2(0.f, 0.f);
-                        const float2 yr = hr ? Q[idx + 1] : make_float2(0.f, 0.f);
+                        const float2 yl = hl ? Q[il] : make_float2(0.f, 0.f);
+                        const float2 yr = hr ? Q[ir] : make_float2(0.f, 0.f);
                         const float2 yv = hv ? Q[vidx] : make_float2(0.f, 0.f);
                         const float2 p = Pw[v * RMAX + idx];
                         const float sx = (yl.x + yr.x) + yv.x;
@@ -208,9 +215,11 @@ __global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArg
                         Pw[v * RMAX + idx] = h;
                         if (inter[j]) {
                             tb_accum(acc[j][v], qk, h, k);
-                            if (k == 1) {
-                                part[2 * v + 0] += (double)x.x * x.x + (double)x.y * x.y;
-                                part[2 * v + 1] += (double)x.x * h.x + (double)x.y * h.y;
+                            if constexpr (FIRST) {
+                                if (k == 1) {
+                                    part[2 * v + 0] = fmaf(x.x, x.x, fmaf(x.y, x.y, part[2 * v + 0]));
+                                    part[2 * v + 1] = fmaf(x.x, h.x, fmaf(x.y, h.y, part[2 * v + 1]));
+                                }
                             }
                         }
                     }
@@ -220,13 +229,10 @@ __global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArg
                 sP = sQ;
                 sQ = tmp;
             }
-            // ---- write back: sQ = T_ke, sP = T_{ke-1} --------------------------------------
-            const bool done = (ke == B.M);
+            // ---- write back: sQ = T_ke, sP = T_{ke-1}; the accumulators are read here --------
             float2 ph, pl;
             tb_split(B.ph_re, ph.x, pl.x);
             tb_split(B.ph_im, ph.y, pl.y);
-            const bool to_main = first || (a.ka <= B.ksplit);
-            const bool tail_has = a.prev_ka > B.ksplit;  // an earlier launch wrote the tail
 #pragma unroll
             for (int j = 0; j < SPT; ++j) {
                 if (!inter[j]) continue;
@@ -235,37 +241,22 @@ __global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArg
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     const float2 tk = sQ[v * RMAX + idx];
-                    float2 val = acc[j][v];
+                    if (!first) {  // E (and the tail) this launch continues
+                        float2 e = make_float2(0.f, 0.f);
+                        if (to_main || done) e = accE[g * NV + v];
+                        if (!to_main && tail_has) {
+                            const float2 t2 = tail[g * NV + v];
+                            e = done ? make_float2(e.x + t2.x, e.y + t2.y) : t2;
+                        }
+                        acc[j][v] = make_float2(e.x + acc[j][v].x, e.y + acc[j][v].y);
+                    }
                     if (!done) {
                         out_cur[g * NV + v] = tk;
                         out_prev[g * NV + v] = sP[v * RMAX + idx];
-                        if (to_main) {
-                            if (!first) {
-                                const float2 e = accE[g * NV + v];
-                                val = make_float2(e.x + val.x, e.y + val.y);
-                            }
-                            accE[g * NV + v] = val;
-                        } else {
-                            if (tail_has) {
-                                const float2 e = tail[g * NV + v];
-                                val = make_float2(e.x + val.x, e.y + val.y);
-                            }
-                            tail[g * NV + v] = val;
-                        }
+                        if (to_main) accE[g * NV + v] = acc[j][v];
+                        else tail[g * NV + v] = acc[j][v];
                     } else {
-                        // psi = e^{-i b dt} (E + tail + partial)
-                        if (to_main) {
-                            const float2 e = accE[g * NV + v];
-                            val = make_float2(e.x + val.x, e.y + val.y);
-                        } else {
-                            if (tail_has) {
-                                const float2 e = tail[g * NV + v];
-                                val = make_float2(e.x + val.x, e.y + val.y);
-                            }
-                            const float2 e = accE[g * NV + v];
-                            val = make_float2(e.x + val.x, e.y + val.y);
-                        }
-                        psi[g * NV + v] = tb_phase(val, ph, pl);
+                        psi[g * NV + v] = tb_phase(acc[j][v], ph, pl);  // E + tail + partial
                         const double t2 = (double)tk.x * tk.x + (double)tk.y * tk.y;
                         const double lim = 4.0 * a.norm2[((size_t)T.block * NV + v) * 2];
                         if (!(t2 <= lim)) atomicOr(a.errflag, 1);
@@ -273,14 +264,14 @@ __global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArg
                 }
             }
         }
-        if (first) {
+        if constexpr (FIRST) {
             // per-tile partials of ||T_0||^2 and <T_0|H~ T_0>, fixed-order block reduction
             const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
             for (int s = 0; s < 2 * NV; ++s) {
-                double x = part[s];
-                for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-                if (lane == 0) s_red[warp * 2 * NV + s] = x;
+                double xs = (double)part[s];
+                for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
+                if (lane == 0) s_red[warp * 2 * NV + s] = xs;
             }
             __syncthreads();
             if (tid < 2 * NV) {
@@ -291,7 +282,7 @@ __global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArg
         }
         __syncthreads();  // shared memory is reused by the next tile
     }
-    if (first) {
+    if constexpr (FIRST) {
         __shared__ unsigned int s_last;
         __threadfence();
         __syncthreads();
@@ -324,7 +315,9 @@ size_t tb_smem_bytes(int nv, int spt)
 template <int NV, int SPT>
 static int tb_launch_t(const TBArgs& a, int grid, cudaStream_t s)
 {
-    k_rec_tb<NV, SPT><<<grid, TB_THREADS, tb_smem_bytes(NV, SPT), s>>>(a);
+    const size_t smem = tb_smem_bytes(NV, SPT);
+    if (a.ka == 1) k_rec_tb<NV, SPT, true><<<grid, TB_THREADS, smem, s>>>(a);
+    else k_rec_tb<NV, SPT, false><<<grid, TB_THREADS, smem, s>>>(a);
     CHEB_CUDA(cudaGetLastError());
     return CHEB_OK;
 }
@@ -332,8 +325,9 @@ static int tb_launch_t(const TBArgs& a, int grid, cudaStream_t s)
 template <int NV, int SPT>
 static int tb_attr_t()
 {
-    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tb<NV, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)tb_smem_bytes(NV, SPT)));
+    const int smem = (int)tb_smem_bytes(NV, SPT);
+    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tb<NV, SPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tb<NV, SPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     return CHEB_OK;
 }
 
