@@ -53,6 +53,12 @@ def parse():
                     help="skip the oracle timing (profiling runs)")
     ap.add_argument("--lean", action="store_true",
                     help="timed region only: no e2e, FP64 or accuracy legs (profiling runs)")
+    ap.add_argument("--workload", default="ensemble",
+                    choices=["ensemble", "ribbon", "holstein", "doublewell", "adjoint"],
+                    help="ensemble (default, the headline line); the others measure the other "
+                         "configurations of the hot path")
+    ap.add_argument("--prec", default=None, choices=["c64", "c128"],
+                    help="vector precision for --workload ribbon/holstein (default c128)")
     ap.add_argument("--blocking", default=None,
                     help="S:SPT -- force S orders per launch with SPT sites per thread and skip "
                          "the autotuner (profiling runs); 0:0 forces single-order launches")
@@ -418,12 +424,259 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+# ----------------------------------------------------------------------------------------
+# the other configurations (one problem per GPU): --workload ribbon | holstein | doublewell |
+# adjoint
+# ----------------------------------------------------------------------------------------
+def _single_setup(args):
+    """(name, build_plan(cb) -> (plan, psi, host_packet), dt, nsteps_config, oracle_operator,
+    emin/emax/alpha, sites, description)"""
+    wk = args.workload
+    if wk == "ribbon":
+        rb = wl.Ribbon()
+        return dict(name="zigzag ribbon 128x2048, W=1, single vector, dt=1", sites=rb.n_sites,
+                    dt=rb.dt, nsteps=rb.nsteps, kind="ribbon", obj=rb, bounds=rb.bounds(),
+                    alpha=0.0, packet=rb.packet())
+    if wk == "holstein":
+        hs = wl.Holstein()
+        return dict(name="Holstein L=12 periodic, nph<=10 (D=7,759,752), dt=0.25", sites=hs.dim,
+                    dt=hs.dt, nsteps=hs.nsteps, kind="holstein", obj=hs, bounds=hs.bounds(),
+                    alpha=hs.alpha, packet=hs.initial_state())
+    if wk == "doublewell":
+        d = wl.DoubleWell1D()
+        return dict(name="1D double well N=2048, dt=0.5 (M=6353)", sites=d.n, dt=d.dt,
+                    nsteps=d.nsteps, kind="doublewell", obj=d, bounds=d.bounds(), alpha=0.01,
+                    packet=d.packet())
+    rb = wl.Ribbon(W=60, L=1000, disorder=1.0, seed=3022, c0=250, r0=30)
+    return dict(name="adjoint gradient of P_R (x_R=500) on a 60x1000 ribbon, T=300, dt=1",
+                sites=rb.n_sites, dt=rb.dt, nsteps=300, kind="adjoint", obj=rb,
+                bounds=rb.bounds(), alpha=0.0, packet=rb.packet())
+
+
+def _single_plan(cb, cfg, prec):
+    import torch
+
+    o = cfg["obj"]
+    if cfg["kind"] in ("ribbon", "adjoint"):
+        eps = torch.from_numpy(o.onsite()).to("cuda")
+        desc, keep = cb.desc_ribbons([o.W], [o.L], o.hop, eps)
+    elif cfg["kind"] == "holstein":
+        desc, keep = cb.desc_holstein(o.L, o.nph, o.periodic, o.hop, o.omega0, o.g), ()
+    else:
+        V = torch.from_numpy(o.potential()).to("cuda")
+        desc, keep = cb.desc_lat1d(o.n, o.dx, V), (V,)
+    lo, hi = cfg["bounds"]
+    plan = cb.Plan(desc, [lo], [hi], cfg["alpha"], prec, 1, keep=keep)
+    dt = torch.complex64 if prec == cb.CHEB_C64 else torch.complex128
+    psi = torch.from_numpy(cfg["packet"]).to(dt).to("cuda").contiguous()
+    return plan, psi
+
+
+def _oracle_operator(cfg):
+    import oracle
+
+    o = cfg["obj"]
+    if cfg["kind"] in ("ribbon", "adjoint"):
+        return oracle.honeycomb(o.W, o.L, o.hop, o.onsite())
+    if cfg["kind"] == "holstein":
+        return oracle.holstein(o.L, o.nph, o.periodic, o.hop, o.omega0, o.g)
+    return oracle.lattice1d(o.n, o.dx, o.potential())
+
+
+def run_single(args, world, rank, local):
+    import torch
+
+    import oracle
+    import paper_0907_3022_gb300 as cb
+
+    torch.cuda.set_device(local)
+    cfg = _single_setup(args)
+    prec = cb.CHEB_C64 if args.prec == "c64" else cb.CHEB_C128
+    plan, psi = _single_plan(cb, cfg, prec)
+    stream = torch.cuda.current_stream()
+    plan.evolve(psi, cfg["dt"], 0)
+    plan.autotune()
+    M = plan.block(0)["M"]
+    a, b = oracle.rescale(*cfg["bounds"], cfg["alpha"])
+    out = {}
+    if cfg["kind"] == "adjoint":
+        # one step = one gradient of P_R through T = 300 time steps (forward, checkpointed
+        # recompute and reverse sweep); matvec-steps counted: forward T M, checkpoint forward
+        # T M, segment recompute <= T M, reverse T (M + 1)
+        T = cfg["nsteps"]
+        grad = torch.zeros(cfg["sites"], dtype=torch.float64, device="cuda")
+        P = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            plan.adjoint_potential(psi, cfg["dt"], T, region_col=500, grad=grad, P=P)
+        mv_per_step = T * (4 * M + 1)
+        launches0 = plan.launches()
+        clocks = Clocks(local)
+        torch.cuda.synchronize()
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.adjoint_potential(psi, cfg["dt"], T, region_col=500, grad=grad, P=P)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        gpu_launches = plan.launches() - launches0
+        roofline = None
+        value = mv_per_step * args.steps / (ms / 1e3)
+        if not args.no_cpu_baseline:
+            H = _oracle_operator(cfg)
+            C, _ = oracle.coeffs(a, b, cfg["dt"])
+            mask = (np.arange(cfg["sites"]) % cfg["obj"].L > 500).astype(np.uint8)
+            t0 = time.perf_counter()
+            Pr, gref, _ = H.adjoint_region(a, b, C, 20, cfg["packet"], mask)
+            tcpu = time.perf_counter() - t0
+            out["cpu_baseline"] = {"value": 20 * (4 * M + 1) / tcpu, "unit": UNIT, "cores": 1,
+                                   "kind": "oracle", "sample": "gradient through 20 of the 300 "
+                                   "time steps (FP64 oracle stores every v_k)"}
+        line_cfg = {"workload": cfg["name"], "checkpointing": "ceil(sqrt(M+1)) pairs per step"}
+        dtype = "f64" if prec == cb.CHEB_C128 else "c64"
+        unit_note = {"gradients_per_s": args.steps / (ms / 1e3)}
+    else:
+        ss_per_step = M * cfg["sites"]
+        mv_per_step = M
+        plan.evolve(psi, cfg["dt"], args.warmup)
+        plan.sync()
+        # value: the graph path (small problems are launch-latency bound, so per-launch events
+        # would distort it); kernel durations: a second, event-bracketed run of a few steps
+        launches0 = plan.launches()
+        clocks = Clocks(local)
+        torch.cuda.synchronize()
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.evolve(psi, cfg["dt"], args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        gpu_launches = plan.launches() - launches0
+        plan.set_timing(True)
+        plan.kernel_stats(reset=True)
+        plan.evolve(psi, cfg["dt"], min(args.steps, 5))
+        kms, kcount, kbytes = plan.kernel_stats(reset=True)
+        plan.set_timing(False)
+        value = mv_per_step * args.steps / (ms / 1e3)
+        peak, peak_kind = measured_peaks()
+        achieved = kbytes / (kms / 1e3) / 1e9
+        bound = "hbm"
+        note = None
+        if prec == cb.CHEB_C128:
+            bound = "alu"
+            note = ("complex128: about 10 FP64 instructions per site-order against ~1.19 "
+                    "TFLOP/s FP64 (measured FMA probe); the HBM figures are for reference")
+        l2_note = ("working set in L2" if cfg["sites"] * 16 * 5 < 100e6 else "inputs larger than L2")
+        roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": ("k_rec<%s,1,%s>" % ("double" if prec == cb.CHEB_C128 else "float",
+                                                    "SellOp" if cfg["kind"] == "holstein" else "StencilOp")),
+                    "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "launches": kcount, "kernel_ms_total": kms,
+                    "alg_bytes_per_launch": kbytes / max(kcount, 1), "note": note}
+        # accuracy: against the oracle after min(steps done, config) steps from the packet
+        nacc = {"holstein": 2, "ribbon": 50}.get(cfg["kind"], cfg["nsteps"])
+        if args.lean:
+            nacc = 0
+        if nacc:
+            x = torch.from_numpy(cfg["packet"]).to(psi.dtype).to("cuda").contiguous()
+            plan.evolve(x, cfg["dt"], nacc)
+            H = _oracle_operator(cfg)
+            C, _ = oracle.coeffs(a, b, cfg["dt"])
+            ref = H.evolve(a, b, C, nacc, cfg["packet"])
+            res = x.cpu().numpy().astype(np.complex128)
+            out["accuracy"] = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(res - ref) /
+                                                              np.linalg.norm(ref)),
+                               "sample": f"{nacc} steps from the initial state"}
+        if not args.no_cpu_baseline and not args.lean:
+            H = _oracle_operator(cfg)
+            C, _ = oracle.coeffs(a, b, cfg["dt"])
+            psi0 = cfg["packet"]
+            t0 = time.perf_counter()
+            H.step(a, b, C, psi0)
+            tcpu = time.perf_counter() - t0
+            out["cpu_baseline"] = {"value": mv_per_step / tcpu, "unit": UNIT, "cores": 1,
+                                   "kind": "oracle", "sample": "one time step (FP64 oracle)",
+                                   "site_steps_per_s": ss_per_step / tcpu}
+        # e2e: host packet in, one step, psi out
+        pin = torch.from_numpy(cfg["packet"]).to(psi.dtype).pin_memory()
+        pout = torch.empty_like(pin).pin_memory()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(args.steps):
+            psi.copy_(pin, non_blocking=True)
+            plan.evolve(psi, cfg["dt"], 1)
+            pout.copy_(psi, non_blocking=True)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        nb = pin.numel() * pin.element_size()
+        out["e2e"] = {"value": mv_per_step * args.steps / (h0.elapsed_time(h1) / 1e3),
+                      "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+        line_cfg = {"workload": cfg["name"], "sites": cfg["sites"], "M": M, "l2": l2_note,
+                    "launch_shape": dict(zip(("threads", "sites_per_thread", "grid",
+                                              "vecs_per_thread"), plan.launch_shape()))}
+        dtype = "f64" if prec == cb.CHEB_C128 else "c64"
+        unit_note = {"site_steps_per_s": ss_per_step * args.steps / (ms / 1e3)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": line_cfg, "roofline": roofline, "gpu_launches": gpu_launches,
+            "clocks": clk}
+    line.update(unit_note)
+    line.update(out)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
+def run_reference_single(args, world, rank):
+    """The oracle as the reference arm for --workload != ensemble (one step per step)."""
+    if rank != 0:
+        return 0
+    import oracle
+
+    cfg = _single_setup(args)
+    H = _oracle_operator(cfg)
+    a, b = oracle.rescale(*cfg["bounds"], cfg["alpha"])
+    C, M = oracle.coeffs(a, b, cfg["dt"])
+    psi = cfg["packet"]
+    for _ in range(args.warmup):
+        psi = H.step(a, b, C, psi)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        psi = H.step(a, b, C, psi)
+    tt = time.perf_counter() - t0
+    value = M * args.steps / tt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} time steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     try:
         if args.impl == "reference":
+            if args.workload != "ensemble":
+                return run_reference_single(args, world, rank)
             return run_reference(args, world, rank)
+        if args.workload != "ensemble":
+            return run_single(args, world, rank, local)
         return run_ours(args, world, rank, local)
     finally:
         if world > 1:

@@ -207,7 +207,10 @@ int cheb_region_norm_noalloc(const void* psi, int prec, int64_t n_sites, int32_t
               when onsite_per_vec == 0, [site][vec] when 1);
      lambda0: dP/d(conj psi0), plan layout and precision;
      P      : doubles [nvec] (only with the region objective).
-   CHEB_ERR_UNSUPPORTED for Holstein plans. */
+   The plan keeps the workspace (nsteps + 1 trajectory vectors plus about 3 sqrt(M) more)
+   and records the whole computation as a CUDA graph that later calls with the same
+   pointers, nsteps and dt replay.  Synchronises the plan's stream before returning.
+   CHEB_ERR_UNSUPPORTED for Holstein plans and for plans with several ribbons. */
 int cheb_adjoint_potential(cheb_plan* plan, const void* psi0, double dt, int nsteps,
                            const void* lambda_n, int64_t region_col, double* grad,
                            void* lambda0, double* P);

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "cheb_internal.cuh"
@@ -171,11 +172,13 @@ __global__ void k_adj_region_seed(AdjArgs a, const void* psi_, void* lam_, int64
     }
 }
 
+// Enqueue the whole gradient computation on stream s (capturable: no allocation, no
+// synchronisation).  ws holds the trajectory, checkpoints, segment, adjoint pair and lambda.
 template <typename R>
-static int adjoint_impl(Plan* p, const void* psi0, int nsteps, const void* lambda_n,
-                        int64_t region_col, double* grad, void* lambda0, double* P)
+static int adjoint_enqueue(Plan* p, cudaStream_t s, char* ws, const void* psi0, int nsteps,
+                           const void* lambda_n, int64_t region_col, double* g, void* lambda0,
+                           double* P)
 {
-    cudaStream_t s = p->stream;
     const size_t vb = p->vec_bytes();
     const DevBlock B = p->hblocks[0];
     const int M = B.M;
@@ -185,50 +188,31 @@ static int adjoint_impl(Plan* p, const void* psi0, int nsteps, const void* lambd
               p->desc.onsite_per_vec};
     const int grid = std::min<int>(a.nitems, 65535);
     const int th = 256;
-
-    // workspace: trajectory, checkpoints, segment, two adjoint buffers, lambda
-    char* ws = nullptr;
-    const size_t nvecs = (size_t)(nsteps + 1) + 2 * (size_t)nseg + (size_t)S + 3;
-    CHEB_CUDA(cudaMalloc(&ws, nvecs * vb));
     auto V = [&](size_t i) { return static_cast<void*>(ws + i * vb); };
     const size_t o_traj = 0, o_ck = nsteps + 1, o_seg = o_ck + 2 * nseg, o_w = o_seg + S,
                  o_lam = o_w + 2;
     int rc = CHEB_OK;
-    auto done = [&](int code) {
-        cudaStreamSynchronize(s);
-        cudaFree(ws);
-        return code;
-    };
     // forward trajectory with the fused propagator
-    if (cudaMemcpyAsync(V(o_traj), psi0, vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return done(fail(CHEB_ERR_CUDA, "adjoint: copy psi0"));
+    CHEB_CUDA(cudaMemcpyAsync(V(o_traj), psi0, vb, cudaMemcpyDeviceToDevice, s));
     for (int st = 0; st < nsteps; ++st) {
-        if (cudaMemcpyAsync(V(o_traj + st + 1), V(o_traj + st), vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-            return done(fail(CHEB_ERR_CUDA, "adjoint: copy step"));
-        rc = cheb_step(reinterpret_cast<cheb_plan*>(p), V(o_traj + st + 1), p->dt);
-        if (rc) return done(rc);
+        CHEB_CUDA(cudaMemcpyAsync(V(o_traj + st + 1), V(o_traj + st), vb, cudaMemcpyDeviceToDevice, s));
+        rc = plan_enqueue_step(p, V(o_traj + st + 1), s);
+        if (rc) return rc;
     }
     // seed
     void* lam = V(o_lam);
     if (lambda_n) {
-        if (cudaMemcpyAsync(lam, lambda_n, vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-            return done(fail(CHEB_ERR_CUDA, "adjoint: copy lambda_n"));
+        CHEB_CUDA(cudaMemcpyAsync(lam, lambda_n, vb, cudaMemcpyDeviceToDevice, s));
     } else {
         k_adj_region_seed<R><<<grid, th, 0, s>>>(a, V(o_traj + nsteps), lam, region_col);
         p->launches++;
         if (P) {
             rc = launch_observable(p, V(o_traj + nsteps), CHEB_OBS_PROB_COLS, (double)region_col, P, s);
-            if (rc) return done(rc);
+            if (rc) return rc;
         }
     }
     const size_t gbytes = (size_t)p->n_sites * (p->desc.onsite_per_vec ? p->nvec : 1) * sizeof(double);
-    double* g = grad;
-    double* gtmp = nullptr;
-    if (!g) {
-        if (cudaMalloc(&gtmp, gbytes) != cudaSuccess) return done(fail(CHEB_ERR_NOMEM, "adjoint grad"));
-        g = gtmp;
-    }
-    cudaMemsetAsync(g, 0, gbytes, s);
+    CHEB_CUDA(cudaMemsetAsync(g, 0, gbytes, s));
     auto fwd = [&](const void* cur, const void* prev, void* out, int first) {
         k_adj_forward<R><<<grid, th, 0, s>>>(a, cur, prev, out, first);
         p->launches++;
@@ -237,14 +221,15 @@ static int adjoint_impl(Plan* p, const void* psi0, int nsteps, const void* lambd
         // checkpoints of this step: pairs (v_{jS}, v_{jS+1})
         void* P0 = V(o_seg);
         void* P1 = V(o_seg + 1);
-        cudaMemcpyAsync(P0, V(o_traj + st), vb, cudaMemcpyDeviceToDevice, s);  // v_0
-        fwd(P0, nullptr, P1, 1);                                                // v_1
+        CHEB_CUDA(cudaMemcpyAsync(P0, V(o_traj + st), vb, cudaMemcpyDeviceToDevice, s));  // v_0
+        fwd(P0, nullptr, P1, 1);                                                           // v_1
         // P0 holds v_k, P1 holds v_{k+1}
         for (int k = 0; k <= M; ++k) {
             if (k % S == 0) {
                 const int j = k / S;
-                cudaMemcpyAsync(V(o_ck + 2 * j), P0, vb, cudaMemcpyDeviceToDevice, s);
-                if (k + 1 <= M) cudaMemcpyAsync(V(o_ck + 2 * j + 1), P1, vb, cudaMemcpyDeviceToDevice, s);
+                CHEB_CUDA(cudaMemcpyAsync(V(o_ck + 2 * j), P0, vb, cudaMemcpyDeviceToDevice, s));
+                if (k + 1 <= M)
+                    CHEB_CUDA(cudaMemcpyAsync(V(o_ck + 2 * j + 1), P1, vb, cudaMemcpyDeviceToDevice, s));
             }
             if (k + 2 <= M) {
                 fwd(P1, P0, P0, 0);  // v_{k+2} over v_k
@@ -258,12 +243,13 @@ static int adjoint_impl(Plan* p, const void* psi0, int nsteps, const void* lambd
         // reverse over segments
         for (int j = nseg - 1; j >= 0; --j) {
             const int k0 = j * S, k1 = std::min(k0 + S - 1, M);
-            cudaMemcpyAsync(V(o_seg), V(o_ck + 2 * j), vb, cudaMemcpyDeviceToDevice, s);
-            if (k1 > k0) cudaMemcpyAsync(V(o_seg + 1), V(o_ck + 2 * j + 1), vb, cudaMemcpyDeviceToDevice, s);
+            CHEB_CUDA(cudaMemcpyAsync(V(o_seg), V(o_ck + 2 * j), vb, cudaMemcpyDeviceToDevice, s));
+            if (k1 > k0)
+                CHEB_CUDA(cudaMemcpyAsync(V(o_seg + 1), V(o_ck + 2 * j + 1), vb, cudaMemcpyDeviceToDevice, s));
             for (int k = k0 + 2; k <= k1; ++k)
                 fwd(V(o_seg + (k - 1 - k0)), V(o_seg + (k - 2 - k0)), V(o_seg + (k - k0)), 0);
             for (int k = k1; k >= k0; --k) {
-                void* wk = V(o_w + (k & 1));            // w_k overwrites w_{k+2}
+                void* wk = V(o_w + (k & 1));             // w_k overwrites w_{k+2}
                 const void* w1 = V(o_w + ((k + 1) & 1)); // w_{k+1}
                 k_adj_reverse<R><<<grid, th, 0, s>>>(a, k, M, lam, w1, wk, V(o_seg + (k - k0)),
                                                      p->d_qcoef, g);
@@ -271,15 +257,86 @@ static int adjoint_impl(Plan* p, const void* psi0, int nsteps, const void* lambd
             }
         }
         // lambda_s = w_0
-        cudaMemcpyAsync(lam, V(o_w + 0), vb, cudaMemcpyDeviceToDevice, s);
+        CHEB_CUDA(cudaMemcpyAsync(lam, V(o_w + 0), vb, cudaMemcpyDeviceToDevice, s));
     }
-    if (lambda0) cudaMemcpyAsync(lambda0, lam, vb, cudaMemcpyDeviceToDevice, s);
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (gtmp) cudaFree(gtmp);
-    if (e != cudaSuccess) return done(cuda_fail(e, "adjoint kernels"));
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return done(cuda_fail(e, "adjoint launch"));
-    return done(CHEB_OK);
+    if (lambda0) CHEB_CUDA(cudaMemcpyAsync(lambda0, lam, vb, cudaMemcpyDeviceToDevice, s));
+    CHEB_CUDA(cudaGetLastError());
+    return CHEB_OK;
+}
+
+// The gradient call is recorded once as a CUDA graph (about 80 launches and 25 copies per
+// time step, each too short to hide its own launch overhead) and replayed while the
+// pointers, the number of steps and the plan's coefficients stay the same.
+template <typename R>
+static int adjoint_impl(Plan* p, const void* psi0, int nsteps, const void* lambda_n,
+                        int64_t region_col, double* grad, void* lambda0, double* P)
+{
+    const size_t vb = p->vec_bytes();
+    const int M = p->hblocks[0].M;
+    const int S = (int)std::ceil(std::sqrt((double)(M + 1)));
+    const int nseg = (M + 1 + S - 1) / S;
+    const size_t nvecs = (size_t)(nsteps + 1) + 2 * (size_t)nseg + (size_t)S + 3;
+    const size_t gbytes = (size_t)p->n_sites * (p->desc.onsite_per_vec ? p->nvec : 1) * sizeof(double);
+    const size_t need = nvecs * vb + (grad ? 0 : gbytes);
+    if (p->adj_ws_bytes < need) {
+        if (p->adj_graph) {
+            cudaGraphExecDestroy(p->adj_graph);
+            p->adj_graph = nullptr;
+        }
+        if (p->adj_ws) cudaFree(p->adj_ws);
+        p->adj_ws = nullptr;
+        p->adj_ws_bytes = 0;
+        if (cudaMalloc(&p->adj_ws, need) != cudaSuccess)
+            return fail(CHEB_ERR_NOMEM, "adjoint workspace (trajectory of nsteps + 1 vectors)");
+        p->adj_ws_bytes = need;
+    }
+    char* ws = static_cast<char*>(p->adj_ws);
+    double* g = grad ? grad : reinterpret_cast<double*>(ws + nvecs * vb);
+    int rc = obs_prepare(p);
+    if (rc) return rc;
+    Plan::AdjKey key;
+    std::memset(&key, 0, sizeof(key));  // padding included, for the memcmp below
+    key.psi0 = psi0;
+    key.lambda_n = lambda_n;
+    key.region_col = region_col;
+    key.grad = grad;
+    key.lambda0 = lambda0;
+    key.P = P;
+    key.nsteps = nsteps;
+    key.dt = p->dt;
+    key.epoch = p->shape_epoch;
+    key.ws = p->adj_ws;
+    const bool hit = p->adj_graph && std::memcmp(&key, &p->adj_key, sizeof(key)) == 0;
+    if (!hit) {
+        if (p->adj_graph) {
+            cudaGraphExecDestroy(p->adj_graph);
+            p->adj_graph = nullptr;
+        }
+        const bool timing = p->timing;
+        p->timing = false;  // no per-launch events inside the graph
+        const int64_t before = p->launches;
+        cudaGraph_t graph = nullptr;
+        CHEB_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rc = adjoint_enqueue<R>(p, p->cap_stream, ws, psi0, nsteps, lambda_n, region_col, g,
+                                lambda0, P);
+        cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &graph);
+        p->timing = timing;
+        p->adj_graph_kernels = (int)(p->launches - before);
+        p->launches = before;
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "adjoint: cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&p->adj_graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ce, "adjoint: cudaGraphInstantiate");
+        p->adj_key = key;
+    }
+    CHEB_CUDA(cudaGraphLaunch(p->adj_graph, p->stream));
+    p->launches += p->adj_graph_kernels;
+    CHEB_CUDA(cudaStreamSynchronize(p->stream));
+    return CHEB_OK;
 }
 
 }  // namespace cheb

@@ -422,6 +422,8 @@ static int enqueue_step_tb(Plan* p, void* psi, cudaStream_t st)
     return CHEB_OK;
 }
 
+int plan_enqueue_step(Plan* p, void* psi, cudaStream_t s) { return enqueue_step(p, psi, s); }
+
 static int check_psi(const Plan* p, const void* psi)
 {
     if (!psi) return fail(CHEB_ERR_INVALID, "psi is NULL");
@@ -466,8 +468,9 @@ static void free_plan(Plan* p)
         if (t.d_tiles) cudaFree(t.d_tiles);
         if (t.d_begin) cudaFree(t.d_begin);
     }
-    for (void* q : {p->d_C, p->d_D, p->d_E, (void*)p->d_tb_partials})
+    for (void* q : {p->d_C, p->d_D, p->d_E, (void*)p->d_tb_partials, p->adj_ws})
         if (q) cudaFree(q);
+    if (p->adj_graph) cudaGraphExecDestroy(p->adj_graph);
     void* ptrs[] = {p->d_blocks, p->d_items, p->d_block_item_begin, p->d_diag, p->d_A, p->d_B,
                     p->d_tail,
                     p->d_qcoef, p->d_partials, p->d_counter, p->d_red, p->d_err,

@@ -233,6 +233,24 @@ struct Plan {
     double* d_tb_partials = nullptr;
     size_t tb_partials_cap = 0;
 
+    // adjoint: plan-owned workspace and the graph of the last gradient call
+    void* adj_ws = nullptr;
+    size_t adj_ws_bytes = 0;
+    cudaGraphExec_t adj_graph = nullptr;
+    struct AdjKey {
+        const void* psi0;
+        const void* lambda_n;
+        int64_t region_col;
+        const void* grad;
+        const void* lambda0;
+        const void* P;
+        int nsteps;
+        double dt;
+        int64_t epoch;
+        const void* ws;
+    } adj_key{};
+    int adj_graph_kernels = 0;
+
     // kernel timing (cheb_plan_set_timing)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -247,6 +265,8 @@ struct Plan {
 };
 
 int plan_build_items(Plan* p);
+int plan_enqueue_step(Plan* p, void* psi, cudaStream_t s);
+int obs_prepare(Plan* p);
 int vpt_for(int prec, int nvec, int want);
 
 }  // namespace cheb

@@ -542,6 +542,19 @@ __global__ void k_obs_finalize(const double* partials, const int32_t* block_item
 int launch_holstein_observable(Plan* p, const void* psi, int kind, double* out, cudaStream_t s);
 int launch_holstein_energy(Plan* p, const void* psi, double* out, cudaStream_t s);
 
+// allocate the stencil observables' partials ahead of a stream capture
+int obs_prepare(Plan* p)
+{
+    const size_t need = p->hitems.size() * (size_t)p->nvec;
+    if (p->obs_scratch_cap >= need) return CHEB_OK;
+    if (p->d_obs_scratch) cudaFree(p->d_obs_scratch);
+    p->d_obs_scratch = nullptr;
+    p->obs_scratch_cap = 0;
+    CHEB_CUDA(cudaMalloc(&p->d_obs_scratch, need * sizeof(double)));
+    p->obs_scratch_cap = need;
+    return CHEB_OK;
+}
+
 int launch_observable(Plan* p, const void* psi, int kind, double param, double* out,
                       cudaStream_t s)
 {
