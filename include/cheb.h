@@ -65,9 +65,10 @@ typedef enum {
        (ribbon q starts at site sum_{p<q} W_p L_p); each has its own a, b, c_k and M.
        onsite = eps_j. */
     CHEB_HONEYCOMB_ZZ = 1,
-    /* Holstein chain, Sec. 3.3, Eq. (ghm), one spinless electron, Delta_i = 0 and
-       g_i = g: H = -t sum_i (c_i^+ c_{i+1} + h.c.) - g w0 sum_i (b_i^+ + b_i) n_i
-       + w0 sum_i b_i^+ b_i, in the basis |e; n_0..n_{L-1}> with sum_i n_i <= nph (Sec. 3.3).
+    /* Holstein chain, Sec. 3.3, Eq. (ghm), one spinless electron:
+       H = sum_i Delta_i n_i - t sum_i (c_i^+ c_{i+1} + h.c.) - sum_i g_i w0 (b_i^+ + b_i) n_i
+       + w0 sum_i b_i^+ b_i, in the basis |e; n_0..n_{L-1}> with sum_i n_i <= nph (Sec. 3.3);
+       Delta_i from onsite (device [L], NULL: 0), g_i from hol_g (NULL: g).
        Basis index = e * Dph + rank(n), Dph = C(nph + L, L), rank = position of n in the
        lexicographic order of all admissible tuples (n_0 most significant) -- see
        cheb_holstein_rank.  Stored as a SELL-C-sigma matrix built on the device. */
@@ -96,8 +97,11 @@ typedef struct cheb_ham_desc {
     int32_t hol_periodic;    /* 1: bond (L-1, 0) present (needs L >= 3)                   */
     double omega0;           /* phonon frequency w0                                        */
     double g;                /* dimensionless coupling g                                   */
-    int32_t sell_sigma;      /* SELL sorting window in rows (0 or 1: no sorting; else a
-                                multiple of 32)                                            */
+    int32_t sell_sigma;      /* reserved (SELL row sorting is not applied; must be 0 or 1)  */
+    /* CHEB_HOLSTEIN, optional: device [L] site couplings g_i (Eq. ghm,
+       g_i = ((eps_p + eps_p,i)/w0)^{1/2}); NULL: g at every site.  With onsite = device [L]
+       site potentials Delta_i (NULL: 0) this is the generalised model of Sec. 3.3. */
+    const double* hol_g;
 } cheb_ham_desc;
 
 typedef struct cheb_plan cheb_plan;
@@ -248,7 +252,8 @@ int cheb_plan_blocking(const cheb_plan* plan, int* orders_per_launch, int* sites
 /* Copies of the plan's device data to host memory, for checking the construction:
    the SELL matrix of a Holstein plan as CSR in original row order (rowptr [n+1] int64,
    col [nnz] int64, val [nnz] double with the unscaled H entries); nnz_out gets the count.
-   Pass col = val = NULL to query nnz only. */
+   Pass col = val = NULL to query nnz only.  Plans with more than 2^27 rows keep no
+   unscaled copy of the matrix (CHEB_ERR_UNSUPPORTED). */
 int cheb_plan_export_csr(cheb_plan* plan, int64_t* rowptr, int64_t* col, double* val,
                          int64_t* nnz_out);
 /* Number of kernel launches the plan has enqueued since creation (graph replays count

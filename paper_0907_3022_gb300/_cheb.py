@@ -49,6 +49,7 @@ class cheb_ham_desc(ctypes.Structure):
         ("omega0", ctypes.c_double),
         ("g", ctypes.c_double),
         ("sell_sigma", ctypes.c_int32),
+        ("hol_g", ctypes.c_void_p),
     ]
 
 
@@ -352,7 +353,9 @@ def desc_ribbons(W, L, hop: float = 1.0, onsite=None, onsite_per_vec: bool = Fal
 
 
 def desc_holstein(L: int, nph: int, periodic: bool, hop: float, omega0: float, g: float,
-                  delta=None) -> cheb_ham_desc:
+                  delta=None, gsite=None) -> cheb_ham_desc:
+    """Holstein descriptor; delta / gsite: optional device float64 tensors [L] with the site
+    potentials Delta_i and couplings g_i (keep them alive while the plan is built)."""
     d = cheb_ham_desc()
     d.kind = CHEB_HOLSTEIN
     d.nblocks = 1
@@ -363,4 +366,5 @@ def desc_holstein(L: int, nph: int, periodic: bool, hop: float, omega0: float, g
     d.omega0 = omega0
     d.g = g
     d.onsite = _ptr(delta)
+    d.hol_g = _ptr(gsite)
     return d

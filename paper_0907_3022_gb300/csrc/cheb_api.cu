@@ -533,6 +533,9 @@ extern "C" int cheb_plan_create(cheb_plan** out, const cheb_ham_desc* h, const d
 
     if (h->onsite && !aligned16(h->onsite))
         return bail(fail(CHEB_ERR_ALIGN, "onsite must be 16-byte aligned"));
+    if (h->kind == CHEB_HOLSTEIN && h->hol_g && !aligned16(h->hol_g))
+        return bail(fail(CHEB_ERR_ALIGN, "hol_g must be 16-byte aligned"));
+    if (h->sell_sigma > 1) return bail(fail(CHEB_ERR_UNSUPPORTED, "SELL row sorting is not applied"));
     if (h->onsite_per_vec && h->kind == CHEB_HOLSTEIN)
         return bail(fail(CHEB_ERR_UNSUPPORTED, "per-vector on-site data needs a lattice kind"));
     switch (h->kind) {
@@ -939,6 +942,8 @@ extern "C" int cheb_plan_export_csr(cheb_plan* plan, int64_t* rowptr, int64_t* c
     Plan* p = reinterpret_cast<Plan*>(plan);
     if (!p || !nnz_out) return fail(CHEB_ERR_INVALID, "cheb_plan_export_csr: NULL argument");
     if (p->op != OP_SELL) return fail(CHEB_ERR_UNSUPPORTED, "export needs a SELL (Holstein) plan");
+    if (!p->d_sell_val_raw)
+        return fail(CHEB_ERR_UNSUPPORTED, "plans above 2^27 rows keep no unscaled matrix copy");
     const int64_t n = p->n_sites;
     std::vector<uint8_t> rl(n);
     std::vector<double> diag(n);

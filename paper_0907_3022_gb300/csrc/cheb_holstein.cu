@@ -81,6 +81,7 @@ struct HolParams {
     int64_t dph, n;
     double t, omega0, g;
     const double* delta;  // [L] or NULL
+    const double* gsite;  // [L] or NULL
     Binom C;
 };
 
@@ -90,6 +91,7 @@ __device__ inline int hol_row(const HolParams& P, int64_t i, int64_t* col, doubl
 {
     const int e = (int)(i / P.dph);
     const int64_t p = i - (int64_t)e * P.dph;
+    const double ge = P.gsite ? P.gsite[e] : P.g;
     uint8_t occ[HOL_MAX_L];
     hol_unrank(P.C, P.L, P.nph, p, occ);
     int ntot = 0;
@@ -107,14 +109,14 @@ __device__ inline int hol_row(const HolParams& P, int64_t i, int64_t* col, doubl
     if (ntot < P.nph) {
         occ[e] = (uint8_t)(ne + 1);
         col[cnt] = (int64_t)e * P.dph + hol_rank(P.C, P.L, P.nph, occ);
-        val[cnt] = -P.g * P.omega0 * sqrt((double)ne + 1.0);
+        val[cnt] = -ge * P.omega0 * sqrt((double)ne + 1.0);
         ++cnt;
         occ[e] = (uint8_t)ne;
     }
     if (ne > 0) {
         occ[e] = (uint8_t)(ne - 1);
         col[cnt] = (int64_t)e * P.dph + hol_rank(P.C, P.L, P.nph, occ);
-        val[cnt] = -P.g * P.omega0 * sqrt((double)ne);
+        val[cnt] = -ge * P.omega0 * sqrt((double)ne);
         ++cnt;
         occ[e] = (uint8_t)ne;
     }
@@ -153,10 +155,10 @@ __global__ void k_hol_fill(HolParams P, const int64_t* chunk_off, const int32_t*
         const bool real = e < cnt;
         scol[off + (int64_t)e * 32] = real ? (int32_t)col[e] : (int32_t)i;
         sval[off + (int64_t)e * 32] = real ? (R)(2.0 * val[e] / a) : (R)0;
-        sval_raw[off + (int64_t)e * 32] = real ? val[e] : 0.0;
+        if (sval_raw) sval_raw[off + (int64_t)e * 32] = real ? val[e] : 0.0;
     }
-    rowlen[i] = (uint8_t)cnt;
-    diag_raw[i] = d;
+    if (rowlen) rowlen[i] = (uint8_t)cnt;
+    if (diag_raw) diag_raw[i] = d;
     diag_scaled[i] = (R)(2.0 * (d - b) / a);
 }
 
@@ -183,7 +185,10 @@ int holstein_build(Plan* p)
     P.omega0 = h.omega0;
     P.g = h.g;
     P.delta = h.onsite;
+    P.gsite = h.hol_g;
     P.C = Binom{p->d_binom, L};
+    // unscaled copies (CSR export) only for bases up to 2^27 rows
+    const bool keep_raw = n <= ((int64_t)1 << 27);
 
     const int64_t nchunks = (n + 31) / 32;
     p->sell_nchunks = nchunks;
@@ -207,9 +212,11 @@ int holstein_build(Plan* p)
     const size_t ns = (size_t)std::max<int64_t>(p->sell_nnz_stored, 1);
     CHEB_CUDA(cudaMalloc(&p->d_sell_col, ns * sizeof(int32_t)));
     CHEB_CUDA(cudaMalloc(&p->d_sell_val, ns * p->real_size()));
-    CHEB_CUDA(cudaMalloc(&p->d_sell_val_raw, ns * sizeof(double)));
-    CHEB_CUDA(cudaMalloc(&p->d_hol_diag_raw, (size_t)n * sizeof(double)));
-    CHEB_CUDA(cudaMalloc(&p->d_hol_rowlen, (size_t)n));
+    if (keep_raw) {
+        CHEB_CUDA(cudaMalloc(&p->d_sell_val_raw, ns * sizeof(double)));
+        CHEB_CUDA(cudaMalloc(&p->d_hol_diag_raw, (size_t)n * sizeof(double)));
+        CHEB_CUDA(cudaMalloc(&p->d_hol_rowlen, (size_t)n));
+    }
     const DevBlock& B = p->hblocks[0];
     const unsigned gb = (unsigned)((n + th - 1) / th);
     if (p->prec == CHEB_C128)
@@ -238,8 +245,8 @@ int holstein_build(Plan* p)
 template <typename R>
 __global__ void k_hol_obs(HolParams P, const WorkItem* items, int nitems, const void* psi_,
                           int nvec, int kind, const int64_t* chunk_off, const int32_t* chunk_len,
-                          const int32_t* scol, const double* sval_raw, const uint8_t* rowlen,
-                          const double* diag_raw, double* partials, int nslot)
+                          const int32_t* scol, const R* sval, const R* dscaled, double a,
+                          double b, double* partials, int nslot)
 {
     using C = typename CT<R>::type;
     const C* psi = static_cast<const C*>(psi_);
@@ -254,15 +261,19 @@ __global__ void k_hol_obs(HolParams P, const WorkItem* items, int nitems, const 
                     const C x = psi[i * nvec + v];
                     const double wgt = (double)x.x * x.x + (double)x.y * x.y;
                     if (kind == CHEB_OBS_ENERGY) {
-                        double hx = diag_raw[i] * x.x, hy = diag_raw[i] * x.y;
+                        // <x|H|x> = (a/2) <x|2H~ x> + b |x|^2 from the scaled matrix the
+                        // recurrence uses (padding entries are zero)
+                        const double d = (double)dscaled[i];
+                        double hx = d * x.x, hy = d * x.y;
                         const int64_t ch = i >> 5;
                         const int64_t off = chunk_off[ch] + (i & 31);
-                        for (int e = 0; e < rowlen[i]; ++e) {
+                        for (int e = 0; e < chunk_len[ch]; ++e) {
                             const C y = psi[(int64_t)scol[off + (int64_t)e * 32] * nvec + v];
-                            hx += sval_raw[off + (int64_t)e * 32] * y.x;
-                            hy += sval_raw[off + (int64_t)e * 32] * y.y;
+                            const double w = (double)sval[off + (int64_t)e * 32];
+                            hx += w * y.x;
+                            hy += w * y.y;
                         }
-                        acc += (double)x.x * hx + (double)x.y * hy;
+                        acc += 0.5 * a * ((double)x.x * hx + (double)x.y * hy) + b * wgt;
                     } else if (kind == CHEB_OBS_HOL_DENSITY) {
                         acc += wgt;
                     } else {
@@ -346,16 +357,19 @@ static int hol_obs_common(Plan* p, const void* psi, int kind, double* out, cudaS
         p->obs_scratch_cap = need;
     }
     const int grid = std::min(nitems, 65535);
+    const double ba = p->hblocks[0].a, bb = p->hblocks[0].b;
     if (p->prec == CHEB_C128)
         k_hol_obs<double><<<grid, 256, 0, s>>>(P, p->d_items, nitems, psi, p->nvec, kind,
                                                p->d_sell_chunk_off, p->d_sell_chunk_len,
-                                               p->d_sell_col, p->d_sell_val_raw, p->d_hol_rowlen,
-                                               p->d_hol_diag_raw, p->d_obs_scratch, nslot);
+                                               p->d_sell_col, static_cast<const double*>(p->d_sell_val),
+                                               static_cast<const double*>(p->d_diag), ba, bb,
+                                               p->d_obs_scratch, nslot);
     else
         k_hol_obs<float><<<grid, 256, 0, s>>>(P, p->d_items, nitems, psi, p->nvec, kind,
                                               p->d_sell_chunk_off, p->d_sell_chunk_len,
-                                              p->d_sell_col, p->d_sell_val_raw, p->d_hol_rowlen,
-                                              p->d_hol_diag_raw, p->d_obs_scratch, nslot);
+                                              p->d_sell_col, static_cast<const float*>(p->d_sell_val),
+                                              static_cast<const float*>(p->d_diag), ba, bb,
+                                              p->d_obs_scratch, nslot);
     k_hol_obs_finalize<<<1, 256, 0, s>>>(p->d_items, nitems, p->hol_dph, P.L, p->nvec, kind,
                                          nslot, p->d_obs_scratch, out);
     p->launches += 2;

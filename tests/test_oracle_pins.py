@@ -431,3 +431,40 @@ def test_adjoint_matches_daleckii_krein():
         ref[i] = 2 * np.real(np.vdot(lam, dpsi_eig))
     assert abs(P - float(np.sum(Pi * np.abs(psiT) ** 2))) < 1e-12
     assert np.max(np.abs(grad - ref)) < 1e-10
+
+
+def test_holstein_site_dependent_terms_decoupled_limit():
+    """t = 0 decouples the electron sites: with the electron at e the phonons at e form an
+    oscillator displaced by g_e and the other site's phonons a free one, so the levels are
+    Delta_e + w0 (m - g_e^2), m = 0, 1, ..., with multiplicity m + 1 (pins Delta_i and g_i of
+    Eq. ghm per site; the cap of 30 phonons is invisible in the lowest levels)."""
+    L, nph, w0 = 2, 30, 1.5
+    Delta = np.array([0.0, 0.7])
+    g = np.array([0.5, 0.9])
+    H = oracle.holstein(L, nph, False, 0.0, w0, 1.0, Delta=Delta, gsite=g)
+    E = np.sort(np.linalg.eigvalsh(H.dense()))
+    ref = []
+    for e in range(L):
+        for m in range(6):
+            ref += [Delta[e] + w0 * (m - g[e] ** 2)] * (m + 1)
+    ref = np.sort(ref)[:12]
+    assert np.max(np.abs(E[:12] - ref)) < 1e-9
+
+
+def test_polaron_workload_shape():
+    pw = wl.Polaron()
+    assert pw.dim == 622_751_220
+    g = pw.gsite()
+    assert abs(g[0] - math.sqrt(0.5)) < 1e-15 and abs(g[11] - 1.0) < 1e-15
+    assert pw.delta()[11] == 2.0 and pw.delta().sum() == 2.0
+    assert abs(np.linalg.norm(pw.electron_packet()) - 1.0) < 1e-14
+    small = wl.Polaron(L=5, nph=3, barrier_site=3, packet_site=1)
+    H = oracle.holstein(small.L, small.nph, False, small.hop, small.omega0, 1.0,
+                        Delta=small.delta(), gsite=small.gsite())
+    lo, hi = small.bounds()
+    E = np.linalg.eigvalsh(H.dense())
+    assert lo <= E[0] and E[-1] <= hi
+    psi0 = small.initial_state()
+    dens, phon, chi = H.observables(psi0)
+    assert np.allclose(dens, np.abs(small.electron_packet()) ** 2)
+    assert np.allclose(phon, 0) and np.allclose(chi, 0)

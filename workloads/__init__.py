@@ -259,3 +259,84 @@ class Holstein:
         psi = np.zeros(self.dim, dtype=np.complex128)
         psi[0] = 1.0
         return psi
+
+
+@dataclass
+class Polaron:
+    """Polaron formation and tunnelling (Sec. 3.3, Fig. 3): generalised Holstein model on an
+    open chain of 18 sites with at most 11 phonons (D = 18 C(29, 11) = 622,751,220),
+    eps_p = 1, w0 = 2, t = 1, barrier Delta = 2 at site 12 (index 11), and an electron wave
+    packet at site 4 (index 3) with momentum pi/9 in the phonon vacuum.
+
+    Values the paper does not state (readings): the extra coupling at the barrier site,
+    eps_p,12 = eps_p (so g_12 = sqrt(2 eps_p / w0)); the packet width sigma = 2 sites."""
+    L: int = 18
+    nph: int = 11
+    periodic: bool = False
+    hop: float = 1.0
+    omega0: float = 2.0
+    eps_p: float = 1.0
+    barrier_site: int = 11
+    barrier: float = 2.0
+    eps_p_barrier: float = 1.0
+    packet_site: int = 3
+    k: float = math.pi / 9
+    sigma: float = 2.0
+    dt: float = 0.25
+    t_end: float = 20.0
+    alpha: float = 0.01
+
+    @property
+    def dim_phonon(self) -> int:
+        return math.comb(self.nph + self.L, self.L)
+
+    @property
+    def dim(self) -> int:
+        return self.L * self.dim_phonon
+
+    @property
+    def nsteps(self) -> int:
+        return int(round(self.t_end / self.dt))
+
+    def delta(self) -> np.ndarray:
+        d = np.zeros(self.L)
+        if 0 <= self.barrier_site < self.L:
+            d[self.barrier_site] = self.barrier
+        return d
+
+    def gsite(self) -> np.ndarray:
+        """g_i = ((eps_p + eps_p,i) / w0)^{1/2} (Eq. ghm)."""
+        extra = np.zeros(self.L)
+        if 0 <= self.barrier_site < self.L:
+            extra[self.barrier_site] = self.eps_p_barrier
+        return np.sqrt((self.eps_p + extra) / self.omega0)
+
+    def electron_packet(self) -> np.ndarray:
+        """exp(-(i - i0)^2 / (2 sigma^2) + i k i) on the L sites, unit norm."""
+        i = np.arange(self.L, dtype=np.float64)
+        c = np.exp(-((i - self.packet_site) ** 2) / (2 * self.sigma ** 2) + 1j * self.k * i)
+        return c / np.linalg.norm(c)
+
+    def packet_indices(self) -> np.ndarray:
+        """Basis indices |e; vacuum> = e * Dph (the vacuum has rank 0)."""
+        return np.arange(self.L, dtype=np.int64) * self.dim_phonon
+
+    def initial_state(self) -> np.ndarray:
+        psi = np.zeros(self.dim, dtype=np.complex128)
+        psi[self.packet_indices()] = self.electron_packet()
+        return psi
+
+    def bounds(self):
+        """Gershgorin interval: rows with the electron at e, occupation k there and total s
+        have diagonal Delta_e + w0 s and radius hops(e) t + g_e w0 (sqrt(k+1)[s<nph] + sqrt(k))."""
+        d, g = self.delta(), self.gsite()
+        lo, hi = math.inf, -math.inf
+        for e in range(self.L):
+            hops = 2 if self.periodic else (e > 0) + (e < self.L - 1)
+            for s in range(self.nph + 1):
+                for kk in range(s + 1):
+                    rad = hops * abs(self.hop) + abs(g[e]) * self.omega0 * (
+                        (math.sqrt(kk + 1) if s < self.nph else 0.0) + math.sqrt(kk))
+                    lo = min(lo, d[e] + self.omega0 * s - rad)
+                    hi = max(hi, d[e] + self.omega0 * s + rad)
+        return lo, hi
