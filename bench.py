@@ -59,6 +59,9 @@ def parse():
                          "configurations of the hot path")
     ap.add_argument("--prec", default=None, choices=["c64", "c128"],
                     help="vector precision for --workload ribbon/holstein (default c128)")
+    ap.add_argument("--matrix-free", action="store_true",
+                    help="--workload holstein/polaron: matrix-free Holstein operator instead of "
+                         "the stored SELL matrix")
     ap.add_argument("--blocking", default=None,
                     help="S:SPT -- force S orders per launch with SPT sites per thread and skip "
                          "the autotuner (profiling runs); 0:0 forces single-order launches")
@@ -461,7 +464,9 @@ def _single_plan(cb, cfg, prec):
         eps = torch.from_numpy(o.onsite()).to("cuda")
         desc, keep = cb.desc_ribbons([o.W], [o.L], o.hop, eps)
     elif cfg["kind"] == "holstein":
-        desc, keep = cb.desc_holstein(o.L, o.nph, o.periodic, o.hop, o.omega0, o.g), ()
+        desc = cb.desc_holstein(o.L, o.nph, o.periodic, o.hop, o.omega0, o.g,
+                                matrix_free=cfg.get("matrix_free", False))
+        keep = ()
     else:
         V = torch.from_numpy(o.potential()).to("cuda")
         desc, keep = cb.desc_lat1d(o.n, o.dx, V), (V,)
@@ -491,6 +496,7 @@ def run_single(args, world, rank, local):
 
     torch.cuda.set_device(local)
     cfg = _single_setup(args)
+    cfg["matrix_free"] = bool(args.matrix_free)
     prec = cb.CHEB_C64 if args.prec == "c64" else cb.CHEB_C128
     plan, psi = _single_plan(cb, cfg, prec)
     stream = torch.cuda.current_stream()
@@ -573,10 +579,13 @@ def run_single(args, world, rank, local):
             note = ("complex128: about 10 FP64 instructions per site-order against ~1.19 "
                     "TFLOP/s FP64 (measured FMA probe); the HBM figures are for reference")
         l2_note = ("working set in L2" if cfg["sites"] * 16 * 5 < 100e6 else "inputs larger than L2")
+        rtype = "double" if prec == cb.CHEB_C128 else "float"
+        if cfg["matrix_free"] and cfg["kind"] == "holstein":
+            kname = "k_rec_holmf<%s>" % rtype
+        else:
+            kname = "k_rec<%s,1,%s>" % (rtype, "SellOp" if cfg["kind"] == "holstein" else "StencilOp")
         roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "kernel": ("k_rec<%s,1,%s>" % ("double" if prec == cb.CHEB_C128 else "float",
-                                                    "SellOp" if cfg["kind"] == "holstein" else "StencilOp")),
+                    "frac": achieved / peak, "traffic": None, "kernel": kname,
                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "launches": kcount, "kernel_ms_total": kms,
                     "alg_bytes_per_launch": kbytes / max(kcount, 1), "note": note}
@@ -620,6 +629,8 @@ def run_single(args, world, rank, local):
         out["e2e"] = {"value": mv_per_step * args.steps / (h0.elapsed_time(h1) / 1e3),
                       "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
         line_cfg = {"workload": cfg["name"], "sites": cfg["sites"], "M": M, "l2": l2_note,
+                    "operator": ("matrix-free" if cfg["matrix_free"] else "SELL-32")
+                    if cfg["kind"] == "holstein" else "stencil",
                     "launch_shape": dict(zip(("threads", "sites_per_thread", "grid",
                                               "vecs_per_thread"), plan.launch_shape()))}
         dtype = "f64" if prec == cb.CHEB_C128 else "c64"
@@ -679,7 +690,8 @@ def run_polaron(args, world, rank, local):
     prec = cb.CHEB_C128 if args.prec == "c128" else cb.CHEB_C64
     d = torch.from_numpy(pw.delta()).to("cuda")
     g = torch.from_numpy(pw.gsite()).to("cuda")
-    desc = cb.desc_holstein(pw.L, pw.nph, pw.periodic, pw.hop, pw.omega0, 1.0, delta=d, gsite=g)
+    desc = cb.desc_holstein(pw.L, pw.nph, pw.periodic, pw.hop, pw.omega0, 1.0, delta=d, gsite=g,
+                            matrix_free=args.matrix_free)
     lo, hi = pw.bounds()
     t0 = time.perf_counter()
     plan = cb.Plan(desc, [lo], [hi], pw.alpha, prec, 1, keep=(d, g))
@@ -691,6 +703,7 @@ def run_polaron(args, world, rank, local):
     stream = torch.cuda.current_stream()
     plan.evolve(psi, pw.dt, 0)
     M = plan.block(0)["M"]
+    plan.autotune()
     plan.evolve(psi, pw.dt, args.warmup)
     plan.sync()
     launches0 = plan.launches()
@@ -729,12 +742,16 @@ def run_polaron(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": "paper polaron run: 18 sites, <= 11 phonons, D = 622,751,220, "
                                    "dt = 0.25", "M": M, "plan_build_s": build_s,
+                       "operator": "matrix-free" if args.matrix_free else "SELL-32",
+                       "launch_shape": dict(zip(("threads", "sites_per_thread", "grid",
+                                                 "vecs_per_thread"), plan.launch_shape())),
                        "l2": "inputs larger than L2"},
             "site_steps_per_s": M * pw.dim * args.steps / (ms / 1e3),
             "time_to_t20_s": ms / args.steps * pw.nsteps / 1e3,
             "roofline": {"bound": "alu" if prec == cb.CHEB_C128 else "hbm", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_rec<%s,1,SellOp>" % ("double" if prec == cb.CHEB_C128 else "float"),
+                         "kernel": ("k_rec_holmf<%s>" if args.matrix_free else "k_rec<%s,1,SellOp>")
+                                   % ("double" if prec == cb.CHEB_C128 else "float"),
                          "peak_kind": f"{peak_kind} copy bandwidth", "launches": kcount,
                          "alg_bytes_per_launch": kbytes / max(kcount, 1)},
             "gpu_launches": gpu_launches, "clocks": clk,

@@ -71,7 +71,8 @@ typedef enum {
        Delta_i from onsite (device [L], NULL: 0), g_i from hol_g (NULL: g).
        Basis index = e * Dph + rank(n), Dph = C(nph + L, L), rank = position of n in the
        lexicographic order of all admissible tuples (n_0 most significant) -- see
-       cheb_holstein_rank.  Stored as a SELL-C-sigma matrix built on the device. */
+       cheb_holstein_rank.  Stored as a SELL-C-sigma matrix built on the device, or, with
+       hol_matrix_free = 1, applied without a stored matrix (Sec. 3.3). */
     CHEB_HOLSTEIN = 2
 } cheb_kind;
 
@@ -102,6 +103,13 @@ typedef struct cheb_ham_desc {
        g_i = ((eps_p + eps_p,i)/w0)^{1/2}); NULL: g at every site.  With onsite = device [L]
        site potentials Delta_i (NULL: 0) this is the generalised model of Sec. 3.3. */
     const double* hol_g;
+    /* CHEB_HOLSTEIN: 1 = matrix-free operator.  Sec. 3.3 recomputes the matrix elements in
+       every multiplication so that its largest basis fits in memory; here each launch
+       recomputes them from the basis indices (phonon ranks of n +- 1_e, see
+       cheb_holstein_phonon_neighbors) and stores neither the matrix nor the diagonal.  Needs
+       L <= 32 and nph <= 15 (CHEB_ERR_UNSUPPORTED otherwise); same basis, layout and results
+       as the stored matrix.  0 = SELL-C matrix.  The CSR export needs the stored matrix. */
+    int32_t hol_matrix_free;
 } cheb_ham_desc;
 
 typedef struct cheb_plan cheb_plan;
@@ -227,6 +235,14 @@ int64_t cheb_holstein_dim_phonon(int L, int nph);
 int cheb_holstein_rank(int L, int nph, const uint8_t* occ, int e, int64_t* idx);
 /* Inverse of cheb_holstein_rank. */
 int cheb_holstein_unrank(int L, int nph, int64_t idx, uint8_t* occ, int* e);
+/* Phonon neighbours used by the matrix-free operator (Sec. 3.3): for the phonon
+   configurations n of ranks p0 .. p0 + count - 1 (host arrays [count][L], row i for rank
+   p0 + i) up[i][e] = rank(n + 1_e), or -1 when sum n = nph, and dn[i][e] = rank(n - 1_e), or
+   -1 when n_e = 0.  Ranks are phonon ranks (the basis index minus e * Dph).  Computed on the
+   host by the same routine the kernels run.  Needs 1 <= L <= 32, 0 <= nph <= 15,
+   Dph < 2^31 and 0 <= p0, p0 + count <= Dph; CHEB_ERR_INVALID otherwise. */
+int cheb_holstein_phonon_neighbors(int L, int nph, int64_t p0, int64_t count, int64_t* up,
+                                   int64_t* dn);
 
 /* ---- tuning --------------------------------------------------------------------------- */
 /* Times the plan's recurrence kernel over launch shapes (threads per block, sites per

@@ -50,6 +50,7 @@ class cheb_ham_desc(ctypes.Structure):
         ("g", ctypes.c_double),
         ("sell_sigma", ctypes.c_int32),
         ("hol_g", ctypes.c_void_p),
+        ("hol_matrix_free", ctypes.c_int32),
     ]
 
 
@@ -88,6 +89,8 @@ _SIGS = {
     "cheb_holstein_dim_phonon": ([_c.c_int, _c.c_int], _c.c_int64),
     "cheb_holstein_rank": ([_c.c_int, _c.c_int, _u8p, _c.c_int, _i64p], _c.c_int),
     "cheb_holstein_unrank": ([_c.c_int, _c.c_int, _c.c_int64, _u8p, _ip], _c.c_int),
+    "cheb_holstein_phonon_neighbors": ([_c.c_int, _c.c_int, _c.c_int64, _c.c_int64, _i64p,
+                                        _i64p], _c.c_int),
     "cheb_autotune": ([_vp], _c.c_int),
     "cheb_plan_launch": ([_vp, _ip, _ip, _ip, _ip], _c.c_int),
     "cheb_plan_set_blocking": ([_vp, _c.c_int, _c.c_int], _c.c_int),
@@ -177,6 +180,19 @@ def cheb_holstein_unrank(L: int, nph: int, idx: int):
     check(lib().cheb_holstein_unrank(L, nph, idx, o.ctypes.data_as(_u8p), ctypes.byref(e)),
           "cheb_holstein_unrank")
     return e.value, o
+
+
+def cheb_holstein_phonon_neighbors(L: int, nph: int, p0: int, count: int):
+    """(up, dn): int64 [count, L] phonon ranks of n + 1_e and n - 1_e (-1: not admissible)
+    for the phonon configurations of ranks p0 .. p0 + count - 1."""
+    import numpy as np
+
+    up = np.zeros((count, L), dtype=np.int64)
+    dn = np.zeros((count, L), dtype=np.int64)
+    check(lib().cheb_holstein_phonon_neighbors(L, nph, p0, count, up.ctypes.data_as(_i64p),
+                                               dn.ctypes.data_as(_i64p)),
+          "cheb_holstein_phonon_neighbors")
+    return up, dn
 
 
 # ---- plans ---------------------------------------------------------------------------------
@@ -353,9 +369,10 @@ def desc_ribbons(W, L, hop: float = 1.0, onsite=None, onsite_per_vec: bool = Fal
 
 
 def desc_holstein(L: int, nph: int, periodic: bool, hop: float, omega0: float, g: float,
-                  delta=None, gsite=None) -> cheb_ham_desc:
+                  delta=None, gsite=None, matrix_free: bool = False) -> cheb_ham_desc:
     """Holstein descriptor; delta / gsite: optional device float64 tensors [L] with the site
-    potentials Delta_i and couplings g_i (keep them alive while the plan is built)."""
+    potentials Delta_i and couplings g_i (keep them alive while the plan is built);
+    matrix_free: apply H without storing it (L <= 32, nph <= 15)."""
     d = cheb_ham_desc()
     d.kind = CHEB_HOLSTEIN
     d.nblocks = 1
@@ -367,4 +384,5 @@ def desc_holstein(L: int, nph: int, periodic: bool, hop: float, omega0: float, g
     d.g = g
     d.onsite = _ptr(delta)
     d.hol_g = _ptr(gsite)
+    d.hol_matrix_free = int(matrix_free)
     return d

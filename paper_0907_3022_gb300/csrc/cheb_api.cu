@@ -178,11 +178,13 @@ static RecArgs base_args(Plan* p)
 static double launch_bytes(const Plan* p, int k)
 {
     const double cs = (double)p->cplx_size() * p->nvec;
-    const double ds = (double)p->real_size() * (p->desc.onsite_per_vec ? p->nvec : 1);
+    // the matrix-free operator stores no diagonal
+    const double ds = (p->op == OP_HOLMF) ? 0.0
+                      : (double)p->real_size() * (p->desc.onsite_per_vec ? p->nvec : 1);
     double total = 0.0;
     for (const DevBlock& B : p->hblocks) {
         if (k > B.M) continue;
-        const double sites = (p->op == OP_SELL) ? (double)p->n_sites : (double)B.W * B.L;
+        const double sites = (p->op != OP_STENCIL) ? (double)p->n_sites : (double)B.W * B.L;
         double vecs;  // vectors read + written per site
         if (k == 1) vecs = 3;            // read psi; write T_0, T_1
         else if (k == 2) vecs = 4;       // read T_1, T_0; write T_2, psi
@@ -476,7 +478,8 @@ static void free_plan(Plan* p)
                     p->d_qcoef, p->d_partials, p->d_counter, p->d_red, p->d_err,
                     p->d_obs_scratch, p->d_sell_col, p->d_sell_val, p->d_sell_chunk_off,
                     p->d_sell_chunk_len, p->d_hol_diag_raw, p->d_sell_val_raw, p->d_binom,
-                    p->d_hol_rowlen};
+                    p->d_hol_rowlen, p->d_holmf_G, p->d_holmf_dtab, p->d_holmf_qtab,
+                    p->d_holmf_partials};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -575,8 +578,11 @@ extern "C" int cheb_plan_create(cheb_plan** out, const cheb_ham_desc* h, const d
             if (h->hol_sites < 1 || h->hol_sites > 64 || h->hol_nph < 0 || h->hol_nph > 255 ||
                 (h->hol_periodic && h->hol_sites < 3))
                 return bail(fail(CHEB_ERR_INVALID, "HOLSTEIN needs 1 <= L <= 64 (L >= 3 periodic), 0 <= nph <= 255"));
+            if (h->hol_matrix_free &&
+                (h->hol_sites > 32 || h->hol_nph > 15))
+                return bail(fail(CHEB_ERR_UNSUPPORTED, "matrix-free Holstein needs L <= 32 and nph <= 15"));
             p->nblocks = 1;
-            p->op = OP_SELL;
+            p->op = h->hol_matrix_free ? OP_HOLMF : OP_SELL;
             const int64_t dph = cheb_holstein_dim_phonon(h->hol_sites, h->hol_nph);
             if (dph < 1) return bail(fail(CHEB_ERR_INVALID, "Holstein basis too large"));
             p->hol_dph = dph;
@@ -616,7 +622,8 @@ extern "C" int cheb_plan_create(cheb_plan** out, const cheb_ham_desc* h, const d
     rc = upload_blocks(p);
     if (rc) return bail(rc);
     const size_t per = (h->onsite_per_vec ? (size_t)nvec : 1);
-    if (cudaMalloc(&p->d_diag, (size_t)p->n_sites * per * p->real_size()) != cudaSuccess ||
+    if ((p->op != OP_HOLMF &&
+         cudaMalloc(&p->d_diag, (size_t)p->n_sites * per * p->real_size()) != cudaSuccess) ||
         cudaMalloc(&p->d_A, p->vec_bytes()) != cudaSuccess ||
         cudaMalloc(&p->d_B, p->vec_bytes()) != cudaSuccess ||
         (prec == CHEB_C64 && cudaMalloc(&p->d_tail, p->vec_bytes()) != cudaSuccess) ||
@@ -631,7 +638,7 @@ extern "C" int cheb_plan_create(cheb_plan** out, const cheb_ham_desc* h, const d
     rc = plan_build_items(p);
     if (rc) return bail(rc);
     if (h->kind == CHEB_HOLSTEIN) {
-        rc = holstein_build(p);
+        rc = (p->op == OP_HOLMF) ? holmf_build(p) : holstein_build(p);
         if (rc) return bail(rc);
     } else {
         rc = launch_scale_diag(p, h->onsite, p->stream);
@@ -810,7 +817,7 @@ extern "C" int cheb_autotune(cheb_plan* plan)
     const int cap_c[] = {0, 4, 8, 16};
     std::vector<int> vpt_c;
     for (int v : {1, 2, 4})
-        if (vpt_for(p->prec, p->nvec, v) == v) vpt_c.push_back(v);
+        if (vpt_for(p->prec, p->nvec, v) == v && (p->op != OP_HOLMF || v == 1)) vpt_c.push_back(v);
     float best = 1e30f;
     int bt = p->threads, bs = p->spt, bc = p->grid_cap, bv = p->vpt;
     int rc = CHEB_OK;

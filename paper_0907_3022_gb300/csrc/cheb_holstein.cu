@@ -14,76 +14,10 @@
 #include <cmath>
 #include <vector>
 
+#include "cheb_holstein.cuh"
 #include "cheb_internal.cuh"
 
 namespace cheb {
-
-static constexpr int HOL_MAX_L = 64;
-
-// binomial table: C(m, j) at [m * (L + 2) + j], m in [0, nph + L + 1], j in [0, L + 1]
-struct Binom {
-    const int64_t* t;
-    int L;
-    __host__ __device__ int64_t operator()(int m, int j) const {
-        if (m < 0 || j < 0 || j > m) return 0;
-        return t[(int64_t)m * (L + 2) + j];
-    }
-};
-
-static bool make_binom(int L, int nph, std::vector<int64_t>& tab)
-{
-    const int mmax = nph + L + 1;
-    tab.assign((size_t)(mmax + 1) * (L + 2), 0);
-    for (int m = 0; m <= mmax; ++m) {
-        tab[(size_t)m * (L + 2) + 0] = 1;
-        for (int j = 1; j <= std::min(m, L + 1); ++j) {
-            const int64_t a = tab[(size_t)(m - 1) * (L + 2) + j - 1];
-            const int64_t b = (j <= m - 1) ? tab[(size_t)(m - 1) * (L + 2) + j] : 0;
-            if (a > INT64_MAX - b) return false;
-            tab[(size_t)m * (L + 2) + j] = a + b;
-        }
-    }
-    return true;
-}
-
-__host__ __device__ inline int64_t hol_rank(const Binom& C, int L, int nph, const uint8_t* occ)
-{
-    int64_t r = 0;
-    int R = nph;
-    for (int j = 0; j < L; ++j) {
-        const int n = occ[j];
-        r += C(R + L - j, L - j) - C(R - n + L - j, L - j);
-        R -= n;
-    }
-    return r;
-}
-
-__host__ __device__ inline void hol_unrank(const Binom& C, int L, int nph, int64_t p, uint8_t* occ)
-{
-    int R = nph;
-    for (int j = 0; j < L; ++j) {
-        const int m = L - 1 - j;
-        int v = 0;
-        while (v < R) {
-            const int64_t cnt = C(R - v + m, m);  // tuples of the last m sites with sum <= R - v
-            if (p < cnt) break;
-            p -= cnt;
-            ++v;
-        }
-        occ[j] = (uint8_t)v;
-        R -= v;
-    }
-}
-
-// ---- on-device construction of the SELL-C (C = 32) matrix ------------------------------------
-struct HolParams {
-    int L, nph, periodic;
-    int64_t dph, n;
-    double t, omega0, g;
-    const double* delta;  // [L] or NULL
-    const double* gsite;  // [L] or NULL
-    Binom C;
-};
 
 // off-diagonal entries of row i in a fixed order: hop to e-1, hop to e+1, phonon up, down
 __device__ inline int hol_row(const HolParams& P, int64_t i, int64_t* col, double* val,
@@ -91,12 +25,11 @@ __device__ inline int hol_row(const HolParams& P, int64_t i, int64_t* col, doubl
 {
     const int e = (int)(i / P.dph);
     const int64_t p = i - (int64_t)e * P.dph;
-    const double ge = P.gsite ? P.gsite[e] : P.g;
     uint8_t occ[HOL_MAX_L];
     hol_unrank(P.C, P.L, P.nph, p, occ);
     int ntot = 0;
     for (int j = 0; j < P.L; ++j) ntot += occ[j];
-    *diag = (P.delta ? P.delta[e] : 0.0) + P.omega0 * (double)ntot;
+    *diag = hol_diag_value(P, e, ntot);
     int cnt = 0;
     int el = e - 1, er = e + 1;
     if (P.periodic) {
@@ -109,14 +42,14 @@ __device__ inline int hol_row(const HolParams& P, int64_t i, int64_t* col, doubl
     if (ntot < P.nph) {
         occ[e] = (uint8_t)(ne + 1);
         col[cnt] = (int64_t)e * P.dph + hol_rank(P.C, P.L, P.nph, occ);
-        val[cnt] = -ge * P.omega0 * sqrt((double)ne + 1.0);
+        val[cnt] = hol_phonon_value(P, e, ne + 1);
         ++cnt;
         occ[e] = (uint8_t)ne;
     }
     if (ne > 0) {
         occ[e] = (uint8_t)(ne - 1);
         col[cnt] = (int64_t)e * P.dph + hol_rank(P.C, P.L, P.nph, occ);
-        val[cnt] = -ge * P.omega0 * sqrt((double)ne);
+        val[cnt] = hol_phonon_value(P, e, ne);
         ++cnt;
         occ[e] = (uint8_t)ne;
     }
@@ -427,5 +360,33 @@ extern "C" int cheb_holstein_unrank(int L, int nph, int64_t idx, uint8_t* occ, i
         return fail(CHEB_ERR_INVALID, "cheb_holstein_unrank: index out of range");
     *e = (int)(idx / dph);
     hol_unrank(C, L, nph, idx - (int64_t)(*e) * dph, occ);
+    return CHEB_OK;
+}
+
+extern "C" int cheb_holstein_phonon_neighbors(int L, int nph, int64_t p0, int64_t count,
+                                              int64_t* up, int64_t* dn)
+{
+    if (!up || !dn || L < 1 || L > HOLMF_MAX_L || nph < 0 || nph > HOLMF_MAX_NPH || p0 < 0 ||
+        count < 0)
+        return fail(CHEB_ERR_INVALID, "cheb_holstein_phonon_neighbors: bad arguments");
+    std::vector<int64_t> tab;
+    if (!make_binom(L, nph, tab)) return fail(CHEB_ERR_INVALID, "cheb_holstein_phonon_neighbors: overflow");
+    const int64_t dph = Binom{tab.data(), L}(nph + L, L);
+    if (dph >= ((int64_t)1 << 31) || p0 + count > dph)
+        return fail(CHEB_ERR_INVALID, "cheb_holstein_phonon_neighbors: ranks out of range");
+    std::vector<int32_t> g;
+    make_hol_g(L, nph, tab, g);
+    const HolG G{g.data(), nph + 1};
+    for (int64_t i = 0; i < count; ++i) {
+        const int64_t p = p0 + i;
+        uint64_t lo, hi;
+        const int ntot = hol_unrank_packed(G, L, nph, p, lo, hi);
+        int64_t* u = up + i * L;
+        int64_t* d = dn + i * L;
+        hol_phonon_walk(G, L, nph, lo, hi, ntot, [&](int e, int, int64_t du, int64_t dd) {
+            u[e] = du ? p + du : -1;
+            d[e] = dd ? p - dd : -1;
+        });
+    }
     return CHEB_OK;
 }

@@ -30,7 +30,7 @@ template <> struct CT<double> { using type = double2; };
 template <> struct CT<float> { using type = float2; };
 
 // ---- operator geometry -------------------------------------------------------------------
-enum OpKind : int { OP_STENCIL = 0, OP_SELL = 1 };
+enum OpKind : int { OP_STENCIL = 0, OP_SELL = 1, OP_HOLMF = 2 };
 
 // One independent Hamiltonian block: a ribbon (W x L brick wall), the 1D grid (W = 1), or
 // the whole Holstein matrix.  Device copy of the per-block scalars used by the kernels.
@@ -140,8 +140,11 @@ int launch_observable(Plan* p, const void* psi, int kind, double param, double* 
                       cudaStream_t s);
 int launch_scale_diag(Plan* p, const double* onsite, cudaStream_t s);
 
-// Holstein (cheb_holstein.cu)
+// Holstein (cheb_holstein.cu: stored SELL matrix; cheb_holmf.cu: matrix-free operator)
 int holstein_build(Plan* p);
+int holmf_build(Plan* p);
+int launch_holmf(Plan* p, const RecArgs& a, cudaStream_t s);
+int launch_holmf_energy(Plan* p, const void* psi, double* out, cudaStream_t s);
 
 // host Bessel (cheb_coeffs.cpp)
 int bessel_j_seq(double z, int kmax, std::vector<double>& J);
@@ -198,6 +201,13 @@ struct Plan {
     int64_t hol_dph = 0;
     int64_t* d_binom = nullptr;       // binomial table for on-device ranking
     uint8_t* d_hol_rowlen = nullptr;  // true off-diagonal count per row (export, energy)
+
+    // matrix-free Holstein operator
+    int32_t* d_holmf_G = nullptr;     // tuple counts G(j, R)
+    void* d_holmf_dtab = nullptr;     // R [L][nph + 1] scaled diagonal by total phonon number
+    void* d_holmf_qtab = nullptr;     // R [L][nph + 1] scaled phonon matrix elements
+    double* d_holmf_partials = nullptr;
+    size_t holmf_partials_cap = 0;
 
     // launch shape
     int threads = 256;
