@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--matrix-free", action="store_true",
                     help="--workload holstein/polaron: matrix-free Holstein operator instead of "
                          "the stored SELL matrix")
+    ap.add_argument("--hol-size", default=None,
+                    help="L:NPH -- Holstein chain size for --workload holstein (profiling runs; "
+                         "default 12:10)")
     ap.add_argument("--blocking", default=None,
                     help="S:SPT -- force S orders per launch with SPT sites per thread and skip "
                          "the autotuner (profiling runs); 0:0 forces single-order launches")
@@ -442,7 +445,11 @@ def _single_setup(args):
                     alpha=0.0, packet=rb.packet())
     if wk == "holstein":
         hs = wl.Holstein()
-        return dict(name="Holstein L=12 periodic, nph<=10 (D=7,759,752), dt=0.25", sites=hs.dim,
+        if args.hol_size:
+            L, nph = (int(x) for x in args.hol_size.split(":"))
+            hs = wl.Holstein(L=L, nph=nph)
+        return dict(name=f"Holstein L={hs.L} periodic, nph<={hs.nph} (D={hs.dim:,}), dt=0.25",
+                    sites=hs.dim,
                     dt=hs.dt, nsteps=hs.nsteps, kind="holstein", obj=hs, bounds=hs.bounds(),
                     alpha=hs.alpha, packet=hs.initial_state())
     if wk == "doublewell":

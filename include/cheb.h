@@ -258,7 +258,9 @@ int cheb_autotune(cheb_plan* plan);
 int cheb_plan_set_blocking(cheb_plan* plan, int orders_per_launch, int sites_per_thread);
 
 /* Launch shape chosen for the plan: threads per block, sites per thread, grid size, and
-   vectors handled per thread (of the nvec at each site). */
+   vectors handled per thread (of the nvec at each site).  Matrix-free Holstein plans report
+   phonon configurations per tile / threads as sites_per_thread and the configurations a
+   thread advances together (1 or 2) in place of vectors per thread. */
 int cheb_plan_launch(const cheb_plan* plan, int* threads, int* sites_per_thread, int* grid,
                      int* vecs_per_thread);
 /* Orders per launch and sites per thread of the temporal blocking in use (0, 0: off). */

@@ -109,8 +109,11 @@ static int set_dt(Plan* p, double dt)
             table.push_back(((k & 3) >= 2) ? -g : g);
             if (std::fabs(g) >= 1.0 / 256.0) ksplit = std::max(ksplit, k);
         }
-        // complex64: orders with |q_k| < 2^-8 go to the tail accumulator
-        B.ksplit = (p->prec == CHEB_C64) ? ksplit : M;
+        // complex64: orders with |q_k| < 2^-8 go to the tail accumulator; the split is raised
+        // to the next order = 2 (mod 3) so that no group of the single-order launches
+        // straddles it
+        ksplit += ((2 - ksplit % 3) + 3) % 3;
+        B.ksplit = (p->prec == CHEB_C64) ? std::min(ksplit, M) : M;
         B.ph_re = std::cos(B.b * dt);
         B.ph_im = -std::sin(B.b * dt);
         maxM = std::max(maxM, M);
@@ -186,13 +189,12 @@ static double launch_bytes(const Plan* p, int k)
         if (k > B.M) continue;
         const double sites = (p->op != OP_STENCIL) ? (double)p->n_sites : (double)B.W * B.L;
         double vecs;  // vectors read + written per site
-        if (k == 1) vecs = 3;            // read psi; write T_0, T_1
-        else if (k == 2) vecs = 4;       // read T_1, T_0; write T_2, psi
-        else {
-            const bool to_tail = k > B.ksplit;
-            vecs = 5;                    // read T_k, T_{k-1}, acc; write T_{k+1}, acc
-            if (to_tail && k == B.ksplit + 1) vecs -= 1;      // tail starts: not read
-            if (to_tail && k == B.M && k > B.ksplit + 1) vecs += 1;  // last: tail and psi read
+        if (k == 1) {
+            vecs = 2;                    // read psi; write T_1
+        } else {
+            const AccGroup ag(k, B.M, B.ksplit);
+            vecs = 3;                    // read T_{k-1}, T_{k-2} (k = 2: psi); write T_k
+            if (ag.upd) vecs += 1 + (ag.read_acc ? 1 : 0) + (ag.read_psi_last ? 1 : 0);
         }
         total += sites * (vecs * cs + ds);
     }
@@ -594,6 +596,8 @@ extern "C" int cheb_plan_create(cheb_plan** out, const cheb_ham_desc* h, const d
             p->n_sites = (int64_t)h->hol_sites * dph;
             if (p->n_sites >= ((int64_t)1 << 31) - 64)
                 return bail(fail(CHEB_ERR_INVALID, "Holstein dimension >= 2^31"));
+            if (h->hol_matrix_free && (uint64_t)p->n_sites * (uint64_t)nvec >= ((uint64_t)1 << 32))
+                return bail(fail(CHEB_ERR_UNSUPPORTED, "matrix-free Holstein needs rows * nvec < 2^32"));
             break;
         }
         default:
@@ -784,6 +788,14 @@ extern "C" int cheb_plan_launch(const cheb_plan* plan, int* threads, int* spt, i
     if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
     if (threads) *threads = p->threads;
     if (spt) *spt = p->spt;
+    if (p->op == OP_HOLMF) {  // tiles of threads * spt phonon configurations; NR per thread
+        const int64_t units = p->hol_dph * p->nvec;
+        const int64_t tile = (int64_t)p->threads * std::max(1, p->spt);
+        const int64_t ntiles = (units + tile - 1) / tile;
+        if (vpt) *vpt = p->holmf_variant == 2 ? 2 : 1;
+        if (grid) *grid = (int)(p->grid_cap > 0 ? std::min<int64_t>(p->grid_cap, ntiles) : ntiles);
+        return CHEB_OK;
+    }
     if (vpt) *vpt = vpt_for(p->prec, p->nvec, p->vpt);
     if (grid) *grid = p->grid_cap > 0 ? std::min<int>(p->grid_cap, (int)p->hitems.size())
                                       : (int)p->hitems.size();
@@ -818,45 +830,54 @@ extern "C" int cheb_autotune(cheb_plan* plan)
     std::vector<int> vpt_c;
     for (int v : {1, 2, 4})
         if (vpt_for(p->prec, p->nvec, v) == v && (p->op != OP_HOLMF || v == 1)) vpt_c.push_back(v);
+    // matrix-free Holstein: its kernel variants (configurations per thread, register cap)
+    std::vector<int> nr_c = {p->holmf_variant};
+    if (p->op == OP_HOLMF) nr_c = {0, 1, 2};
     float best = 1e30f;
-    int bt = p->threads, bs = p->spt, bc = p->grid_cap, bv = p->vpt;
+    int bt = p->threads, bs = p->spt, bc = p->grid_cap, bv = p->vpt, bn = p->holmf_variant;
     int rc = CHEB_OK;
     const int64_t launches0 = p->launches;
-    for (int vpt : vpt_c) {
-        for (int th : th_c) {
-            for (int spt : spt_c) {
-                p->vpt = vpt;
-                p->threads = th;
-                p->spt = spt;
-                rc = plan_build_items(p);
-                if (rc) break;
-                for (int capm : cap_c) {
-                    p->grid_cap = capm ? capm * p->num_sms : 0;
-                    RecArgs a = base_args(p);
-                    a.mode = REC_GENERAL;
-                    a.j = 2;
-                    a.cur = p->d_A;
-                    a.prev = p->d_B;
-                    a.psi = scratch;
-                    float tot = 0.0f;
-                    for (int rep = 0; rep < 4; ++rep) {
-                        cudaEventRecord(e0, p->stream);
-                        rc = launch_recurrence(p, a, p->op, p->prec, p->stream);
-                        cudaEventRecord(e1, p->stream);
+    for (int nr : nr_c) {
+        p->holmf_variant = nr;
+        for (int vpt : vpt_c) {
+            for (int th : th_c) {
+                if (p->op == OP_HOLMF && nr == 1 && th > 256) continue;
+                for (int spt : spt_c) {
+                    p->vpt = vpt;
+                    p->threads = th;
+                    p->spt = spt;
+                    rc = plan_build_items(p);
+                    if (rc) break;
+                    for (int capm : cap_c) {
+                        p->grid_cap = capm ? capm * p->num_sms : 0;
+                        RecArgs a = base_args(p);
+                        a.mode = REC_GENERAL;
+                        a.j = 2;
+                        a.cur = p->d_A;
+                        a.prev = p->d_B;
+                        a.psi = scratch;
+                        float tot = 0.0f;
+                        for (int rep = 0; rep < 4; ++rep) {
+                            cudaEventRecord(e0, p->stream);
+                            rc = launch_recurrence(p, a, p->op, p->prec, p->stream);
+                            cudaEventRecord(e1, p->stream);
+                            if (rc) break;
+                            cudaEventSynchronize(e1);
+                            float ms = 0.0f;
+                            cudaEventElapsedTime(&ms, e0, e1);
+                            if (rep > 0) tot += ms;  // first launch is warm-up
+                        }
                         if (rc) break;
-                        cudaEventSynchronize(e1);
-                        float ms = 0.0f;
-                        cudaEventElapsedTime(&ms, e0, e1);
-                        if (rep > 0) tot += ms;  // first launch is warm-up
+                        if (tot < best) {
+                            best = tot;
+                            bt = th;
+                            bs = spt;
+                            bc = p->grid_cap;
+                            bv = vpt;
+                            bn = nr;
+                        }
                     }
                     if (rc) break;
-                    if (tot < best) {
-                        best = tot;
-                        bt = th;
-                        bs = spt;
-                        bc = p->grid_cap;
-                        bv = vpt;
-                    }
                 }
                 if (rc) break;
             }
@@ -870,6 +891,7 @@ extern "C" int cheb_autotune(cheb_plan* plan)
     p->spt = bs;
     p->grid_cap = bc;
     p->vpt = bv;
+    p->holmf_variant = bn;
     int rc2 = plan_build_items(p);
     if (rc) {
         cudaFree(scratch);

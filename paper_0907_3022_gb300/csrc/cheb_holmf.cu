@@ -4,12 +4,12 @@
 //
 // Rows are e * Dph + r (electron site e, phonon rank r).  One thread takes one phonon
 // configuration r (and one vector) for all L electron sites: it unranks r once and walks
-// e = L-1 .. 0 with hol_phonon_walk, which yields the ranks of n +- 1_e.  Electron hops keep r,
+// e = L-1 .. 0 with HolWalk, which yields the ranks of n +- 1_e.  Electron hops keep r,
 // so the hop terms of row (e, r) are the values the thread loaded for rows (e +- 1, r): every
 // element of T_j is read once, plus the two phonon gathers T_j[e Dph + rank(n +- 1_e)], which
-// stay inside the slab of electron site e.  Per row and order the launch moves
-// T_j, T_{j-1}, T_{j+1} and the accumulator (read and write) and nothing else: no matrix, no
-// stored diagonal (complex64: 40 bytes per row instead of about 70 with the SELL matrix).
+// stay inside the slab of electron site e.  Per row and order the launch moves T_j, T_{j-1}
+// and T_{j+1}, and every third launch the accumulator (read and write, see AccGroup): no
+// matrix and no stored diagonal (complex64: 24 + 16/3 bytes per row and order).
 //
 // The sums are formed in the order of the stored rows (hop to e-1, hop to e+1, phonon up,
 // phonon down, then the diagonal) with the same scaled values, so the stored and the
@@ -28,11 +28,12 @@ namespace cheb {
 struct HolMFArgs {
     int32_t L, nph, periodic, energy_only;
     int64_t dph;
-    const int32_t* G;     // [(L + 1)(nph + 1)], see HolG
+    const int2* G;        // [(L + 1)(nph + 1)], see HolG
     const void* dtab;     // R [L][nph + 1]: 2 (Delta_e + w0 s - b)/a, s = total phonon number
     const void* qtab;     // R [L][nph + 1]: 2 (-g_e w0 sqrt(m))/a
-    int64_t tile_units;   // (phonon configuration, vector) pairs per tile
+    uint32_t tile_units;  // (phonon configuration, vector) pairs per tile
     int32_t ntiles;
+    int32_t log2_nvec;
     double* energy_out;   // energy_only: <psi|H|psi> per vector
 };
 
@@ -74,12 +75,18 @@ __device__ void holmf_finalize(const RecArgs& a, const HolMFArgs& m, const DevBl
     if (threadIdx.x == 0) *a.done_counter = 0u;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(512) k_rec_holmf(RecArgs a, HolMFArgs m)
+// One launch of the recurrence for the mode MODE (REC_FIRST / REC_SECOND / REC_GENERAL);
+// each thread advances NR phonon configurations in lockstep (NR = 2 doubles the loads in
+// flight per thread).  MINB > 1 caps the registers so that MINB blocks of 256 threads fit
+// on an SM (more warps to hide the gather latency; launches then use <= 256 threads).
+template <typename R, int MODE, int NR, int MINB>
+__global__ void __launch_bounds__(MINB > 1 ? 256 : 512, MINB) k_rec_holmf(RecArgs a, HolMFArgs m)
 {
     using C = typename V2<R>::C;
     using U = SiteUpdate<R>;
-    __shared__ int32_t sG[(HOLMF_MAX_L + 1) * (HOLMF_MAX_NPH + 1)];
+    constexpr bool FIRST = (MODE == REC_FIRST);
+    constexpr bool SECOND = (MODE == REC_SECOND);
+    __shared__ int2 sG[(HOLMF_MAX_L + 1) * (HOLMF_MAX_NPH + 1)];
     __shared__ R sD[HOLMF_MAX_L * (HOLMF_MAX_NPH + 1)];
     __shared__ R sQ[HOLMF_MAX_L * (HOLMF_MAX_NPH + 1)];
     __shared__ double s_red[16 * 32 * 2 + 2];
@@ -91,10 +98,12 @@ __global__ void __launch_bounds__(512) k_rec_holmf(RecArgs a, HolMFArgs m)
     }
     __syncthreads();
     const HolG G{sG, w};
-    const int nv = a.nvec;
+    const int nv = a.nvec, lnv = m.log2_nvec;
     const int L = m.L, nph = m.nph;
     const bool periodic = m.periodic != 0;
-    const int64_t es = m.dph * nv;  // distance between the rows of neighbouring electron sites
+    // element offsets fit 32 bits (rows * nvec < 2^32 is checked at plan creation)
+    const uint32_t units = (uint32_t)m.dph << lnv;
+    const uint32_t es = units;  // distance between the rows of neighbouring electron sites
     const C* __restrict__ cur = static_cast<const C*>(a.cur);
     C* __restrict__ prev = static_cast<C*>(a.prev);
     C* __restrict__ out1 = static_cast<C*>(a.out1);
@@ -103,112 +112,121 @@ __global__ void __launch_bounds__(512) k_rec_holmf(RecArgs a, HolMFArgs m)
     const C* __restrict__ qc = static_cast<const C*>(a.qcoef);
     const DevBlock B = a.blocks[0];
     const int k = a.j + 1;
-    const bool first = (a.mode == REC_FIRST);
     const bool store = !m.energy_only;
     const R beta = (R)B.beta;
     const C zero = V2<R>::make(0, 0);
-    C qk = zero, q0 = zero, q1 = zero, ph = zero, pl = zero;
-    bool last = false, to_tail = false, read_psi = false, read_tail = false, read_psi_last = false;
-    if (!first) {
+    const AccGroup ag(FIRST ? 1 : k, B.M, B.ksplit);
+    C qm2 = zero, qm1 = zero, qk = zero, ph = zero, pl = zero;
+    if (!FIRST) {
         qk = qc[B.coef_off + k];
-        if (a.mode == REC_SECOND) {
-            q0 = qc[B.coef_off + 0];
-            q1 = qc[B.coef_off + 1];
-        }
-        last = (k == B.M);
+        if (ag.n >= 2) qm1 = qc[B.coef_off + k - 1];
+        if (ag.n >= 3) qm2 = qc[B.coef_off + k - 2];
         split_const<R>(B.ph_re, ph.x, pl.x);
         split_const<R>(B.ph_im, ph.y, pl.y);
-        to_tail = k > B.ksplit;
-        const bool gen = (a.mode == REC_GENERAL);
-        read_psi = gen && !to_tail;
-        read_tail = gen && to_tail && (k > B.ksplit + 1);
-        read_psi_last = last && to_tail;
     }
-    const int64_t units = m.dph * nv;
+    C* __restrict__ accp = ag.to_tail ? tail : psi;
     for (int t = blockIdx.x; t < m.ntiles; t += gridDim.x) {
         R part0 = 0, part1 = 0;
-        const int64_t u1 = min((int64_t)(t + 1) * m.tile_units, units);
-        for (int64_t u = (int64_t)t * m.tile_units + threadIdx.x; u < u1; u += blockDim.x) {
-            const int64_t r = u / nv;
-            const int v = (int)(u - r * nv);
-            uint64_t lo, hi;
-            const int ntot = hol_unrank_packed(G, L, nph, r, lo, hi);
-            const int64_t col = r * nv + v;  // element (e, r, v) at e * es + col
-            const C xlast = cur[(int64_t)(L - 1) * es + col];
-            C xr = periodic ? cur[col] : zero;  // T_j at e + 1 (e = L-1: site 0 if periodic)
-            C xc = xlast;                        // T_j at e
-            hol_phonon_walk(G, L, nph, lo, hi, ntot, [&](int e, int ne, int64_t up, int64_t dn) {
-                const int64_t base = (int64_t)e * es + col;
-                C xl = zero;  // T_j at e - 1 (e = 0: site L-1 if periodic)
-                if (e > 0) xl = cur[base - es];
-                else if (periodic) xl = xlast;
-                C p = zero, acc = zero, ps = zero, xu = zero, xd = zero;
-                if (!first) p = prev[base];
-                if (read_psi) acc = psi[base];
-                else if (read_tail) acc = tail[base];
-                if (read_psi_last) ps = psi[base];
-                if (up) xu = cur[base + up * nv];
-                if (dn) xd = cur[base - dn * nv];
-                // h = 2 H~ x - p, terms in the stored-row order
-                C h = V2<R>::make(-p.x, -p.y);
-                if (e > 0 || periodic) {
-                    h.x = fma(beta, xl.x, h.x);
-                    h.y = fma(beta, xl.y, h.y);
+        const uint32_t ub = (uint32_t)t * m.tile_units;
+        const uint32_t u1 = min(ub + m.tile_units, units);
+        for (uint32_t u0 = ub + threadIdx.x; u0 < u1; u0 += NR * blockDim.x) {
+            // unit u = r * nvec + v is also the offset of element (e = 0, r, v)
+            HolWalk W[NR];
+            uint32_t col[NR];
+            bool ok[NR];
+            C xr[NR], xc[NR], xlast[NR];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const uint32_t u = u0 + i * blockDim.x;
+                ok[i] = u < u1;
+                col[i] = ok[i] ? u : u0;  // a missing configuration repeats the first, unstored
+                W[i].begin(G, L, nph, (int32_t)(col[i] >> lnv));
+                xlast[i] = cur[(uint32_t)(L - 1) * es + col[i]];
+                xr[i] = periodic ? cur[col[i]] : zero;  // T_j at e + 1 (e = L-1: site 0)
+                xc[i] = xlast[i];                        // T_j at e
+            }
+            for (int e = L - 1; e >= 0; --e) {
+                C xl[NR], p[NR], acc[NR], ps[NR], xu[NR], xd[NR];
+                int ne[NR];
+                // every load of this electron site first
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    int32_t up, dn;
+                    ne[i] = W[i].step(G, L, nph, e, up, dn);
+                    const uint32_t base = (uint32_t)e * es + col[i];
+                    xl[i] = (e > 0) ? cur[base - es] : (periodic ? xlast[i] : zero);
+                    p[i] = FIRST ? zero : (SECOND ? psi[base] : prev[base]);  // T_{k-2}
+                    acc[i] = ag.read_acc ? accp[base] : zero;
+                    ps[i] = ag.read_psi_last ? psi[base] : zero;
+                    xu[i] = up ? cur[base + ((uint32_t)up << lnv)] : zero;
+                    xd[i] = dn ? cur[base - ((uint32_t)dn << lnv)] : zero;
+                    if (!up) ne[i] |= 1 << 8;  // flags: no raising / no lowering term
+                    if (!dn) ne[i] |= 1 << 9;
                 }
-                if (e + 1 < L || periodic) {
-                    h.x = fma(beta, xr.x, h.x);
-                    h.y = fma(beta, xr.y, h.y);
-                }
-                if (up) {
-                    const R qv = sQ[e * w + ne + 1];
-                    h.x = fma(qv, xu.x, h.x);
-                    h.y = fma(qv, xu.y, h.y);
-                }
-                if (dn) {
-                    const R qv = sQ[e * w + ne];
-                    h.x = fma(qv, xd.x, h.x);
-                    h.y = fma(qv, xd.y, h.y);
-                }
-                const R d = sD[e * w + ntot];
-                h.x = fma(d, xc.x, h.x);
-                h.y = fma(d, xc.y, h.y);
-                if (first) {
-                    const C t1 = V2<R>::make((R)0.5 * h.x, (R)0.5 * h.y);
-                    part0 = fma(xc.x, xc.x, fma(xc.y, xc.y, part0));
-                    part1 = fma(xc.x, t1.x, fma(xc.y, t1.y, part1));
-                    if (store) {
-                        prev[base] = xc;
-                        out1[base] = t1;
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    const uint32_t base = (uint32_t)e * es + col[i];
+                    const int n_e = ne[i] & 255;
+                    // h = 2 H~ x - p, terms in the stored-row order
+                    C h = V2<R>::make(-p[i].x, -p[i].y);
+                    if (e > 0 || periodic) {
+                        h.x = fma(beta, xl[i].x, h.x);
+                        h.y = fma(beta, xl[i].y, h.y);
                     }
-                } else {
-                    prev[base] = h;  // T_{j+1} over T_{j-1}
-                    if (a.mode == REC_SECOND) {
-                        U::accum(acc, q0, p, 0);
-                        U::accum(acc, q1, xc, 1);
-                        U::accum(acc, qk, h, 2);
-                    } else {
-                        U::accum(acc, qk, h, k);
+                    if (e + 1 < L || periodic) {
+                        h.x = fma(beta, xr[i].x, h.x);
+                        h.y = fma(beta, xr[i].y, h.y);
                     }
-                    if (last) {
-                        if (read_psi_last) acc = V2<R>::make(ps.x + acc.x, ps.y + acc.y);
-                        acc = U::phase(acc, ph, pl);
-                        const double t2 = (double)h.x * h.x + (double)h.y * h.y;
-                        if (!(t2 <= 4.0 * a.norm2[(size_t)v * 2])) atomicOr(a.errflag, 1);
-                        psi[base] = acc;
-                    } else {
-                        (to_tail ? tail : psi)[base] = acc;
+                    if (!(ne[i] & (1 << 8))) {
+                        const R qv = sQ[e * w + n_e + 1];
+                        h.x = fma(qv, xu[i].x, h.x);
+                        h.y = fma(qv, xu[i].y, h.y);
                     }
+                    if (!(ne[i] & (1 << 9))) {
+                        const R qv = sQ[e * w + n_e];
+                        h.x = fma(qv, xd[i].x, h.x);
+                        h.y = fma(qv, xd[i].y, h.y);
+                    }
+                    const R d = sD[e * w + W[i].ntot];
+                    h.x = fma(d, xc[i].x, h.x);
+                    h.y = fma(d, xc[i].y, h.y);
+                    if (FIRST) {
+                        const C t1 = V2<R>::make((R)0.5 * h.x, (R)0.5 * h.y);
+                        if (ok[i]) {
+                            part0 = fma(xc[i].x, xc[i].x, fma(xc[i].y, xc[i].y, part0));
+                            part1 = fma(xc[i].x, t1.x, fma(xc[i].y, t1.y, part1));
+                            if (store) out1[base] = t1;
+                        }
+                    } else if (ok[i]) {
+                        prev[base] = h;  // T_k over T_{k-2}
+                        if (ag.upd) {
+                            C ac = acc[i];
+                            if (ag.n >= 3) U::accum(ac, qm2, p[i], k - 2);
+                            if (ag.n >= 2) U::accum(ac, qm1, xc[i], k - 1);
+                            U::accum(ac, qk, h, k);
+                            if (ag.last) {
+                                if (ag.read_psi_last) ac = V2<R>::make(ps[i].x + ac.x, ps[i].y + ac.y);
+                                ac = U::phase(ac, ph, pl);
+                                const double t2 = (double)h.x * h.x + (double)h.y * h.y;
+                                const int v = (int)(col[i] & (nv - 1));
+                                if (!(t2 <= 4.0 * a.norm2[(size_t)v * 2])) atomicOr(a.errflag, 1);
+                                psi[base] = ac;
+                            } else {
+                                accp[base] = ac;
+                            }
+                        }
+                    }
+                    xr[i] = xc[i];
+                    xc[i] = xl[i];
                 }
-                xr = xc;
-                xc = xl;
-            });
+            }
         }
-        if (first) {
+        if (FIRST) {
             double dpart[2] = {(double)part0, (double)part1};
             block_reduce_groups<2>(dpart, nv, s_red, a.partials + (size_t)t * nv * 2);
         }
     }
-    if (first) holmf_finalize(a, m, B, s_red);
+    if (FIRST) holmf_finalize(a, m, B, s_red);
 }
 
 // scaled tables from the same matrix elements as the stored rows
@@ -233,10 +251,10 @@ int holmf_build(Plan* p)
     CHEB_CUDA(cudaMalloc(&p->d_binom, tab.size() * sizeof(int64_t)));
     CHEB_CUDA(cudaMemcpy(p->d_binom, tab.data(), tab.size() * sizeof(int64_t),
                          cudaMemcpyHostToDevice));
-    std::vector<int32_t> g;
+    std::vector<int2> g;
     make_hol_g(L, nph, tab, g);
-    CHEB_CUDA(cudaMalloc(&p->d_holmf_G, g.size() * sizeof(int32_t)));
-    CHEB_CUDA(cudaMemcpy(p->d_holmf_G, g.data(), g.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CHEB_CUDA(cudaMalloc(&p->d_holmf_G, g.size() * sizeof(int2)));
+    CHEB_CUDA(cudaMemcpy(p->d_holmf_G, g.data(), g.size() * sizeof(int2), cudaMemcpyHostToDevice));
     const size_t nt = (size_t)L * (nph + 1);
     CHEB_CUDA(cudaMalloc(&p->d_holmf_dtab, nt * p->real_size()));
     CHEB_CUDA(cudaMalloc(&p->d_holmf_qtab, nt * p->real_size()));
@@ -271,6 +289,25 @@ int holmf_build(Plan* p)
     return CHEB_OK;
 }
 
+template <typename R, int NR, int MINB>
+static void launch_nr(const RecArgs& a, const HolMFArgs& m, int grid, int th, cudaStream_t s)
+{
+    if (a.mode == REC_FIRST) k_rec_holmf<R, REC_FIRST, NR, MINB><<<grid, th, 0, s>>>(a, m);
+    else if (a.mode == REC_SECOND) k_rec_holmf<R, REC_SECOND, NR, MINB><<<grid, th, 0, s>>>(a, m);
+    else k_rec_holmf<R, REC_GENERAL, NR, MINB><<<grid, th, 0, s>>>(a, m);
+}
+
+// variants: 0 = one configuration per thread, 1 = the same with 5 blocks of 256 threads
+// per SM, 2 = two configurations per thread
+template <typename R>
+static void launch_modes(const RecArgs& a, const HolMFArgs& m, int variant, int grid, int th,
+                         cudaStream_t s)
+{
+    if (variant == 2) launch_nr<R, 2, 1>(a, m, grid, th, s);
+    else if (variant == 1) launch_nr<R, 1, 5>(a, m, grid, th, s);
+    else launch_nr<R, 1, 1>(a, m, grid, th, s);
+}
+
 static int holmf_launch(Plan* p, const RecArgs& a0, double* energy_out, cudaStream_t s)
 {
     HolMFArgs m{};
@@ -283,21 +320,24 @@ static int holmf_launch(Plan* p, const RecArgs& a0, double* energy_out, cudaStre
     m.dtab = p->d_holmf_dtab;
     m.qtab = p->d_holmf_qtab;
     const int th = p->threads;
-    m.tile_units = (int64_t)th * std::max(1, p->spt);
+    m.tile_units = (uint32_t)(th * std::max(1, p->spt));
     const int64_t units = p->hol_dph * p->nvec;
     const int64_t ntiles = (units + m.tile_units - 1) / m.tile_units;
     if ((size_t)ntiles * p->nvec * 2 > p->holmf_partials_cap || ntiles > INT32_MAX)
         return fail(CHEB_ERR_INVALID, "matrix-free Holstein: tile count exceeds the partials buffer");
     m.ntiles = (int32_t)ntiles;
     m.energy_out = energy_out;
+    m.log2_nvec = 0;
+    while ((1 << m.log2_nvec) < p->nvec) ++m.log2_nvec;
     RecArgs a = a0;
     a.partials = p->d_holmf_partials;
     int grid = (int)ntiles;
     if (p->grid_cap > 0 && grid > p->grid_cap) grid = p->grid_cap;
-    if (p->prec == CHEB_C128)
-        k_rec_holmf<double><<<grid, th, 0, s>>>(a, m);
-    else
-        k_rec_holmf<float><<<grid, th, 0, s>>>(a, m);
+    const int variant = p->holmf_variant;
+    if (variant == 1 && th > 256)
+        return fail(CHEB_ERR_INVALID, "matrix-free Holstein: variant 1 needs <= 256 threads");
+    if (p->prec == CHEB_C128) launch_modes<double>(a, m, variant, grid, th, s);
+    else launch_modes<float>(a, m, variant, grid, th, s);
     p->launches++;
     CHEB_CUDA(cudaGetLastError());
     return CHEB_OK;

@@ -374,19 +374,19 @@ extern "C" int cheb_holstein_phonon_neighbors(int L, int nph, int64_t p0, int64_
     const int64_t dph = Binom{tab.data(), L}(nph + L, L);
     if (dph >= ((int64_t)1 << 31) || p0 + count > dph)
         return fail(CHEB_ERR_INVALID, "cheb_holstein_phonon_neighbors: ranks out of range");
-    std::vector<int32_t> g;
+    std::vector<int2> g;
     make_hol_g(L, nph, tab, g);
     const HolG G{g.data(), nph + 1};
     for (int64_t i = 0; i < count; ++i) {
         const int64_t p = p0 + i;
-        uint64_t lo, hi;
-        const int ntot = hol_unrank_packed(G, L, nph, p, lo, hi);
-        int64_t* u = up + i * L;
-        int64_t* d = dn + i * L;
-        hol_phonon_walk(G, L, nph, lo, hi, ntot, [&](int e, int, int64_t du, int64_t dd) {
-            u[e] = du ? p + du : -1;
-            d[e] = dd ? p - dd : -1;
-        });
+        HolWalk W;
+        W.begin(G, L, nph, (int32_t)p);
+        for (int e = L - 1; e >= 0; --e) {
+            int32_t du, dd;
+            W.step(G, L, nph, e, du, dd);
+            up[i * L + e] = du ? p + du : -1;
+            dn[i * L + e] = dd ? p - dd : -1;
+        }
     }
     return CHEB_OK;
 }

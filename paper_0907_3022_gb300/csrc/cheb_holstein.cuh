@@ -108,29 +108,31 @@ __host__ __device__ inline double hol_phonon_value(const HolParams& P, int e, in
 constexpr int HOLMF_MAX_L = 32;
 constexpr int HOLMF_MAX_NPH = 15;
 
-// G(j, R) at t[j * w + R], j in [0, L], R in [0, nph], w = nph + 1 (values < 2^31)
+// Tuple counts of the walk: G(j, R) = C(R + L - j, L - j), stored as the pair
+// (G(j, R - 1), G(j, R)) at t[j * w + R] (G(j, -1) = 0), j in [0, L], R in [0, nph],
+// w = nph + 1.  Every value is below Dph < 2^31.
 struct HolG {
-    const int32_t* t;
+    const int2* t;
     int w;
-    __host__ __device__ int64_t operator()(int j, int R) const { return t[j * w + R]; }
+    __host__ __device__ int2 pair(int j, int R) const { return t[j * w + R]; }
+    __host__ __device__ int32_t operator()(int j, int R) const { return t[j * w + R].y; }
 };
 
-inline void make_hol_g(int L, int nph, const std::vector<int64_t>& binom, std::vector<int32_t>& g)
+inline void make_hol_g(int L, int nph, const std::vector<int64_t>& binom, std::vector<int2>& g)
 {
     Binom C{binom.data(), L};
-    g.assign((size_t)(L + 1) * (nph + 1), 0);
+    const int w = nph + 1;
+    g.assign((size_t)(L + 1) * w, make_int2(0, 0));
     for (int j = 0; j <= L; ++j)
-        for (int R = 0; R <= nph; ++R) g[(size_t)j * (nph + 1) + R] = (int32_t)C(R + L - j, L - j);
+        for (int R = 0; R <= nph; ++R)
+            g[(size_t)j * w + R] = make_int2(R > 0 ? (int32_t)C(R - 1 + L - j, L - j) : 0,
+                                             (int32_t)C(R + L - j, L - j));
 }
 
-__host__ __device__ inline int hol_occ(uint64_t lo, uint64_t hi, int j)
-{
-    return (int)(((j < 16) ? (lo >> (4 * j)) : (hi >> (4 * (j - 16)))) & 15u);
-}
-
-// occupations of phonon rank p (packed) and their sum
+// Occupations of phonon rank p, packed 4 bits per site with site L-1 in the lowest bits of
+// lo (sites L-17 .. 0 continue in hi), and their sum.
 template <class GT>
-__host__ __device__ inline int hol_unrank_packed(const GT& G, int L, int nph, int64_t p,
+__host__ __device__ inline int hol_unrank_packed(const GT& G, int L, int nph, int32_t p,
                                                  uint64_t& lo, uint64_t& hi)
 {
     lo = 0;
@@ -139,36 +141,49 @@ __host__ __device__ inline int hol_unrank_packed(const GT& G, int L, int nph, in
     for (int j = 0; j < L; ++j) {
         int v = 0;
         while (v < R) {
-            const int64_t cnt = G(j + 1, R - v);  // tuples of sites j+1.. with sum <= R - v
+            const int32_t cnt = G(j + 1, R - v);  // tuples of sites j+1.. with sum <= R - v
             if (p < cnt) break;
             p -= cnt;
             ++v;
         }
-        if (j < 16) lo |= (uint64_t)v << (4 * j);
-        else hi |= (uint64_t)v << (4 * (j - 16));
+        const int q = L - 1 - j;
+        if (q < 16) lo |= (uint64_t)v << (4 * q);
+        else hi |= (uint64_t)v << (4 * (q - 16));
         R -= v;
     }
     return nph - R;
 }
 
-// f(e, n_e, up, dn) for e = L-1 down to 0, with up = rank(n + 1_e) - rank(n) (0 when
-// sum n = nph) and dn = rank(n) - rank(n - 1_e) (0 when n_e = 0)
-template <class GT, class F>
-__host__ __device__ inline void hol_phonon_walk(const GT& G, int L, int nph, uint64_t lo,
-                                                uint64_t hi, int ntot, F&& f)
-{
-    int64_t su = 0, sd = 0;
-    int after = 0;  // sum of n_j over j > e
-    for (int e = L - 1; e >= 0; --e) {
-        if (e + 1 < L) {
-            const int Rn = nph - ntot + after;  // R_{e+1}
-            sd += G(e + 1, Rn);
-            if (Rn >= 1) su += G(e + 1, Rn - 1);
-        }
-        const int ne = hol_occ(lo, hi, e);
-        f(e, ne, ntot < nph ? 1 + su : (int64_t)0, ne > 0 ? 1 + sd : (int64_t)0);
-        after += ne;
+// Walk over the electron sites e = L-1, L-2, ..., 0 of one phonon configuration n: step(e)
+// returns n_e and the offsets up = rank(n + 1_e) - rank(n) (0 when sum n = nph) and
+// dn = rank(n) - rank(n - 1_e) (0 when n_e = 0).  Offsets are below Dph < 2^31.
+struct HolWalk {
+    uint64_t lo, hi;   // occupations still to visit, the next one in the lowest 4 bits
+    int ntot, after;   // total phonon number; sum of n_j over the sites already passed (j > e)
+    int32_t su, sd;    // sum_{j > e} G(j, R_j - 1) and G(j, R_j)
+
+    template <class GT>
+    __host__ __device__ void begin(const GT& G, int L, int nph, int32_t p) {
+        ntot = hol_unrank_packed(G, L, nph, p, lo, hi);
+        after = 0;
+        su = 0;
+        sd = 0;
     }
-}
+    template <class GT>
+    __host__ __device__ int step(const GT& G, int L, int nph, int e, int32_t& up, int32_t& dn) {
+        if (e + 1 < L) {
+            const int2 g = G.pair(e + 1, nph - ntot + after);  // at R_{e+1}
+            su += g.x;
+            sd += g.y;
+        }
+        const int ne = (int)(lo & 15u);
+        lo = (lo >> 4) | (hi << 60);
+        hi >>= 4;
+        up = ntot < nph ? 1 + su : 0;
+        dn = ne > 0 ? 1 + sd : 0;
+        after += ne;
+        return ne;
+    }
+};
 
 }  // namespace cheb

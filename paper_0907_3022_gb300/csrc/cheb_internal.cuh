@@ -54,6 +54,31 @@ struct WorkItem {
     int64_t count;  // sites in the tile
 };
 
+// Accumulation of psi in groups of orders (Eq. U_1).  The launch forming T_k adds to the
+// accumulator only when k = 2 (mod 3) or k = M, and then adds every order formed since the
+// previous such launch: T_{k-2}, T_{k-1}, T_k (the three recurrence vectors it holds), or
+// the last one or two orders at k = M.  The terms are added in increasing order, so the sum
+// is the same as adding each order when it is formed, for a third of the accumulator
+// traffic.  complex64 plans keep the orders above ksplit (a value = 2 mod 3, or M) in the
+// tail accumulator, so a group never straddles ksplit.
+struct AccGroup {
+    bool upd;            // this launch updates an accumulator
+    bool last;           // k = M: psi receives its final value
+    bool to_tail;        // the group goes to the tail accumulator
+    bool read_acc;       // the accumulator already holds earlier groups
+    bool read_psi_last;  // last group of a tail: psi + (tail + group)
+    int n;               // orders in the group (1, 2 or 3)
+    __host__ __device__ AccGroup(int k, int M, int ksplit) {
+        last = (k == M);
+        upd = (k >= 2) && (k % 3 == 2 || last);
+        const int uprev = 3 * (k / 3) - 1;  // previous updating launch (-1: none)
+        n = upd ? k - uprev : 0;
+        to_tail = upd && uprev >= ksplit;
+        read_acc = upd && (to_tail ? uprev >= ksplit + 3 : uprev >= 2);
+        read_psi_last = last && to_tail;
+    }
+};
+
 // Recurrence launch arguments (one launch = one order j, producing T_{j+1}).
 enum RecMode : int { REC_FIRST = 0, REC_SECOND = 1, REC_GENERAL = 2 };
 
@@ -203,11 +228,13 @@ struct Plan {
     uint8_t* d_hol_rowlen = nullptr;  // true off-diagonal count per row (export, energy)
 
     // matrix-free Holstein operator
-    int32_t* d_holmf_G = nullptr;     // tuple counts G(j, R)
+    int2* d_holmf_G = nullptr;        // tuple-count pairs (G(j, R - 1), G(j, R))
     void* d_holmf_dtab = nullptr;     // R [L][nph + 1] scaled diagonal by total phonon number
     void* d_holmf_qtab = nullptr;     // R [L][nph + 1] scaled phonon matrix elements
     double* d_holmf_partials = nullptr;
     size_t holmf_partials_cap = 0;
+    int holmf_variant = 0;            // 0, 1: one phonon configuration per thread
+                                      // (1: register cap); 2: two
 
     // launch shape
     int threads = 256;

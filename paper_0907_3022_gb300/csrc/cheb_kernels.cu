@@ -1,12 +1,14 @@
 // Fused Chebyshev recurrence kernel (Sec. 2.2, Eqs. U_1 and rec) and FP64 reductions.
 //
 // One launch forms T_{j+1} for every block whose order M reaches j+1:
-//   FIRST   (j = 0):  T_1 = H~ psi                    -> A = psi, B = T_1
+//   FIRST   (j = 0):  T_1 = H~ psi                    -> B = T_1
 //                     and per (block, vec) ||psi||^2, <psi|H~ psi>   (deterministic FP64)
-//   SECOND  (j = 1):  T_2 = 2 H~ T_1 - T_0            -> A = T_2,
-//                     psi = q_0 T_0 + q_1' T_1 + q_2 T_2          (psi written, not read)
-//   GENERAL (j >= 2): T_{j+1} = 2 H~ T_j - T_{j-1}     -> over T_{j-1},
-//                     psi += q'_{j+1} T_{j+1};  at j+1 = M: psi *= e^{-i b dt}
+//   SECOND  (j = 1):  T_2 = 2 H~ T_1 - T_0 (T_0 = psi) -> A = T_2,
+//                     psi = q_0 T_0 + q_1' T_1 + q_2 T_2
+//   GENERAL (j >= 2): T_{j+1} = 2 H~ T_j - T_{j-1}     -> over T_{j-1};
+//                     at j+1 = 2 (mod 3): psi += q'_{j-1} T_{j-1} + q'_j T_j + q'_{j+1} T_{j+1};
+//                     at j+1 = M: the orders left, then psi *= e^{-i b dt}
+// (the accumulator is touched by every third launch, see AccGroup).
 // complex64 plans send the orders with |q_k| < 2^-8 (k > ksplit) to a second accumulator
 // "tail" and add it to psi at the last order: added straight into psi, terms smaller than
 // half an ulp of psi would be rounded away every time, which truncates the series early
@@ -18,7 +20,7 @@
 // d_i x_i + sum_j v_ij x_j with v_ij = 2 H_ij / a stored in SELL-C order (Holstein).
 //
 // Memory per site and order (GENERAL, one vector): read T_j (+ neighbours, from cache),
-// T_{j-1}, d_i, psi; write T_{j+1}, psi.
+// T_{j-1}, d_i; write T_{j+1}; every third order also read and write psi.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -144,6 +146,7 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
     const C* __restrict__ qc = static_cast<const C*>(a.qcoef);  // (hi, lo) per k
     const int k = a.j + 1;  // order formed by this launch
     const bool first = (a.mode == REC_FIRST);
+    const bool second = (a.mode == REC_SECOND);
 
     for (int w = blockIdx.x; w < a.nitems; w += gridDim.x) {
         const WorkItem it = a.items[w];
@@ -158,22 +161,17 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
             Op<R, VPT> op;
             op.init(a, B);
             const int64_t units = it.count * nvg;  // (site, vector group) pairs in the tile
-            const C qk = qc[B.coef_off + k];
-            C q0 = V2<R>::make(0, 0), q1 = V2<R>::make(0, 0);
-            if (a.mode == REC_SECOND) {
-                q0 = qc[B.coef_off + 0];
-                q1 = qc[B.coef_off + 1];
+            const AccGroup ag(k, B.M, B.ksplit);
+            C qm2 = V2<R>::make(0, 0), qm1 = qm2, qk = qm2;
+            if (!first) {
+                qk = qc[B.coef_off + k];
+                if (ag.n >= 2) qm1 = qc[B.coef_off + k - 1];
+                if (ag.n >= 3) qm2 = qc[B.coef_off + k - 2];
             }
-            const bool last = (k == B.M);
             C ph, pl;
             split_const<R>(B.ph_re, ph.x, pl.x);
             split_const<R>(B.ph_im, ph.y, pl.y);
-            const bool to_tail = k > B.ksplit;
-            const bool gen = (a.mode == REC_GENERAL);
-            // accumulator read by this launch: psi (k <= ksplit), tail (k > ksplit + 1), none
-            const bool read_psi = gen && !to_tail;
-            const bool read_tail = gen && to_tail && (k > B.ksplit + 1);
-            const bool read_psi_last = last && to_tail;  // last order: psi + tail
+            C* __restrict__ accp = ag.to_tail ? tail : psi;
             for (int64_t u = threadIdx.x; u < units; u += blockDim.x) {
                 const int64_t sl = it.first + u / nvg;  // site (row) within the block
                 const int g = (int)(u % nvg);
@@ -187,17 +185,15 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
 #pragma unroll
                     for (int v = 0; v < VPT; ++v) p[v] = V2<R>::make(0, 0);
                 } else {
-                    IO::load(prev + base, p);
+                    IO::load((second ? psi : prev) + base, p);  // T_{k-2} (SECOND: T_0 = psi)
                 }
-                if (read_psi) {
-                    IO::load(psi + base, acc);
-                } else if (read_tail) {
-                    IO::load(tail + base, acc);
+                if (ag.read_acc) {
+                    IO::load(accp + base, acc);
                 } else {
 #pragma unroll
                     for (int v = 0; v < VPT; ++v) acc[v] = V2<R>::make(0, 0);
                 }
-                if (read_psi_last) IO::load(psi + base, ps);
+                if (ag.read_psi_last) IO::load(psi + base, ps);
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) d[v] = a.diag_per_vec ? diag[base + v] : diag[gs];
                 // h = 2 H~ x - p  (FIRST: p = 0)
@@ -218,37 +214,33 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
                         part[2 * v + 0] = fma(x[v].x, x[v].x, fma(x[v].y, x[v].y, part[2 * v + 0]));
                         part[2 * v + 1] = fma(x[v].x, t1[v].x, fma(x[v].y, t1[v].y, part[2 * v + 1]));
                     }
-                    IO::store(prev + base, x);
                     IO::store(out1 + base, t1);
                 } else {
-                    IO::store(prev + base, h);  // T_{j+1} over T_{j-1}
-                    if (a.mode == REC_SECOND) {  // k = 2 <= ksplit
+                    IO::store(prev + base, h);  // T_k over T_{k-2}
+                    if (ag.upd) {
 #pragma unroll
                         for (int v = 0; v < VPT; ++v) {
-                            U::accum(acc[v], q0, p[v], 0);  // T_0
-                            U::accum(acc[v], q1, x[v], 1);  // T_1
-                            U::accum(acc[v], qk, h[v], 2);  // T_2
+                            if (ag.n >= 3) U::accum(acc[v], qm2, p[v], k - 2);
+                            if (ag.n >= 2) U::accum(acc[v], qm1, x[v], k - 1);
+                            U::accum(acc[v], qk, h[v], k);
                         }
-                    } else {
+                        if (ag.last) {
+                            if (ag.read_psi_last) {  // psi + (tail + newest orders)
 #pragma unroll
-                        for (int v = 0; v < VPT; ++v) U::accum(acc[v], qk, h[v], k);
-                    }
-                    if (last) {
-                        if (read_psi_last) {  // psi + (tail + q_M T_M)
+                                for (int v = 0; v < VPT; ++v)
+                                    acc[v] = V2<R>::make(ps[v].x + acc[v].x, ps[v].y + acc[v].y);
+                            }
 #pragma unroll
-                            for (int v = 0; v < VPT; ++v)
-                                acc[v] = V2<R>::make(ps[v].x + acc[v].x, ps[v].y + acc[v].y);
+                            for (int v = 0; v < VPT; ++v) {
+                                acc[v] = U::phase(acc[v], ph, pl);
+                                const double t2 = (double)h[v].x * h[v].x + (double)h[v].y * h[v].y;
+                                const double lim = 4.0 * a.norm2[((size_t)it.block * nv + g * VPT + v) * 2];
+                                if (!(t2 <= lim)) atomicOr(a.errflag, 1);
+                            }
+                            IO::store(psi + base, acc);
+                        } else {
+                            IO::store(accp + base, acc);
                         }
-#pragma unroll
-                        for (int v = 0; v < VPT; ++v) {
-                            acc[v] = U::phase(acc[v], ph, pl);
-                            const double t2 = (double)h[v].x * h[v].x + (double)h[v].y * h[v].y;
-                            const double lim = 4.0 * a.norm2[((size_t)it.block * nv + g * VPT + v) * 2];
-                            if (!(t2 <= lim)) atomicOr(a.errflag, 1);
-                        }
-                        IO::store(psi + base, acc);
-                    } else {
-                        IO::store((to_tail ? tail : psi) + base, acc);
                     }
                 }
             }
