@@ -42,6 +42,29 @@ METRIC = ("Chebyshev matvec-steps/s and achieved HBM GB/s (% of GB300 peak), "
 UNIT = "matvec-steps/s"
 WORKLOAD = "ensemble of 64 uneven zigzag ribbons x 4 packets, complex64, dt=1"
 
+# Algorithmic bytes per unit (one site or basis row, one Chebyshev order) of the unblocked
+# fused recurrence that moves every operand once: T_j, T_{j-1}, T_{j+1}, psi read and written,
+# the on-site array, plus the stored matrix for the SELL operator.  "achieved" in the bench
+# line is this figure x the units a launch processes / the launch's duration, so a kernel that
+# reuses data on chip (temporal blocking, grouped accumulation) can exceed the copy bandwidth;
+# its own DRAM bytes are reported as "traffic".
+ALG_BYTES_PER_UNIT = {
+    ("ensemble", "c64"): 164.0,   # 4 packets share the on-site array: 4 * 40 + 4
+    ("ribbon", "c64"): 44.0, ("ribbon", "f64"): 88.0,
+    ("doublewell", "f64"): 88.0, ("doublewell", "c64"): 44.0,
+    ("holstein", "c64"): 71.0, ("holstein", "f64"): 127.0,          # SELL-32 (~3.9 entries)
+    ("holstein-mf", "c64"): 40.0, ("holstein-mf", "f64"): 80.0,     # vectors only
+}
+
+# DRAM bytes of one step of the default ensemble (dram__bytes_read.sum +
+# dram__bytes_write.sum over all launches of a step, one ncu pass), by blocking (orders per
+# launch, sites per thread); the launches per step follow from the schedule.
+TB_DRAM_BYTES_PER_STEP = {(5, 4): 10.866e9}
+
+# DRAM bytes of one step of the paper's polaron run with the matrix-free operator, by
+# (precision, M), same capture method
+POLARON_MF_DRAM_BYTES_PER_STEP = {("c64", 24): 497.2e9}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -54,7 +77,8 @@ def parse():
     ap.add_argument("--lean", action="store_true",
                     help="timed region only: no e2e, FP64 or accuracy legs (profiling runs)")
     ap.add_argument("--workload", default="ensemble",
-                    choices=["ensemble", "ribbon", "holstein", "doublewell", "adjoint", "polaron"],
+                    choices=["ensemble", "ribbon", "holstein", "doublewell", "paperwell", "adjoint",
+                             "polaron", "armchair", "driven"],
                     help="ensemble (default, the headline line); the others measure the other "
                          "configurations of the hot path")
     ap.add_argument("--prec", default=None, choices=["c64", "c128"],
@@ -304,16 +328,30 @@ def run_ours(args, world, rank, local):
     site_steps = sum_over_ranks(ss_per_step * args.steps, world) / (ms / 1e3)
 
     peak, peak_kind = measured_peaks()
-    achieved = kbytes / (kms / 1e3) / 1e9  # GB/s
+    # per launch: the unblocked algorithmic bytes of the site-orders it forms
+    launches_per_step = kcount / args.steps
+    alg_per_launch = ALG_BYTES_PER_UNIT[("ensemble", "c64")] * (ss_per_step / ens.nvec) / launches_per_step
+    ms_per_launch = kms / kcount
+    achieved = alg_per_launch / (ms_per_launch / 1e3) / 1e9  # GB/s
+    blk = tuple(plan.blocking())
+    traffic = None
+    if blk in TB_DRAM_BYTES_PER_STEP and sorted(set(Ms)) == [20, 21]:
+        traffic = TB_DRAM_BYTES_PER_STEP[blk] / launches_per_step
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": ("k_rec_tb<4,%d> (all launches of the step)" % plan.blocking()[1]
-                           if plan.blocking()[0] else
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": ("k_rec_tb<4,%d> (all launches of the step)" % blk[1]
+                           if blk[0] else
                            "k_rec<float,%d,StencilOp> (all launches of the step)"
                            % plan.launch_shape()[3]),
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "launches": kcount, "kernel_ms_total": kms,
-                "alg_bytes_per_launch": kbytes / max(kcount, 1)}
+                "alg_bytes_per_launch": alg_per_launch,
+                "alg_bytes_per_unit": ALG_BYTES_PER_UNIT[("ensemble", "c64")],
+                "unit_definition": "one site (4 packets) and one Chebyshev order",
+                "kernel_bytes_per_launch": kbytes / max(kcount, 1),
+                "kernel_bytes_note": "operands the blocked launches themselves must move "
+                                     "(region inputs once per interior site)",
+                "dram_achieved": (traffic / (ms_per_launch / 1e3) / 1e9) if traffic else None}
 
     out = {}
     if not args.lean:
@@ -452,6 +490,11 @@ def _single_setup(args):
                     sites=hs.dim,
                     dt=hs.dt, nsteps=hs.nsteps, kind="holstein", obj=hs, bounds=hs.bounds(),
                     alpha=hs.alpha, packet=hs.initial_state())
+    if wk == "paperwell":
+        d = wl.PaperDoubleWell()
+        return dict(name="double well of Sec. 3.1, N=2048, dt=0.4 to t=40", sites=d.n, dt=d.dt,
+                    nsteps=d.nsteps, kind="doublewell", obj=d, bounds=d.bounds(), alpha=0.01,
+                    packet=d.packet(), exact=True)
     if wk == "doublewell":
         d = wl.DoubleWell1D()
         return dict(name="1D double well N=2048, dt=0.5 (M=6353)", sites=d.n, dt=d.dt,
@@ -578,7 +621,12 @@ def run_single(args, world, rank, local):
         plan.set_timing(False)
         value = mv_per_step * args.steps / (ms / 1e3)
         peak, peak_kind = measured_peaks()
-        achieved = kbytes / (kms / 1e3) / 1e9
+        dkey = "f64" if prec == cb.CHEB_C128 else "c64"
+        ukind = cfg["kind"] + ("-mf" if cfg["matrix_free"] and cfg["kind"] == "holstein" else "")
+        per_unit = ALG_BYTES_PER_UNIT[(ukind, dkey)]
+        ms_per_launch = kms / max(kcount, 1)
+        alg_per_launch = per_unit * cfg["sites"] * M * min(args.steps, 5) / max(kcount, 1)
+        achieved = alg_per_launch / (ms_per_launch / 1e3) / 1e9
         bound = "hbm"
         note = None
         if prec == cb.CHEB_C128:
@@ -595,7 +643,9 @@ def run_single(args, world, rank, local):
                     "frac": achieved / peak, "traffic": None, "kernel": kname,
                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "launches": kcount, "kernel_ms_total": kms,
-                    "alg_bytes_per_launch": kbytes / max(kcount, 1), "note": note}
+                    "alg_bytes_per_launch": alg_per_launch, "alg_bytes_per_unit": per_unit,
+                    "unit_definition": "one row (site) and one Chebyshev order",
+                    "kernel_bytes_per_launch": kbytes / max(kcount, 1), "note": note}
         # accuracy: against the oracle after min(steps done, config) steps from the packet
         nacc = {"holstein": 2, "ribbon": 50}.get(cfg["kind"], cfg["nsteps"])
         if args.lean:
@@ -610,6 +660,16 @@ def run_single(args, world, rank, local):
             out["accuracy"] = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(res - ref) /
                                                               np.linalg.norm(ref)),
                                "sample": f"{nacc} steps from the initial state"}
+            if cfg.get("exact"):
+                # against full diagonalisation (Sec. 3.1 quotes < 2e-11 for the Chebyshev
+                # method), absolute error in the continuum normalisation psi_i / sqrt(dx)
+                from scipy.linalg import eigh_tridiagonal
+
+                dd, ee = cfg["obj"].tridiagonal()
+                E, U = eigh_tridiagonal(dd, ee)
+                ex = U @ (np.exp(-1j * E * nacc * cfg["dt"]) * (U.T @ cfg["packet"]))
+                out["accuracy"]["max_abs_err_vs_exact_diagonalisation"] = float(
+                    np.max(np.abs(res - ex)) / np.sqrt(cfg["obj"].dx))
         if not args.no_cpu_baseline and not args.lean:
             H = _oracle_operator(cfg)
             C, _ = oracle.coeffs(a, b, cfg["dt"])
@@ -685,6 +745,184 @@ def run_reference_single(args, world, rank):
     return 0
 
 
+def run_driven(args, world, rank, local):
+    """Time-dependent H(t) (Sec. 2.2), piecewise constant over each step: the 128 x 2048
+    zigzag ribbon with an oscillating field F sin(Omega t) (c - L/2)/L along the ribbon added
+    to its disorder, sampled at the step midpoints; every step rescales the diagonal on the
+    device before its M launches."""
+    import torch
+
+    import oracle
+    import paper_0907_3022_gb300 as cb
+
+    torch.cuda.set_device(local)
+    prec = cb.CHEB_C64 if args.prec == "c64" else cb.CHEB_C128
+    cdt = torch.complex64 if prec == cb.CHEB_C64 else torch.complex128
+    rb = wl.Ribbon()
+    F, Om = 0.5, 0.2
+    col = (np.arange(rb.n_sites) % rb.L - rb.L / 2) / rb.L
+    base = rb.onsite()
+
+    def field(t):
+        return base + F * math.sin(Om * t) * col
+
+    K = args.steps
+    seq = torch.from_numpy(np.stack([field((s + 0.5) * rb.dt) for s in range(K)])).to("cuda")
+    lo, hi = rb.bounds()
+    lo, hi = lo - F / 2, hi + F / 2
+    eps = torch.from_numpy(base).to("cuda")
+    desc, keep = cb.desc_ribbons([rb.W], [rb.L], rb.hop, eps)
+    plan = cb.Plan(desc, [lo], [hi], 0.0, prec, 1, keep=keep)
+    psi = torch.from_numpy(rb.packet()).to(cdt).to("cuda").contiguous()
+    plan.evolve(psi, rb.dt, 0)
+    plan.autotune()
+    M = plan.block(0)["M"]
+    plan.evolve_td(psi, rb.dt, max(args.warmup, 3), seq)
+    stream = torch.cuda.current_stream()
+    launches0 = plan.launches()
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.evolve_td(psi, rb.dt, K, seq)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    gpu_launches = plan.launches() - launches0
+    # the same number of steps with H fixed (graph path), for the cost of the per-step update
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    plan.evolve(psi, rb.dt, K)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    out = {}
+    if not args.lean:
+        nacc = 3
+        x = torch.from_numpy(rb.packet()).to(cdt).to("cuda").contiguous()
+        plan.evolve_td(x, rb.dt, nacc, seq)
+        a, b = oracle.rescale(lo, hi, 0.0)
+        C, _ = oracle.coeffs(a, b, rb.dt)
+        t0 = time.perf_counter()
+        ref = oracle.evolve_piecewise(lambda V: oracle.honeycomb(rb.W, rb.L, rb.hop, V),
+                                      [field((s + 0.5) * rb.dt) for s in range(nacc)], a, b, C,
+                                      rb.packet())
+        tcpu = time.perf_counter() - t0
+        res = x.cpu().numpy().astype(np.complex128)
+        out["accuracy"] = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(res - ref)
+                                                          / np.linalg.norm(ref)),
+                           "sample": f"{nacc} steps from the packet"}
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = {"value": M * nacc / tcpu, "unit": UNIT, "cores": 1,
+                                   "kind": "oracle", "sample": f"{nacc} driven steps (operator "
+                                   "rebuilt every step, FP64 oracle, single thread)"}
+    line = {"metric": METRIC, "value": M * K / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": ms / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64" if prec == cb.CHEB_C64 else "f64", "data": "synthetic",
+            "config": {"workload": "driven zigzag ribbon 128x2048: disorder + F sin(Omega t) "
+                                   "(c - L/2)/L, F = 0.5, Omega = 0.2, dt = 1, midpoint samples",
+                       "M": M, "static_ms_per_step": s0.elapsed_time(s1) / K,
+                       "l2": "working set in L2"},
+            "roofline": None, "gpu_launches": gpu_launches, "clocks": clk}
+    line.update(out)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
+def run_armchair(args, world, rank, local):
+    """Table 2 (Sec. 3.2): armchair ribbons of 10 x 1000 atoms with disorder W = 0.5 and 4 (one
+    two-ribbon plan), the state on one central site, propagated to t = 10^4 with dt = 1, 10
+    and 100; each propagation is timed once (time to solution), the rate is the sum of the
+    matvecs over the sum of the times."""
+    import torch
+
+    import oracle
+    import paper_0907_3022_gb300 as cb
+
+    torch.cuda.set_device(local)
+    prec = cb.CHEB_C64 if args.prec == "c64" else cb.CHEB_C128
+    cdt = torch.complex64 if prec == cb.CHEB_C64 else torch.complex128
+    rbs = [wl.ArmchairRibbon(disorder=w, stream=q) for q, w in enumerate((0.5, 4.0))]
+    eps = torch.from_numpy(np.concatenate([rb.onsite() for rb in rbs])).to("cuda")
+    desc, keep = cb.desc_armchair([rb.n_a for rb in rbs], [rb.length for rb in rbs], 1.0, eps)
+    plan = cb.Plan(desc, [rb.bounds()[0] for rb in rbs], [rb.bounds()[1] for rb in rbs], 0.0,
+                   prec, 1, keep=keep)
+    x0 = np.concatenate([rb.packet() for rb in rbs])
+    stream = torch.cuda.current_stream()
+    runs, finals = {}, {}
+    tot_mv, tot_ms, tot_steps = 0.0, 0.0, 0
+    launches0 = plan.launches()
+    clocks = Clocks(local)
+    clocks.start()
+    for dt in (1.0, 10.0, 100.0):
+        nsteps = int(round(1e4 / dt))
+        psi = torch.from_numpy(x0).to(cdt).to("cuda").contiguous()
+        plan.evolve(psi, dt, 0)
+        plan.autotune()
+        plan.evolve(psi, dt, max(args.warmup, 3))
+        psi.copy_(torch.from_numpy(x0).to(cdt))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.evolve(psi, dt, nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        Ms = [plan.block(q)["M"] for q in range(len(rbs))]
+        mv = sum(Ms) * nsteps
+        runs[str(int(dt))] = {"M": Ms, "steps": nsteps, "seconds_to_t1e4": ms / 1e3,
+                              "matvec_steps_per_s": mv / (ms / 1e3)}
+        finals[dt] = psi.cpu().numpy().astype(np.complex128)
+        tot_mv += mv
+        tot_ms += ms
+        tot_steps += nsteps
+    clk = clocks.stop()
+    gpu_launches = plan.launches() - launches0
+    acc = {"max_abs_diff_dt1_vs_dt100": float(np.max(np.abs(finals[1.0] - finals[100.0]))),
+           "max_abs_diff_dt10_vs_dt100": float(np.max(np.abs(finals[10.0] - finals[100.0])))}
+    out = {}
+    if not args.lean:
+        off = np.cumsum([0] + [rb.n_sites for rb in rbs])
+        errs = []
+        t0 = time.perf_counter()
+        for q, rb in enumerate(rbs):
+            a, b = oracle.rescale(*rb.bounds(), 0.0)
+            C, _ = oracle.coeffs(a, b, 100.0)
+            ref = oracle.honeycomb(rb.W, rb.L, 1.0, rb.onsite()).evolve(a, b, C, 100, rb.packet())
+            errs.append(float(np.linalg.norm(finals[100.0][off[q]:off[q + 1]] - ref)
+                              / np.linalg.norm(ref)))
+        tcpu = time.perf_counter() - t0
+        acc["rel_l2_vs_fp64_oracle_dt100"] = max(errs)
+        if not args.no_cpu_baseline:
+            mv100 = sum(runs["100"]["M"]) * 100
+            out["cpu_baseline"] = {"value": mv100 / tcpu, "unit": UNIT, "cores": 1,
+                                   "kind": "oracle", "sample": "both ribbons to t = 10^4 with "
+                                   "dt = 100 (FP64 oracle, single thread)",
+                                   "seconds_to_t1e4_dt100": tcpu}
+    line = {"metric": METRIC, "value": tot_mv / (tot_ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": tot_steps, "warmup": max(args.warmup, 3), "ms_per_step": tot_ms / tot_steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64" if prec == cb.CHEB_C64 else "f64", "data": "synthetic",
+            "config": {"workload": "Table 2: armchair ribbons 10 x 1000 atoms, W = 0.5 and 4, one "
+                                   "central site, t = 10^4 with dt = 1, 10, 100",
+                       "runs": runs, "l2": "working set in L2"},
+            "roofline": None, "gpu_launches": gpu_launches, "clocks": clk, "accuracy": acc,
+            "paper_context": "Table 2: one Xeon 5160 core, 378 / 97 / 45 s for dt = 1 / 10 / 100 "
+                             "(its M = 104 / 264 / 1210 follow another cutoff)"}
+    line.update(out)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
 def run_polaron(args, world, rank, local):
     """The paper's polaron run (Sec. 3.3, Fig. 3): 18 sites, <= 11 phonons, D = 622,751,220;
     one step = one dt = 0.25 of the whole state; observables at the end of the timed region."""
@@ -740,7 +978,14 @@ def run_polaron(args, world, rank, local):
     n2 = torch.zeros(1, dtype=torch.float64, device="cuda")
     plan.observables(psi, cb.CHEB_OBS_NORM2, 0.0, n2)
     peak, peak_kind = measured_peaks()
-    achieved = kbytes / (kms / 1e3) / 1e9
+    dkey = "f64" if prec == cb.CHEB_C128 else "c64"
+    per_unit = ALG_BYTES_PER_UNIT[("holstein-mf" if args.matrix_free else "holstein", dkey)]
+    alg_per_launch = per_unit * pw.dim  # every launch forms one order for every row
+    ms_per_launch = kms / max(kcount, 1)
+    achieved = alg_per_launch / (ms_per_launch / 1e3) / 1e9
+    traffic = None
+    if args.matrix_free and (dkey, M) in POLARON_MF_DRAM_BYTES_PER_STEP:
+        traffic = POLARON_MF_DRAM_BYTES_PER_STEP[(dkey, M)] / M
     steps_done = args.warmup + args.steps + 1
     line = {"metric": METRIC, "value": M * args.steps / (ms / 1e3), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -756,11 +1001,14 @@ def run_polaron(args, world, rank, local):
             "site_steps_per_s": M * pw.dim * args.steps / (ms / 1e3),
             "time_to_t20_s": ms / args.steps * pw.nsteps / 1e3,
             "roofline": {"bound": "alu" if prec == cb.CHEB_C128 else "hbm", "achieved": achieved,
-                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "kernel": ("k_rec_holmf<%s>" if args.matrix_free else "k_rec<%s,1,SellOp>")
                                    % ("double" if prec == cb.CHEB_C128 else "float"),
                          "peak_kind": f"{peak_kind} copy bandwidth", "launches": kcount,
-                         "alg_bytes_per_launch": kbytes / max(kcount, 1)},
+                         "alg_bytes_per_launch": alg_per_launch, "alg_bytes_per_unit": per_unit,
+                         "unit_definition": "one basis row and one Chebyshev order",
+                         "kernel_bytes_per_launch": kbytes / max(kcount, 1),
+                         "dram_achieved": (traffic / (ms_per_launch / 1e3) / 1e9) if traffic else None},
             "gpu_launches": gpu_launches, "clocks": clk,
             "physics": {"t": steps_done * pw.dt, "norm2": float(n2.item()), **obs},
             "paper_context": "Sec. 3.3: the same basis on 18 SGI Altix 4700 processors, ~60 GB, "
@@ -780,11 +1028,23 @@ def main():
                 print(json.dumps({"impl": "reference", "unavailable": "the oracle would need "
                                   "~200 GB of host memory for D = 622,751,220"}))
                 return 0
+            if args.workload == "driven":
+                print(json.dumps({"impl": "reference", "unavailable": "the oracle leg of the "
+                                  "driven line is its cpu_baseline"}))
+                return 0
+            if args.workload == "armchair":
+                print(json.dumps({"impl": "reference", "unavailable": "the oracle leg of the "
+                                  "armchair line is its cpu_baseline (dt = 100)"}))
+                return 0
             if args.workload != "ensemble":
                 return run_reference_single(args, world, rank)
             return run_reference(args, world, rank)
         if args.workload == "polaron":
             return run_polaron(args, world, rank, local)
+        if args.workload == "armchair":
+            return run_armchair(args, world, rank, local)
+        if args.workload == "driven":
+            return run_driven(args, world, rank, local)
         if args.workload != "ensemble":
             return run_single(args, world, rank, local)
         return run_ours(args, world, rank, local)

@@ -63,7 +63,9 @@ typedef enum {
        along, index r*L + c; neighbours (r, c-1), (r, c+1) and (r+1, c) if r + c is even,
        (r-1, c) if odd; open at every border.  nblocks ribbons are stored one after another
        (ribbon q starts at site sum_{p<q} W_p L_p); each has its own a, b, c_k and M.
-       onsite = eps_j. */
+       onsite = eps_j.  The columns c = 0 and c = L-1 are armchair edges, so a ribbon with
+       armchair edges along its length (Table 2: N_a dimer lines across) is the same operator
+       with W = its length and L = N_a. */
     CHEB_HONEYCOMB_ZZ = 1,
     /* Holstein chain, Sec. 3.3, Eq. (ghm), one spinless electron:
        H = sum_i Delta_i n_i - t sum_i (c_i^+ c_{i+1} + h.c.) - sum_i g_i w0 (b_i^+ + b_i) n_i
@@ -168,6 +170,18 @@ int cheb_step(cheb_plan* plan, void* psi, double dt);
    the bound |v_k| <= ||psi|| that holds when the spectrum lies inside [emin, emax]. */
 int cheb_evolve(cheb_plan* plan, void* psi, double dt, int nsteps, int obs_every,
                 double* obs);
+
+/* Time-dependent Hamiltonian (Sec. 2.2: the time variation of H(t) limits the step): nsteps
+   steps of dt with H held constant over each step, step s using the on-site energies at
+   onsite_seq + s * stride (device, double, in the layout of the descriptor's onsite array;
+   stride in doubles, even, >= the array length).  Sampling V(t) at the step midpoints
+   t_s + dt/2 makes the scheme second order in dt.  The rescaling a, b stays the one of the
+   plan, so its bounds must enclose the spectrum of every H(t_s) (CHEB_ERR_DIVERGED
+   otherwise).  obs_every / obs as cheb_evolve.  Afterwards the plan keeps the last step's
+   on-site energies.  Lattice kinds only (CHEB_ERR_UNSUPPORTED for Holstein plans).
+   Synchronises the plan's stream. */
+int cheb_evolve_td(cheb_plan* plan, void* psi, double dt, int nsteps, const double* onsite_seq,
+                   int64_t stride, int obs_every, double* obs);
 
 /* Status of the work enqueued so far: synchronises the stream, returns CHEB_ERR_DIVERGED
    if the growth check fired since the last call (and clears it), CHEB_ERR_CUDA on an

@@ -228,7 +228,10 @@ def lattice1d(n: int, dx: float, V) -> Operator:
     return Operator(lib().oracle_op_lattice1d(n, dx, _d(V)), keep=(V,))
 
 
-def honeycomb(W: int, L: int, t: float, eps=None, periodic: bool = False) -> Operator:
+def honeycomb(W: int, L: int, t: float, eps=None, periodic: bool | int = False) -> Operator:
+    """Brick-wall honeycomb lattice: W rows (zigzag chains), L columns (dimer lines);
+    periodic: False open, True / 1 a torus, 2 rows wrapped only (armchair ribbon made
+    infinite along its length)."""
     e = _f64(eps) if eps is not None else None
     return Operator(lib().oracle_op_honeycomb(W, L, t, _d(e) if e is not None else None,
                                               int(periodic)), keep=(e,))
@@ -283,3 +286,15 @@ def holstein(L: int, nph: int, periodic: bool, t: float, omega0: float, g: float
     op = HolsteinOperator(h, keep=(D, G))
     op._L = L
     return op
+
+
+def evolve_piecewise(make_op, onsite_seq, a: float, b: float, C: np.ndarray, psi) -> np.ndarray:
+    """Time-dependent H(t) held constant over each step (Sec. 2.2: the time variation of H
+    limits the step): for s = 0, 1, ..., psi <- exp(-i H_s dt) psi by the Chebyshev step of
+    Eq. U_1 with H_s = make_op(onsite_seq[s]) and the fixed rescaling (a, b), which must
+    enclose the spectrum of every H_s.  Sampling the on-site energies at the step midpoints
+    makes the scheme second order in dt."""
+    psi = _c128(psi).copy()
+    for V in onsite_seq:
+        psi = make_op(V).step(a, b, C, psi)
+    return psi

@@ -217,13 +217,20 @@ oracle_op* oracle_op_lattice1d(long n, double dx, const double* V)
    Brick-wall picture of the honeycomb lattice: site (r, c) with r in [0, W) across the ribbon
    and c in [0, L) along it, index r*L + c.  Its three neighbours are (r, c-1), (r, c+1) and
    (r+1, c) when r + c is even, (r-1, c) when r + c is odd.  Rows r are zigzag chains, so the
-   edges r = 0 and r = W-1 are zigzag edges.  periodic != 0 wraps both directions (a torus,
-   used only to check the spectrum against its closed form; needs W and L even).            */
+   edges r = 0 and r = W-1 are zigzag edges and the columns c = 0 and c = L-1 armchair edges:
+   a ribbon with armchair edges along its length is the same lattice with the long direction
+   across the rows (W = length, L = number of dimer lines).  periodic = 1 wraps both
+   directions (a torus; needs W and L even), periodic = 2 wraps the rows only (an armchair
+   ribbon made infinite along its length; needs W even); both serve only to check spectra
+   against closed forms.                                                                     */
 static long hc_index(int W, int L, int r, int c, int periodic)
 {
-    if (periodic) {
+    if (periodic == 1) {
         r = (r % W + W) % W;
         c = (c % L + L) % L;
+    } else if (periodic == 2) {
+        if (c < 0 || c >= L) return -1;
+        r = (r % W + W) % W;
     } else if (r < 0 || r >= W || c < 0 || c >= L) {
         return -1;
     }
@@ -232,8 +239,9 @@ static long hc_index(int W, int L, int r, int c, int periodic)
 
 oracle_op* oracle_op_honeycomb(int W, int L, double t, const double* eps, int periodic)
 {
-    if (W < 1 || L < 1) return NULL;
-    if (periodic && ((W % 2) || (L % 2) || W < 2 || L < 4)) return NULL;
+    if (W < 1 || L < 1 || periodic < 0 || periodic > 2) return NULL;
+    if (periodic == 1 && ((W % 2) || (L % 2) || W < 2 || L < 4)) return NULL;
+    if (periodic == 2 && ((W % 2) || W < 4)) return NULL;
     long n = (long)W * L;
     oracle_op* H = op_new(n, 4 * n);
     if (!H) return NULL;

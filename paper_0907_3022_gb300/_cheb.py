@@ -83,6 +83,8 @@ _SIGS = {
     "cheb_step": ([_vp, _vp, _c.c_double], _c.c_int),
     "cheb_evolve": ([_vp, _vp, _c.c_double, _c.c_int, _c.c_int, _vp], _c.c_int),
     "cheb_sync": ([_vp], _c.c_int),
+    "cheb_evolve_td": ([_vp, _vp, _c.c_double, _c.c_int, _vp, _c.c_int64, _c.c_int, _vp],
+                       _c.c_int),
     "cheb_observables": ([_vp, _vp, _c.c_int, _c.c_double, _vp], _c.c_int),
     "cheb_adjoint_potential": ([_vp, _vp, _c.c_double, _c.c_int, _vp, _c.c_int64, _vp, _vp, _vp],
                                _c.c_int),
@@ -256,6 +258,15 @@ class Plan:
         check(lib().cheb_evolve(self.handle, _ptr(psi), dt, nsteps, obs_every, _ptr(obs)),
               "cheb_evolve")
 
+    def evolve_td(self, psi, dt: float, nsteps: int, onsite_seq, stride: int | None = None,
+                  obs_every: int = 0, obs=None):
+        """H(t) piecewise constant: step s uses the on-site energies onsite_seq[s] (device
+        float64 tensor [nsteps, ...], rows 16-byte aligned)."""
+        if stride is None:
+            stride = onsite_seq[0].numel() if nsteps > 0 else 0
+        check(lib().cheb_evolve_td(self.handle, _ptr(psi), dt, nsteps, _ptr(onsite_seq), stride,
+                                   obs_every, _ptr(obs)), "cheb_evolve_td")
+
     def sync(self):
         check(lib().cheb_sync(self.handle), "cheb_sync")
 
@@ -366,6 +377,13 @@ def desc_ribbons(W, L, hop: float = 1.0, onsite=None, onsite_per_vec: bool = Fal
     d.onsite = _ptr(onsite)
     d.onsite_per_vec = int(onsite_per_vec)
     return d, (Wa, La, onsite)
+
+
+def desc_armchair(n_a, lengths, hop: float, onsite=None, onsite_per_vec: bool = False):
+    """Armchair ribbons (armchair edges along the length; n_a dimer lines across): the
+    brick-wall operator of CHEB_HONEYCOMB_ZZ with the long direction across the rows,
+    W = length, L = n_a.  Returns (descriptor, arrays to keep alive)."""
+    return desc_ribbons(list(lengths), list(n_a), hop, onsite, onsite_per_vec)
 
 
 def desc_holstein(L: int, nph: int, periodic: bool, hop: float, omega0: float, g: float,

@@ -769,6 +769,43 @@ extern "C" int cheb_evolve(cheb_plan* plan, void* psi, double dt, int nsteps, in
     return cheb_sync(plan);
 }
 
+// Time-dependent on-site energies: H held constant over each step (Sec. 2.2); step s first
+// rescales the plan's diagonal from its own on-site array, then runs the M launches.
+extern "C" int cheb_evolve_td(cheb_plan* plan, void* psi, double dt, int nsteps,
+                              const double* onsite_seq, int64_t stride, int obs_every,
+                              double* obs)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    if (p->desc.kind == CHEB_HOLSTEIN)
+        return fail(CHEB_ERR_UNSUPPORTED, "cheb_evolve_td needs a lattice plan");
+    if (nsteps < 0) return fail(CHEB_ERR_INVALID, "nsteps < 0");
+    int rc = check_psi(p, psi);
+    if (rc) return rc;
+    if (nsteps == 0) return CHEB_OK;
+    if (!onsite_seq) return fail(CHEB_ERR_INVALID, "cheb_evolve_td: onsite_seq is NULL");
+    const int64_t per = (int64_t)p->n_sites * (p->desc.onsite_per_vec ? p->nvec : 1);
+    if (nsteps > 1 && stride < per)
+        return fail(CHEB_ERR_INVALID, "cheb_evolve_td: stride smaller than one on-site array");
+    if (!aligned16(onsite_seq) || (nsteps > 1 && (stride & 1)))
+        return fail(CHEB_ERR_ALIGN, "cheb_evolve_td: every step's array must be 16-byte aligned");
+    if (obs && !aligned16(obs)) return fail(CHEB_ERR_ALIGN, "obs must be 16-byte aligned");
+    rc = set_dt(p, dt);
+    if (rc) return rc;
+    const size_t rec_bytes = (size_t)p->nblocks * p->nvec * 2 * sizeof(double);
+    for (int s = 0; s < nsteps; ++s) {
+        rc = launch_scale_diag(p, onsite_seq + (size_t)s * (size_t)stride, p->stream);
+        if (rc) return rc;
+        rc = enqueue_step(p, psi, p->stream);
+        if (rc) return rc;
+        if (obs && obs_every > 0 && s % obs_every == 0) {
+            CHEB_CUDA(cudaMemcpyAsync(obs + (size_t)(s / obs_every) * p->nblocks * p->nvec * 2,
+                                      p->d_red, rec_bytes, cudaMemcpyDeviceToDevice, p->stream));
+        }
+    }
+    return cheb_sync(plan);
+}
+
 extern "C" int cheb_observables(cheb_plan* plan, const void* psi, int kind, double param,
                                 double* out)
 {

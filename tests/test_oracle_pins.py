@@ -181,6 +181,103 @@ def test_propagator_matches_exact_diagonalisation_1d():
     assert np.linalg.norm(psi - ex) / np.linalg.norm(ex) < 2e-11
 
 
+def _tridiagonal_exact(d, e, psi0, t):
+    """exp(-iHt) psi0 for the real symmetric tridiagonal H by full diagonalisation (LAPACK)."""
+    from scipy.linalg import eigh_tridiagonal
+
+    E, V = eigh_tridiagonal(d, e)
+    return V @ (np.exp(-1j * E * t) * (V.T @ psi0))
+
+
+def test_paper_double_well_accuracy_claim():
+    """Sec. 3.1: N = 2048, M = 1500 moments at dt = 0.4, t = 40; the Chebyshev wave function
+    agrees with full diagonalisation to an absolute error below 2e-11 (the paper's
+    normalisation: psi_i / sqrt(dx)).  Also the physics of the set-up: the packet starts
+    below the barrier and part of it tunnels to the right well."""
+    d = wl.PaperDoubleWell()
+    lo, hi = d.bounds()
+    a, b = oracle.rescale(lo, hi, 0.01)
+    C, M = oracle.coeffs(a, b, d.dt)
+    assert M == 1499  # 1500 moments c_0 .. c_1499
+    H = oracle.lattice1d(d.n, d.dx, d.potential())
+    x0 = d.packet()
+    psi = H.evolve(a, b, C, d.nsteps, x0)
+    dd, ee = d.tridiagonal()
+    ex = _tridiagonal_exact(dd, ee, x0, d.t_end)
+    assert np.max(np.abs(psi - ex)) / math.sqrt(d.dx) < 2e-11
+    n2, E0 = H.norm_energy(x0)
+    assert abs(n2 - 1.0) < 1e-14 and 0.5 < E0 < d.V0  # below the barrier V(0) = V0
+    assert np.min(d.potential()) > -1e-3 and abs(d.potential()[d.n // 2] - d.V0) < 1e-12
+    right = np.sum(np.abs(ex[d.x > 0]) ** 2)
+    assert 0.02 < right < 0.5
+
+
+def test_piecewise_uniform_shift_closed_form():
+    """H(t) = H_0 + v(t) 1 with v linear in t: exp(-i int v) exp(-i H_0 T) psi exactly, and
+    the midpoint rule integrates a linear v without error, so the piecewise-constant
+    propagation reproduces the closed form to rounding."""
+    d = wl.DoubleWell1D(n=128, x_lo=-8.0, x_hi=8.0)
+    V0 = d.potential()
+    dt, nsteps, v0, v1 = 0.05, 40, 0.3, -0.7
+    T = dt * nsteps
+    tm = (np.arange(nsteps) + 0.5) * dt
+    lo, hi = d.bounds()
+    lo, hi = lo + min(v0, v0 + v1 * T), hi + max(v0, v0 + v1 * T)
+    a, b = oracle.rescale(lo, hi, 0.01)
+    C, _ = oracle.coeffs(a, b, dt)
+    seq = [V0 + v0 + v1 * t for t in tm]
+    psi = oracle.evolve_piecewise(lambda V: oracle.lattice1d(d.n, d.dx, V), seq, a, b, C,
+                                  d.packet())
+    dd, ee = d.tridiagonal()
+    ex = np.exp(-1j * (v0 * T + 0.5 * v1 * T * T)) * _tridiagonal_exact(dd, ee, d.packet(), T)
+    assert np.max(np.abs(psi - ex)) < 1e-12
+
+
+def _driven_well(n=96):
+    """Double well with a field F sin(Omega t) x switched on (does not commute with H_0)."""
+    d = wl.DoubleWell1D(n=n, x_lo=-6.0, x_hi=6.0)
+    F, Om = 0.8, 1.3
+    return d, (lambda t: d.potential() + F * math.sin(Om * t) * d.x), F * np.max(np.abs(d.x))
+
+
+def test_piecewise_midpoint_converges_to_schroedinger_solution():
+    """The dt -> 0 limit of the piecewise-constant propagation is the solution of
+    i dpsi/dt = H(t) psi, computed here by an unrelated integrator (scipy DOP853, rtol 1e-12);
+    midpoint sampling makes the error fall by ~4x per halving of dt (second order)."""
+    from scipy.integrate import solve_ivp
+
+    d, Vt, vmax = _driven_well()
+    T = 2.0
+    dd, ee = d.tridiagonal()
+    base = dd - d.potential()
+
+    def rhs(t, y):
+        psi = y[: d.n] + 1j * y[d.n:]
+        h = (base + Vt(t)) * psi
+        h[1:] += ee * psi[:-1]
+        h[:-1] += ee * psi[1:]
+        dpsi = -1j * h
+        return np.concatenate([dpsi.real, dpsi.imag])
+
+    x0 = d.packet()
+    sol = solve_ivp(rhs, (0.0, T), np.concatenate([x0.real, x0.imag]), method="DOP853",
+                    rtol=1e-12, atol=1e-13)
+    ref = sol.y[: d.n, -1] + 1j * sol.y[d.n:, -1]
+    lo, hi = d.bounds()
+    a, b = oracle.rescale(lo - vmax, hi + vmax, 0.01)
+    errs = []
+    for nsteps in (20, 40, 80):
+        dt = T / nsteps
+        C, _ = oracle.coeffs(a, b, dt)
+        seq = [Vt((s + 0.5) * dt) for s in range(nsteps)]
+        psi = oracle.evolve_piecewise(lambda V: oracle.lattice1d(d.n, d.dx, V), seq, a, b, C,
+                                      x0)
+        errs.append(np.linalg.norm(psi - ref))
+    assert errs[0] > 1e-6  # the driving matters at this step
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.5 < e1 / e2 < 4.5
+
+
 def test_harmonic_coherent_state_returns_after_period():
     """V = x^2/2: a displaced ground state returns to itself after t = 2 pi (up to O(dx^2))."""
     n = 512
@@ -262,6 +359,25 @@ def test_honeycomb_open_ribbon_structure():
     assert (off != 0).sum(axis=1).max() == 3
     E = np.linalg.eigvalsh(oracle.honeycomb(W, L, 1.0).dense())
     assert np.allclose(E, -E[::-1], atol=1e-12)
+
+
+@pytest.mark.parametrize("Na", [4, 5, 8, 10])
+def test_honeycomb_armchair_ribbon_spectrum_closed_form(Na):
+    """Armchair reading of the brick-wall (Sec. 3.2 ribbons with armchair edges): the
+    columns are the N_a dimer lines; with the rows wrapped the ribbon is infinite along its
+    length and its bands are E = +-t (1 + 4 cos^2 th_p + 4 cos th_p cos(phi/2))^(1/2),
+    th_p = p pi/(N_a + 1), phi the Bloch phase per two rows; N_a = 3m - 1 is metallic."""
+    W = 48
+    H = oracle.honeycomb(W, Na, 1.0, periodic=2)
+    E = np.sort(np.linalg.eigvalsh(H.dense()))
+    th = np.arange(1, Na + 1) * np.pi / (Na + 1)
+    phi = 2 * np.pi * np.arange(W // 2) / (W // 2)
+    e = np.sqrt(np.maximum(0.0, 1 + 4 * np.cos(th)[:, None] ** 2
+                           + 4 * np.cos(th)[:, None] * np.cos(phi / 2)[None, :])).ravel()
+    ref = np.sort(np.concatenate([e, -e]))
+    assert np.max(np.abs(E - ref)) < 1e-12
+    gap = np.min(np.abs(E))
+    assert (gap < 1e-12) == (Na % 3 == 2)
 
 
 def test_propagator_matches_exact_diagonalisation_ribbon():

@@ -104,6 +104,69 @@ class DoubleWell1D:
         return float(lo), float(hi)
 
 
+@dataclass
+class PaperDoubleWell:
+    """The double well of Sec. 3.1: V(q) = V0 + (1/2) m w0^2 (-q^2 + a q^4) with m = 1,
+    w0 = 0.4, a = 0.02, V0 = 1 (reference units; hbar = 1), minima V = 0 at q = +-5 and the
+    barrier V = 1 at q = 0; the Gaussian of Eq. psi0, (2 pi sigma^2)^(-1/4)
+    exp(-(q - q0)^2/(4 sigma^2) + i p0 q), with sigma = 1/sqrt(2), q0 = -5, p0 = 1; N = 2048
+    grid points; dt = 0.4 to t = 40.  The grid extent is not stated: [-17.6, 17.6) is read,
+    the extent at which the 1e-14 cutoff gives the paper's M = 1500 moments at dt = 0.4."""
+    n: int = 2048
+    q_lo: float = -17.6
+    q_hi: float = 17.6
+    m: float = 1.0
+    omega0: float = 0.4
+    a4: float = 0.02
+    V0: float = 1.0
+    q0: float = -5.0
+    p0: float = 1.0
+    sigma: float = 2.0 ** -0.5
+    dt: float = 0.4
+    t_end: float = 40.0
+
+    @property
+    def dx(self) -> float:
+        return (self.q_hi - self.q_lo) / self.n
+
+    @property
+    def x(self) -> np.ndarray:
+        return self.q_lo + self.dx * np.arange(self.n)
+
+    @property
+    def nsteps(self) -> int:
+        return int(round(self.t_end / self.dt))
+
+    def potential(self) -> np.ndarray:
+        q = self.x
+        return self.V0 + 0.5 * self.m * self.omega0 ** 2 * (-q * q + self.a4 * q ** 4)
+
+    def packet(self) -> np.ndarray:
+        """Eq. psi0 on the grid, scaled to a unit vector (sum |psi_i|^2 = 1; the continuum
+        normalisation of the paper is psi_i / sqrt(dx))."""
+        q = self.x
+        s2 = self.sigma ** 2
+        psi = (2 * np.pi * s2) ** -0.25 * np.exp(-((q - self.q0) ** 2) / (4 * s2)
+                                                  + 1j * self.p0 * q)
+        return psi / np.linalg.norm(psi)
+
+    def tridiagonal(self):
+        """Diagonal and off-diagonal of the 3-point H = -1/(2m) d^2/dq^2 + V (m = 1)."""
+        d = 1.0 / self.dx ** 2 + self.potential()
+        e = np.full(self.n - 1, -0.5 / self.dx ** 2)
+        return d, e
+
+    def bounds(self):
+        """Exact extreme eigenvalues of the grid Hamiltonian (LAPACK tridiagonal solver)."""
+        from scipy.linalg import eigh_tridiagonal
+
+        d, e = self.tridiagonal()
+        lo = eigh_tridiagonal(d, e, eigvals_only=True, select="i", select_range=(0, 0))[0]
+        hi = eigh_tridiagonal(d, e, eigvals_only=True, select="i",
+                              select_range=(self.n - 1, self.n - 1))[0]
+        return float(lo), float(hi)
+
+
 # ----------------------------------------------------------------------------------------
 # Zigzag honeycomb ribbons (brick-wall indexing: site (r, c) -> r * L + c, r across, c along)
 # ----------------------------------------------------------------------------------------
@@ -151,6 +214,55 @@ def ribbon_packet(W: int, L: int, sigma: float, k0: float, r0: int, c0: int) -> 
 
 ENSEMBLE_K0 = (math.pi / 6, math.pi / 4, math.pi / 3, math.pi / 2)
 ENSEMBLE_DISORDER = (0.5, 1.0, 2.0)
+
+
+@dataclass
+class ArmchairRibbon:
+    """Armchair ribbon of Sec. 3.2 / Table 2: N_a = 10 dimer lines across and 1000 atoms along
+    each (10,000 atoms, 1.11 x 212.8 nm^2), Anderson disorder in [-W/2, W/2], the state
+    localised on one site in the centre, propagated to t = 10^4 (units 1/t) with dt = 1, 10 or
+    100.  In the brick-wall indexing the long direction runs across the rows: W_bw = length
+    rows, L_bw = N_a columns, site (r, c) -> r * N_a + c."""
+    n_a: int = 10
+    length: int = 1000
+    hop: float = 1.0
+    disorder: float = 0.5
+    seed: int = 907
+    stream: int = 0
+    dt: float = 1.0
+    t_end: float = 1e4
+
+    @property
+    def W(self) -> int:  # brick-wall rows
+        return self.length
+
+    @property
+    def L(self) -> int:  # brick-wall columns
+        return self.n_a
+
+    @property
+    def n_sites(self) -> int:
+        return self.length * self.n_a
+
+    @property
+    def nsteps(self) -> int:
+        return int(round(self.t_end / self.dt))
+
+    def onsite(self) -> np.ndarray:
+        return anderson_disorder(self.n_sites, self.disorder, self.seed, self.stream)
+
+    def bounds(self):
+        """Gershgorin interval +-(3t + W/2)."""
+        r = 3.0 * abs(self.hop) + 0.5 * self.disorder
+        return -r, r
+
+    def start_site(self) -> int:
+        return (self.length // 2) * self.n_a + self.n_a // 2
+
+    def packet(self) -> np.ndarray:
+        psi = np.zeros(self.n_sites, dtype=np.complex128)
+        psi[self.start_site()] = 1.0
+        return psi
 
 
 @dataclass
