@@ -171,6 +171,21 @@ int cheb_step(cheb_plan* plan, void* psi, double dt);
 int cheb_evolve(cheb_plan* plan, void* psi, double dt, int nsteps, int obs_every,
                 double* obs);
 
+/* A batch of independent jobs from host memory: job j's state (n_sites x nvec complex values
+   of the plan's precision, layout [site][vec]; vec_bytes = n_sites * nvec * 16 (complex128)
+   or 8 (complex64) bytes) at (const char*)in + j * in_stride is copied to the device,
+   propagated nsteps steps of dt and copied back to (char*)out + j * out_stride.  Strides are
+   in bytes, 0 (every job reads / writes the same state) or >= vec_bytes.  The host-to-device
+   copy of job j + 1 and the device-to-host copy of job j - 1 overlap the propagation of job j
+   (two device buffers of the plan; one stream per copy direction); the copies overlap only
+   with pinned host memory (cudaHostAlloc / cudaHostRegister).  in and out may be the same
+   buffer only with equal nonzero strides (CHEB_ERR_INVALID otherwise); other overlaps are the
+   caller's error.  Host buffers are owned by the caller and must hold every addressed state.
+   Synchronises before returning; CHEB_ERR_DIVERGED as cheb_evolve.  No counterpart in the
+   paper (many initial states served from host memory). */
+int cheb_evolve_host(cheb_plan* plan, const void* in, int64_t in_stride, void* out,
+                     int64_t out_stride, int64_t njobs, double dt, int nsteps);
+
 /* Time-dependent Hamiltonian (Sec. 2.2: the time variation of H(t) limits the step): nsteps
    steps of dt with H held constant over each step, step s using the on-site energies at
    onsite_seq + s * stride (device, double, in the layout of the descriptor's onsite array;

@@ -83,6 +83,8 @@ _SIGS = {
     "cheb_step": ([_vp, _vp, _c.c_double], _c.c_int),
     "cheb_evolve": ([_vp, _vp, _c.c_double, _c.c_int, _c.c_int, _vp], _c.c_int),
     "cheb_sync": ([_vp], _c.c_int),
+    "cheb_evolve_host": ([_vp, _vp, _c.c_int64, _vp, _c.c_int64, _c.c_int64, _c.c_double, _c.c_int],
+                         _c.c_int),
     "cheb_evolve_td": ([_vp, _vp, _c.c_double, _c.c_int, _vp, _c.c_int64, _c.c_int, _vp],
                        _c.c_int),
     "cheb_observables": ([_vp, _vp, _c.c_int, _c.c_double, _vp], _c.c_int),
@@ -257,6 +259,32 @@ class Plan:
     def evolve(self, psi, dt: float, nsteps: int, obs_every: int = 0, obs=None):
         check(lib().cheb_evolve(self.handle, _ptr(psi), dt, nsteps, obs_every, _ptr(obs)),
               "cheb_evolve")
+
+    def evolve_host(self, host_in, host_out, njobs: int, dt: float, nsteps: int,
+                    in_stride: int | None = None, out_stride: int | None = None):
+        """njobs independent states from host memory (contiguous CPU tensors or numpy arrays;
+        pinned memory for overlapped copies).  Strides in bytes: None = one state per job
+        (consecutive states), 0 = the same state for every job."""
+        vb = self.sites * self.nvec * (16 if self.prec == CHEB_C128 else 8)
+
+        def hbuf(t):
+            if hasattr(t, "data_ptr"):
+                if t.is_cuda or not t.is_contiguous():
+                    raise ValueError("contiguous host tensor expected")
+                return t.data_ptr(), t.numel() * t.element_size()
+            if not t.flags["C_CONTIGUOUS"]:
+                raise ValueError("contiguous host array expected")
+            return t.ctypes.data, t.nbytes
+
+        pin, nin = hbuf(host_in)
+        pout, nout = hbuf(host_out)
+        si = vb if in_stride is None else in_stride
+        so = vb if out_stride is None else out_stride
+        for n, st in ((nin, si), (nout, so)):
+            if njobs > 0 and n < (njobs - 1) * st + vb:
+                raise ValueError("host buffer smaller than the states the jobs address")
+        check(lib().cheb_evolve_host(self.handle, pin, si, pout, so, njobs, dt, nsteps),
+              "cheb_evolve_host")
 
     def evolve_td(self, psi, dt: float, nsteps: int, onsite_seq, stride: int | None = None,
                   obs_every: int = 0, obs=None):

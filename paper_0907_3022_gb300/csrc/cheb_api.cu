@@ -435,12 +435,29 @@ static int check_psi(const Plan* p, const void* psi)
     return CHEB_OK;
 }
 
-static int ensure_graph(Plan* p, void* psi)
+// The step graph for this psi pointer: a cached one if dt and the launch shape are unchanged,
+// else captured into the least recently used slot.
+static int ensure_graph(Plan* p, void* psi, Plan::StepGraph** out)
 {
-    if (p->graph && p->graph_psi == psi && p->graph_epoch == p->shape_epoch) return CHEB_OK;
-    if (p->graph) {
-        cudaGraphExecDestroy(p->graph);
-        p->graph = nullptr;
+    Plan::StepGraph* slot = nullptr;
+    for (Plan::StepGraph& g : p->graphs)
+        if (g.exec && g.psi == psi && g.epoch == p->shape_epoch) slot = &g;
+    if (slot) {
+        slot->used = ++p->graph_clock;
+        *out = slot;
+        return CHEB_OK;
+    }
+    slot = &p->graphs[0];
+    for (Plan::StepGraph& g : p->graphs) {
+        if (!g.exec) {
+            slot = &g;
+            break;
+        }
+        if (g.used < slot->used) slot = &g;
+    }
+    if (slot->exec) {
+        cudaGraphExecDestroy(slot->exec);
+        slot->exec = nullptr;
     }
     cudaGraph_t g = nullptr;
     CHEB_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -454,20 +471,30 @@ static int ensure_graph(Plan* p, void* psi)
         return rc;
     }
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-    ce = cudaGraphInstantiate(&p->graph, g, 0);
+    ce = cudaGraphInstantiate(&slot->exec, g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
-    p->graph_psi = psi;
-    p->graph_epoch = p->shape_epoch;
-    p->graph_kernels = (int)captured;
+    slot->psi = psi;
+    slot->epoch = p->shape_epoch;
+    slot->kernels = (int)captured;
+    slot->used = ++p->graph_clock;
+    *out = slot;
     return CHEB_OK;
 }
 
 static void free_plan(Plan* p)
 {
     if (!p) return;
-    if (p->graph) cudaGraphExecDestroy(p->graph);
+    for (Plan::StepGraph& g : p->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    for (int b = 0; b < 2; ++b) {
+        if (p->d_job[b]) cudaFree(p->d_job[b]);
+        for (cudaEvent_t e : {p->ev_in[b], p->ev_done[b], p->ev_out[b]})
+            if (e) cudaEventDestroy(e);
+    }
+    if (p->h2d_stream) cudaStreamDestroy(p->h2d_stream);
+    if (p->d2h_stream) cudaStreamDestroy(p->d2h_stream);
     for (TBSet& t : p->tb_sets) {
         if (t.d_tiles) cudaFree(t.d_tiles);
         if (t.d_begin) cudaFree(t.d_begin);
@@ -748,8 +775,9 @@ extern "C" int cheb_evolve(cheb_plan* plan, void* psi, double dt, int nsteps, in
     rc = set_dt(p, dt);
     if (rc) return rc;
     if (nsteps == 0) return CHEB_OK;
+    Plan::StepGraph* graph = nullptr;
     if (!p->timing) {
-        rc = ensure_graph(p, psi);
+        rc = ensure_graph(p, psi, &graph);
         if (rc) return rc;
     }
     const size_t rec_bytes = (size_t)p->nblocks * p->nvec * 2 * sizeof(double);
@@ -758,14 +786,85 @@ extern "C" int cheb_evolve(cheb_plan* plan, void* psi, double dt, int nsteps, in
             rc = enqueue_step(p, psi, p->stream);
             if (rc) return rc;
         } else {
-            CHEB_CUDA(cudaGraphLaunch(p->graph, p->stream));
-            p->launches += p->graph_kernels;
+            CHEB_CUDA(cudaGraphLaunch(graph->exec, p->stream));
+            p->launches += graph->kernels;
         }
         if (obs && obs_every > 0 && s % obs_every == 0) {
             CHEB_CUDA(cudaMemcpyAsync(obs + (size_t)(s / obs_every) * p->nblocks * p->nvec * 2,
                                       p->d_red, rec_bytes, cudaMemcpyDeviceToDevice, p->stream));
         }
     }
+    return cheb_sync(plan);
+}
+
+// Jobs from host memory: job j is copied in while job j-1 runs and copied out while job j+1
+// runs (two device buffers; compute on the plan's stream, one stream per copy direction).
+extern "C" int cheb_evolve_host(cheb_plan* plan, const void* in, int64_t in_stride, void* out,
+                                int64_t out_stride, int64_t njobs, double dt, int nsteps)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    if (njobs < 0 || nsteps < 0) return fail(CHEB_ERR_INVALID, "njobs and nsteps must be >= 0");
+    if (njobs > 0 && (!in || !out)) return fail(CHEB_ERR_INVALID, "cheb_evolve_host: NULL buffer");
+    const size_t jb = p->vec_bytes();
+    if ((in_stride != 0 && in_stride < (int64_t)jb) || (out_stride != 0 && out_stride < (int64_t)jb))
+        return fail(CHEB_ERR_INVALID, "cheb_evolve_host: a stride is neither 0 nor >= one state");
+    if (njobs > 1 && (const void*)out == in && (in_stride != out_stride || in_stride == 0))
+        return fail(CHEB_ERR_INVALID,
+                    "cheb_evolve_host: in and out alias but the jobs' states do not match up");
+    int rc = set_dt(p, dt);
+    if (rc) return rc;
+    if (njobs == 0) return CHEB_OK;
+    for (int b = 0; b < 2; ++b) {
+        if (!p->d_job[b] && cudaMalloc(&p->d_job[b], jb) != cudaSuccess)
+            return fail(CHEB_ERR_NOMEM, "cheb_evolve_host: job buffers");
+        for (cudaEvent_t* e : {&p->ev_in[b], &p->ev_done[b], &p->ev_out[b]})
+            if (!*e) CHEB_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    if (!p->h2d_stream) CHEB_CUDA(cudaStreamCreateWithFlags(&p->h2d_stream, cudaStreamNonBlocking));
+    if (!p->d2h_stream) CHEB_CUDA(cudaStreamCreateWithFlags(&p->d2h_stream, cudaStreamNonBlocking));
+    Plan::StepGraph* graph[2] = {nullptr, nullptr};
+    if (!p->timing && nsteps > 0) {
+        for (int b = 0; b < 2; ++b) {
+            rc = ensure_graph(p, p->d_job[b], &graph[b]);
+            if (rc) return rc;
+        }
+    }
+    const char* src = static_cast<const char*>(in);
+    char* dst = static_cast<char*>(out);
+    auto copy_in = [&](int64_t j) -> int {
+        const int b = (int)(j & 1);
+        if (j >= 2) CHEB_CUDA(cudaStreamWaitEvent(p->h2d_stream, p->ev_out[b], 0));  // buffer free
+        CHEB_CUDA(cudaMemcpyAsync(p->d_job[b], src + (size_t)j * (size_t)in_stride, jb,
+                                  cudaMemcpyHostToDevice, p->h2d_stream));
+        CHEB_CUDA(cudaEventRecord(p->ev_in[b], p->h2d_stream));
+        return CHEB_OK;
+    };
+    rc = copy_in(0);
+    if (rc) return rc;
+    for (int64_t j = 0; j < njobs; ++j) {
+        const int b = (int)(j & 1);
+        if (j + 1 < njobs) {
+            rc = copy_in(j + 1);
+            if (rc) return rc;
+        }
+        CHEB_CUDA(cudaStreamWaitEvent(p->stream, p->ev_in[b], 0));
+        for (int s = 0; s < nsteps; ++s) {
+            if (graph[b]) {
+                CHEB_CUDA(cudaGraphLaunch(graph[b]->exec, p->stream));
+                p->launches += graph[b]->kernels;
+            } else {
+                rc = enqueue_step(p, p->d_job[b], p->stream);
+                if (rc) return rc;
+            }
+        }
+        CHEB_CUDA(cudaEventRecord(p->ev_done[b], p->stream));
+        CHEB_CUDA(cudaStreamWaitEvent(p->d2h_stream, p->ev_done[b], 0));
+        CHEB_CUDA(cudaMemcpyAsync(dst + (size_t)j * (size_t)out_stride, p->d_job[b], jb,
+                                  cudaMemcpyDeviceToHost, p->d2h_stream));
+        CHEB_CUDA(cudaEventRecord(p->ev_out[b], p->d2h_stream));
+    }
+    CHEB_CUDA(cudaStreamSynchronize(p->d2h_stream));
     return cheb_sync(plan);
 }
 

@@ -244,14 +244,27 @@ struct Plan {
     int64_t tile = 256;
     bool tuned = false;
 
-    // graph of one step (rebuilt when the psi pointer, dt or the launch shape change)
+    // graphs of one step, one per psi pointer (a few kept; rebuilt when dt or the launch
+    // shape change)
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        const void* psi = nullptr;
+        int64_t epoch = -1;
+        int kernels = 0;
+        int64_t used = 0;
+    };
+    static constexpr int kGraphSlots = 4;
+    StepGraph graphs[kGraphSlots];
+    int64_t graph_clock = 0;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    const void* graph_psi = nullptr;
-    double graph_dt = 0.0;
-    int graph_kernels = 0;
-    int64_t graph_epoch = -1;
     int64_t shape_epoch = 0;  // bumped whenever items / launch shape / coefficients change
+
+    // batches of jobs from host memory (cheb_evolve_host): two device buffers, a stream per
+    // copy direction and their events (created on first use)
+    void* d_job[2] = {nullptr, nullptr};
+    cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr},
+                ev_out[2] = {nullptr, nullptr};
 
     int64_t launches = 0;
 
