@@ -58,8 +58,8 @@ ALG_BYTES_PER_UNIT = {
 
 # DRAM bytes of one step of the default ensemble (dram__bytes_read.sum +
 # dram__bytes_write.sum over all launches of a step, one ncu pass), by blocking (orders per
-# launch, sites per thread); the launches per step follow from the schedule.
-TB_DRAM_BYTES_PER_STEP = {(5, 4): 10.866e9}
+# launch, sites per thread, threads per CTA); the launches per step follow from the schedule.
+TB_DRAM_BYTES_PER_STEP = {(5, 4, 256): 10.866e9}
 
 # DRAM bytes of one step of the paper's polaron run with the matrix-free operator, by
 # (precision, M), same capture method
@@ -90,8 +90,9 @@ def parse():
                     help="L:NPH -- Holstein chain size for --workload holstein (profiling runs; "
                          "default 12:10)")
     ap.add_argument("--blocking", default=None,
-                    help="S:SPT -- force S orders per launch with SPT sites per thread and skip "
-                         "the autotuner (profiling runs); 0:0 forces single-order launches")
+                    help="S:SPT[:THREADS] -- force S orders per launch with SPT sites per thread "
+                         "(THREADS per CTA, default 256) and skip the autotuner (profiling "
+                         "runs); 0:0 forces single-order launches")
     return ap.parse_args()
 
 
@@ -291,8 +292,10 @@ def run_ours(args, world, rank, local):
     if args.blocking is None:
         plan.autotune()
     else:
-        bs, bspt = (int(x) for x in args.blocking.split(":"))
-        plan.set_blocking(bs, bspt if bs else 4)
+        parts = [int(x) for x in args.blocking.split(":")]
+        bs, bspt = parts[0], parts[1]
+        btpb = parts[2] if len(parts) > 2 else 256
+        plan.set_blocking(bs, bspt if bs else 4, btpb if bs else 256)
     Ms = [plan.block(q)["M"] for q in range(ens.n_ribbons)]
     sites = [w * l for w, l in ens.sizes]
     mv_per_step = ens.nvec * sum(Ms)
@@ -333,13 +336,13 @@ def run_ours(args, world, rank, local):
     alg_per_launch = ALG_BYTES_PER_UNIT[("ensemble", "c64")] * (ss_per_step / ens.nvec) / launches_per_step
     ms_per_launch = kms / kcount
     achieved = alg_per_launch / (ms_per_launch / 1e3) / 1e9  # GB/s
-    blk = tuple(plan.blocking())
+    blk = tuple(plan.blocking_shape())
     traffic = None
     if blk in TB_DRAM_BYTES_PER_STEP and sorted(set(Ms)) == [20, 21]:
         traffic = TB_DRAM_BYTES_PER_STEP[blk] / launches_per_step
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": ("k_rec_tb<4,%d> (all launches of the step)" % blk[1]
+                "kernel": ("k_rec_tb<4,%d,%d> (all launches of the step)" % (blk[1], blk[2])
                            if blk[0] else
                            "k_rec<float,%d,StencilOp> (all launches of the step)"
                            % plan.launch_shape()[3]),
@@ -451,8 +454,8 @@ def run_ours(args, world, rank, local):
             "l2": f"inputs larger than L2 (working set {wss:.2f} GB of vectors)",
             "launch_shape": dict(zip(("threads", "sites_per_thread", "grid", "vecs_per_thread"),
                                      plan.launch_shape())),
-            "temporal_blocking": dict(zip(("orders_per_launch", "sites_per_thread"),
-                                          plan.blocking())),
+            "temporal_blocking": dict(zip(("orders_per_launch", "sites_per_thread", "threads"),
+                                          plan.blocking_shape())),
             "parallelism": f"replicas x{world} (one ensemble per GPU)",
         },
         "site_vector_steps_per_s": site_steps,

@@ -281,10 +281,14 @@ int cheb_holstein_phonon_neighbors(int L, int nph, int64_t p0, int64_t count, in
 int cheb_autotune(cheb_plan* plan);
 /* Temporal blocking (complex64 lattice plans with nvec 1, 2 or 4 and a shared on-site
    array): orders_per_launch s > 0 makes each launch run s recurrence orders out of shared
-   memory on 2-D tiles of each ribbon with an s-site halo (sites_per_thread 4, 6 or 8 sets the
-   tile budget, 256 threads x sites_per_thread region sites); s = 0 returns to one order per
-   launch.  CHEB_ERR_UNSUPPORTED for other plans.  cheb_autotune also chooses these. */
-int cheb_plan_set_blocking(cheb_plan* plan, int orders_per_launch, int sites_per_thread);
+   memory on 2-D tiles of each ribbon with an s-site halo; a CTA of `threads` threads holds a
+   region of threads x sites_per_thread sites.  Compiled shapes (nvec: sites_per_thread x
+   threads): 256 threads with 4, 6 or 8 (8 only for nvec <= 2); nvec 4 also 3, 4, 6 x 512 and
+   2, 3 x 1024; nvec 2 also 6 x 1024; nvec 1 also 8 x 1024.  threads = 0 means 256.  s = 0
+   returns to one order per launch.  CHEB_ERR_UNSUPPORTED for other plans, CHEB_ERR_INVALID
+   for a shape that is not compiled.  cheb_autotune also chooses these. */
+int cheb_plan_set_blocking(cheb_plan* plan, int orders_per_launch, int sites_per_thread,
+                           int threads);
 
 /* Launch shape chosen for the plan: threads per block, sites per thread, grid size, and
    vectors handled per thread (of the nvec at each site).  Matrix-free Holstein plans report
@@ -292,8 +296,10 @@ int cheb_plan_set_blocking(cheb_plan* plan, int orders_per_launch, int sites_per
    thread advances together (1 or 2) in place of vectors per thread. */
 int cheb_plan_launch(const cheb_plan* plan, int* threads, int* sites_per_thread, int* grid,
                      int* vecs_per_thread);
-/* Orders per launch and sites per thread of the temporal blocking in use (0, 0: off). */
-int cheb_plan_blocking(const cheb_plan* plan, int* orders_per_launch, int* sites_per_thread);
+/* Orders per launch, sites per thread and threads per CTA of the temporal blocking in use
+   (0, 0, 0: off). */
+int cheb_plan_blocking(const cheb_plan* plan, int* orders_per_launch, int* sites_per_thread,
+                       int* threads);
 
 /* ---- introspection for tests ---------------------------------------------------------- */
 /* Copies of the plan's device data to host memory, for checking the construction:

@@ -97,8 +97,8 @@ _SIGS = {
                                         _i64p], _c.c_int),
     "cheb_autotune": ([_vp], _c.c_int),
     "cheb_plan_launch": ([_vp, _ip, _ip, _ip, _ip], _c.c_int),
-    "cheb_plan_set_blocking": ([_vp, _c.c_int, _c.c_int], _c.c_int),
-    "cheb_plan_blocking": ([_vp, _ip, _ip], _c.c_int),
+    "cheb_plan_set_blocking": ([_vp, _c.c_int, _c.c_int, _c.c_int], _c.c_int),
+    "cheb_plan_blocking": ([_vp, _ip, _ip, _ip], _c.c_int),
     "cheb_plan_export_csr": ([_vp, _i64p, _i64p, _dp, _i64p], _c.c_int),
     "cheb_plan_launches": ([_vp], _c.c_int64),
     "cheb_plan_set_timing": ([_vp, _c.c_int], _c.c_int),
@@ -334,16 +334,20 @@ class Plan:
                                      ctypes.byref(g), ctypes.byref(v)), "cheb_plan_launch")
         return t.value, s.value, g.value, v.value
 
-    def set_blocking(self, orders_per_launch: int, sites_per_thread: int = 4):
-        check(lib().cheb_plan_set_blocking(self.handle, orders_per_launch, sites_per_thread),
-              "cheb_plan_set_blocking")
+    def set_blocking(self, orders_per_launch: int, sites_per_thread: int = 4, threads: int = 256):
+        check(lib().cheb_plan_set_blocking(self.handle, orders_per_launch, sites_per_thread,
+                                           threads), "cheb_plan_set_blocking")
 
     def blocking(self):
         """(orders per launch, sites per thread); (0, 0) when off."""
-        s, t = ctypes.c_int(), ctypes.c_int()
-        check(lib().cheb_plan_blocking(self.handle, ctypes.byref(s), ctypes.byref(t)),
-              "cheb_plan_blocking")
-        return s.value, t.value
+        return self.blocking_shape()[:2]
+
+    def blocking_shape(self):
+        """(orders per launch, sites per thread, threads per CTA); zeros when off."""
+        s, t, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib().cheb_plan_blocking(self.handle, ctypes.byref(s), ctypes.byref(t),
+                                       ctypes.byref(n)), "cheb_plan_blocking")
+        return s.value, t.value, n.value
 
     def launches(self) -> int:
         return int(lib().cheb_plan_launches(self.handle))

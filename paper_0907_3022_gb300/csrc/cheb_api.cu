@@ -279,7 +279,7 @@ static int tb_prepare(Plan* p)
         minM = std::min(minM, (int)B.M);
         maxM = std::max(maxM, (int)B.M);
     }
-    int rc0 = tb_configure(p->nvec, p->tb_spt);
+    int rc0 = tb_configure(p->nvec, p->tb_spt, p->tb_tpb);
     if (rc0) {
         p->tb_s = 0;
         return rc0;
@@ -1057,14 +1057,17 @@ extern "C" int cheb_autotune(cheb_plan* plan)
         p->tb_sched.clear();
         float best_ms = 0.0f;
         rc = time_steps(&best_ms);
-        int best_s = 0, best_spt = p->tb_spt;
-        const int spts[] = {4, 6, 8};
-        for (int spt : spts) {
+        int best_s = 0, best_spt = p->tb_spt, best_tpb = p->tb_tpb;
+        const int shapes[][2] = {{4, 256}, {6, 256}, {8, 256}, {3, 512}, {4, 512}, {6, 512},
+                                 {2, 1024}, {3, 1024}, {6, 1024}, {8, 1024}};
+        for (const auto& sh : shapes) {
             if (rc) break;
-            if (spt == 8 && p->nvec == 4) continue;
+            const int spt = sh[0], tpb = sh[1];
+            if (!tb_supported(p->nvec, spt, tpb)) continue;
             for (int s_try : {2, 3, 4, 5, 6, 8}) {
                 p->tb_s = s_try;
                 p->tb_spt = spt;
+                p->tb_tpb = tpb;
                 for (TBSet& t : p->tb_sets) {  // tiles depend on the region budget (spt)
                     cudaFree(t.d_tiles);
                     cudaFree(t.d_begin);
@@ -1080,6 +1083,7 @@ extern "C" int cheb_autotune(cheb_plan* plan)
                     best_ms = ms;
                     best_s = s_try;
                     best_spt = spt;
+                    best_tpb = tpb;
                 }
             }
         }
@@ -1090,6 +1094,7 @@ extern "C" int cheb_autotune(cheb_plan* plan)
         p->tb_sets.clear();
         p->tb_s = best_s;
         p->tb_spt = best_spt;
+        p->tb_tpb = best_tpb;
         int rc3 = tb_prepare(p);
         if (!rc) rc = rc3;
         CHEB_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream));
@@ -1174,7 +1179,7 @@ extern "C" int cheb_plan_kernel_stats(cheb_plan* plan, double* ms, int64_t* laun
     return CHEB_OK;
 }
 
-extern "C" int cheb_plan_set_blocking(cheb_plan* plan, int s, int spt)
+extern "C" int cheb_plan_set_blocking(cheb_plan* plan, int s, int spt, int threads)
 {
     Plan* p = reinterpret_cast<Plan*>(plan);
     if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
@@ -1182,17 +1187,20 @@ extern "C" int cheb_plan_set_blocking(cheb_plan* plan, int s, int spt)
     if (s > 0 && !tb_eligible(p))
         return fail(CHEB_ERR_UNSUPPORTED, "temporal blocking needs a complex64 lattice plan with "
                                           "nvec 1, 2 or 4 and a shared on-site array");
-    if (s > 0 && spt != 4 && spt != 6 && spt != 8)
-        return fail(CHEB_ERR_INVALID, "sites_per_thread must be 4, 6 or 8");
-    if (s > 0 && spt == 8 && p->nvec == 4)
-        return fail(CHEB_ERR_INVALID, "sites_per_thread 8 needs nvec <= 2");
+    if (threads == 0) threads = 256;
+    if (s > 0 && !tb_supported(p->nvec, spt, threads))
+        return fail(CHEB_ERR_INVALID, "temporal blocking: this (nvec, sites_per_thread, threads) "
+                                      "shape is not compiled");
     for (TBSet& t : p->tb_sets) {
         cudaFree(t.d_tiles);
         cudaFree(t.d_begin);
     }
     p->tb_sets.clear();
     p->tb_s = s;
-    if (s > 0) p->tb_spt = spt;
+    if (s > 0) {
+        p->tb_spt = spt;
+        p->tb_tpb = threads;
+    }
     p->tb_sched.clear();
     p->shape_epoch++;
     int rc = tb_prepare(p);
@@ -1202,12 +1210,13 @@ extern "C" int cheb_plan_set_blocking(cheb_plan* plan, int s, int spt)
     return CHEB_OK;
 }
 
-extern "C" int cheb_plan_blocking(const cheb_plan* plan, int* s, int* spt)
+extern "C" int cheb_plan_blocking(const cheb_plan* plan, int* s, int* spt, int* threads)
 {
     const Plan* p = reinterpret_cast<const Plan*>(plan);
     if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
     const bool on = p->tb_s > 0 && tb_eligible(p);
     if (s) *s = on ? p->tb_s : 0;
     if (spt) *spt = on ? p->tb_spt : 0;
+    if (threads) *threads = on ? p->tb_tpb : 0;
     return CHEB_OK;
 }

@@ -154,9 +154,10 @@ struct TBSet {
 struct Plan;
 
 // temporal blocking (cheb_tb.cu)
-size_t tb_smem_bytes(int nv, int spt);
+size_t tb_smem_bytes(int nv, int spt, int tpb);
+bool tb_supported(int nv, int spt, int tpb);
 int tb_launch(Plan* p, const TBArgs& a, cudaStream_t s);
-int tb_configure(int nv, int spt);
+int tb_configure(int nv, int spt, int tpb);
 bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vector<int32_t>& begin);
 
 // kernel launchers (cheb_kernels.cu)
@@ -271,6 +272,7 @@ struct Plan {
     // temporal blocking (complex64 stencils): orders per launch (0: off), sites per thread
     int tb_s = 0;
     int tb_spt = 4;
+    int tb_tpb = 256;         // threads per CTA of the blocked kernel
     int tb_grid_cap = 0;
     void* d_C = nullptr;      // second recurrence pair and the main accumulator
     void* d_D = nullptr;

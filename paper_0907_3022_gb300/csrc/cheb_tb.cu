@@ -28,7 +28,24 @@
 
 namespace cheb {
 
-static constexpr int TB_THREADS = 256;
+// Shared memory of one CTA: two float2 planes per vector and the float on-site plane, for a
+// region of TPB * SPT sites.
+__host__ __device__ constexpr size_t tb_smem(int nv, int spt, int tpb)
+{
+    return 2 * (size_t)nv * tpb * spt * sizeof(float2) + (size_t)tpb * spt * sizeof(float);
+}
+
+// CTAs per SM the launch bounds ask for: 256-thread CTAs as tuned (3 up to 4 sites per
+// thread, else 2); larger CTAs as many as shared memory (227 KB per SM) and the 2048-thread
+// limit allow
+__host__ __device__ constexpr int tb_min_blocks(int nv, int spt, int tpb)
+{
+    if (tpb == 256) return spt <= 4 ? 3 : 2;
+    const size_t by_smem = 232448 / (tb_smem(nv, spt, tpb) + 1024);
+    const size_t by_threads = 2048 / tpb;
+    const size_t b = by_smem < by_threads ? by_smem : by_threads;
+    return b < 1 ? 1 : (int)b;
+}
 
 template <int NV>
 struct TBCplx {
@@ -84,9 +101,10 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <int NV, int SPT, bool FIRST>
-__global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArgs a)
+template <int NV, int SPT, bool FIRST, int TPB>
+__global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBArgs a)
 {
+    constexpr int TB_THREADS = TPB;
     constexpr int RMAX = TB_THREADS * SPT;
     extern __shared__ float4 tb_smem_raw[];
     float2* const sP0 = reinterpret_cast<float2*>(tb_smem_raw);  // [NV][RMAX]
@@ -306,48 +324,51 @@ __global__ void __launch_bounds__(TB_THREADS, (SPT <= 4 ? 3 : 2)) k_rec_tb(TBArg
     }
 }
 
-size_t tb_smem_bytes(int nv, int spt)
-{
-    const size_t rmax = (size_t)TB_THREADS * spt;
-    return 2 * (size_t)nv * rmax * sizeof(float2) + rmax * sizeof(float);
-}
+size_t tb_smem_bytes(int nv, int spt, int tpb) { return tb_smem(nv, spt, tpb); }
 
-template <int NV, int SPT>
+template <int NV, int SPT, int TPB>
 static int tb_launch_t(const TBArgs& a, int grid, cudaStream_t s)
 {
-    const size_t smem = tb_smem_bytes(NV, SPT);
-    if (a.ka == 1) k_rec_tb<NV, SPT, true><<<grid, TB_THREADS, smem, s>>>(a);
-    else k_rec_tb<NV, SPT, false><<<grid, TB_THREADS, smem, s>>>(a);
+    const size_t smem = tb_smem(NV, SPT, TPB);
+    if (a.ka == 1) k_rec_tb<NV, SPT, true, TPB><<<grid, TPB, smem, s>>>(a);
+    else k_rec_tb<NV, SPT, false, TPB><<<grid, TPB, smem, s>>>(a);
     CHEB_CUDA(cudaGetLastError());
     return CHEB_OK;
 }
 
-template <int NV, int SPT>
+template <int NV, int SPT, int TPB>
 static int tb_attr_t()
 {
-    const int smem = (int)tb_smem_bytes(NV, SPT);
-    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tb<NV, SPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tb<NV, SPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int smem = (int)tb_smem(NV, SPT, TPB);
+    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tb<NV, SPT, true, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tb<NV, SPT, false, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     return CHEB_OK;
 }
 
-// Allow the dynamic shared memory of the (nv, spt) instantiation; called while the schedule
-// is prepared, outside any stream capture.
-int tb_configure(int nv, int spt)
+// The (vectors, sites per thread, threads per CTA) shapes compiled: regions of 256 x 4..8
+// sites (2-3 CTAs per SM) and one large CTA per SM (512 or 1024 threads) with the largest
+// region the shared memory holds for the vector count.
+#define CHEB_TB_SHAPES(X)                                                                  \
+    X(4, 4, 256) X(2, 4, 256) X(1, 4, 256) X(4, 6, 256) X(2, 6, 256) X(1, 6, 256)          \
+    X(2, 8, 256) X(1, 8, 256) X(4, 3, 512) X(4, 4, 512) X(4, 6, 512) X(4, 2, 1024)         \
+    X(4, 3, 1024) X(2, 6, 1024) X(1, 8, 1024)
+
+bool tb_supported(int nv, int spt, int tpb)
 {
-    if (spt == 4) {
-        if (nv == 4) return tb_attr_t<4, 4>();
-        if (nv == 2) return tb_attr_t<2, 4>();
-        if (nv == 1) return tb_attr_t<1, 4>();
-    } else if (spt == 6) {
-        if (nv == 4) return tb_attr_t<4, 6>();
-        if (nv == 2) return tb_attr_t<2, 6>();
-        if (nv == 1) return tb_attr_t<1, 6>();
-    } else if (spt == 8) {
-        if (nv == 2) return tb_attr_t<2, 8>();
-        if (nv == 1) return tb_attr_t<1, 8>();
-    }
-    return fail(CHEB_ERR_UNSUPPORTED, "temporal blocking: unsupported nvec / sites per thread");
+#define CHEB_TB_IS(NV, SPT, TPB) if (nv == NV && spt == SPT && tpb == TPB) return true;
+    CHEB_TB_SHAPES(CHEB_TB_IS)
+#undef CHEB_TB_IS
+    return false;
+}
+
+// Allow the dynamic shared memory of the (nv, spt, tpb) instantiation; called while the
+// schedule is prepared, outside any stream capture.
+int tb_configure(int nv, int spt, int tpb)
+{
+#define CHEB_TB_ATTR(NV, SPT, TPB) if (nv == NV && spt == SPT && tpb == TPB) return tb_attr_t<NV, SPT, TPB>();
+    CHEB_TB_SHAPES(CHEB_TB_ATTR)
+#undef CHEB_TB_ATTR
+    return fail(CHEB_ERR_UNSUPPORTED, "temporal blocking: unsupported nvec / sites per thread / threads");
 }
 
 int tb_launch(Plan* p, const TBArgs& a, cudaStream_t s)
@@ -356,30 +377,22 @@ int tb_launch(Plan* p, const TBArgs& a, cudaStream_t s)
     if (p->tb_grid_cap > 0 && grid > p->tb_grid_cap) grid = p->tb_grid_cap;
     if (grid < 1) return CHEB_OK;
     int rc = CHEB_ERR_UNSUPPORTED;
-    const int nv = p->nvec;
-    if (p->tb_spt == 4) {
-        if (nv == 4) rc = tb_launch_t<4, 4>(a, grid, s);
-        else if (nv == 2) rc = tb_launch_t<2, 4>(a, grid, s);
-        else if (nv == 1) rc = tb_launch_t<1, 4>(a, grid, s);
-    } else if (p->tb_spt == 6) {
-        if (nv == 4) rc = tb_launch_t<4, 6>(a, grid, s);
-        else if (nv == 2) rc = tb_launch_t<2, 6>(a, grid, s);
-        else if (nv == 1) rc = tb_launch_t<1, 6>(a, grid, s);
-    } else if (p->tb_spt == 8) {
-        if (nv == 2) rc = tb_launch_t<2, 8>(a, grid, s);
-        else if (nv == 1) rc = tb_launch_t<1, 8>(a, grid, s);
-    }
-    if (rc == CHEB_ERR_UNSUPPORTED) return fail(rc, "temporal blocking: unsupported nvec / sites per thread");
+    const int nv = p->nvec, spt = p->tb_spt, tpb = p->tb_tpb;
+#define CHEB_TB_GO(NV, SPT, TPB) if (nv == NV && spt == SPT && tpb == TPB) rc = tb_launch_t<NV, SPT, TPB>(a, grid, s); else
+    CHEB_TB_SHAPES(CHEB_TB_GO) {}
+#undef CHEB_TB_GO
+    if (rc == CHEB_ERR_UNSUPPORTED)
+        return fail(rc, "temporal blocking: unsupported nvec / sites per thread / threads");
     p->launches++;
     return rc;
 }
 
-// Tiles for a halo of s: row bands of at most 48 interior rows, then as many interior columns
-// as the region budget (TB_THREADS * spt sites) allows.  Returns false if a ribbon cannot be
+// Tiles for a halo of s: row bands chosen for the least halo waste, then as many interior
+// columns as the region budget (threads * spt sites) allows.  Returns false if a ribbon cannot be
 // tiled (the region of one interior column would not fit).
 bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vector<int32_t>& begin)
 {
-    const int rmax = TB_THREADS * p->tb_spt;
+    const int rmax = p->tb_tpb * p->tb_spt;
     tiles.clear();
     begin.assign(p->nblocks + 1, 0);
     for (int q = 0; q < p->nblocks; ++q) {

@@ -52,6 +52,40 @@ def test_blocked_matches_oracle_and_single_order(nvec, s, spt):
             assert rel(out_b[off[r]:off[r + 1], v], ref) <= 1e-4, (r, v)
 
 
+@pytest.mark.parametrize("nvec,spt,threads", [(4, 3, 512), (4, 4, 512), (4, 6, 512),
+                                               (4, 2, 1024), (4, 3, 1024), (2, 6, 1024),
+                                               (1, 8, 1024)])
+@pytest.mark.parametrize("s", [3, 6])
+def test_blocked_large_ctas(nvec, spt, threads, s):
+    """CTAs of 512 and 1024 threads (one large region per SM): same results as single-order
+    launches and the oracle on the edge-shape ensemble."""
+    import paper_0907_3022_gb300 as cb
+
+    ens = wl.RibbonEnsemble(n_ribbons=len(SIZES), sizes=list(SIZES), sigma=4.0,
+                            k0s=wl.ENSEMBLE_K0[:nvec])
+    nsteps = 5
+    x0 = dev_vec(ens.packets(), C64)
+    ref_plan = _plan(cb, ens, nvec)
+    a = x0.clone()
+    ref_plan.evolve(a, ens.dt, nsteps)
+    plan = _plan(cb, ens, nvec)
+    plan.evolve(x0, ens.dt, 0)
+    plan.set_blocking(s, spt, threads)
+    assert plan.blocking_shape() == (s, spt, threads)
+    b = x0.clone()
+    plan.evolve(b, ens.dt, nsteps)
+    out_a, out_b = host(a), host(b)
+    assert rel(out_b, out_a) <= 2e-6
+    off = ens.offsets()
+    for r in (0, 3, 4, 6):
+        W, L = ens.sizes[r]
+        ref, M = oracle_ribbon(W, L, ens.disorder(r), ens.seed, r, ens.k0s[0], nsteps, sigma=4.0)
+        assert rel(out_b[off[r]:off[r + 1], 0], ref) <= 1e-4, r
+    with pytest.raises(cb.ChebError) as e:  # a shape that is not compiled
+        plan.set_blocking(s, 5, threads)
+    assert e.value.status == cb.CHEB_ERR_INVALID
+
+
 def test_blocked_small_orders_and_observables():
     """dt = 0.001 gives M of about 5 per ribbon: with 6 orders per launch the first launch is
     cut to M_min - 1 orders and every ribbon's last order falls inside the second launch."""
