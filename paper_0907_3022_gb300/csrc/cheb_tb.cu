@@ -47,10 +47,39 @@ __host__ __device__ constexpr int tb_min_blocks(int nv, int spt, int tpb)
     return b < 1 ? 1 : (int)b;
 }
 
-template <int NV>
-struct TBCplx {
-    float2 v[NV];
+// Shared-memory planes: one float2 plane for a single vector, else one float4 plane per pair
+// of vectors (vectors 2p and 2p + 1 of a site side by side), so that region loads, neighbour
+// reads and stores move 16 bytes at a time.
+template <int NV> struct TBPlane {
+    using T = float4;
+    static constexpr int NP = NV / 2;  // planes
+    static constexpr int PER = 2;      // vectors per plane element
 };
+template <> struct TBPlane<1> {
+    using T = float2;
+    static constexpr int NP = 1;
+    static constexpr int PER = 1;
+};
+
+__device__ __forceinline__ float2 tb_get(const float2& t, int) { return t; }
+__device__ __forceinline__ float2 tb_get(const float4& t, int c)
+{
+    return c ? make_float2(t.z, t.w) : make_float2(t.x, t.y);
+}
+__device__ __forceinline__ void tb_set(float2& t, int, const float2 v) { t = v; }
+__device__ __forceinline__ void tb_set(float4& t, int c, const float2 v)
+{
+    if (c) {
+        t.z = v.x;
+        t.w = v.y;
+    } else {
+        t.x = v.x;
+        t.y = v.y;
+    }
+}
+template <typename T> __device__ __forceinline__ T tb_zero();
+template <> __device__ __forceinline__ float2 tb_zero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ float4 tb_zero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
 // split of a double into hi + lo floats
 __device__ __forceinline__ void tb_split(double x, float& hi, float& lo)
@@ -95,6 +124,13 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc)
     const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_el(float2* sdst, const float2* gsrc) { cp_async8(sdst, gsrc); }
+__device__ __forceinline__ void cp_async_el(float4* sdst, const float4* gsrc) { cp_async16(sdst, gsrc); }
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -104,21 +140,24 @@ __device__ __forceinline__ void cp_async_wait_all()
 template <int NV, int SPT, bool FIRST, int TPB>
 __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBArgs a)
 {
+    using PT = typename TBPlane<NV>::T;
+    constexpr int NP = TBPlane<NV>::NP, PER = TBPlane<NV>::PER;
     constexpr int TB_THREADS = TPB;
     constexpr int RMAX = TB_THREADS * SPT;
     extern __shared__ float4 tb_smem_raw[];
-    float2* const sP0 = reinterpret_cast<float2*>(tb_smem_raw);  // [NV][RMAX]
-    float2* const sQ0 = sP0 + NV * RMAX;                          // [NV][RMAX]
-    float* const sD = reinterpret_cast<float*>(sQ0 + NV * RMAX);  // [RMAX]
+    PT* const sP0 = reinterpret_cast<PT*>(tb_smem_raw);         // [NP][RMAX]
+    PT* const sQ0 = sP0 + NP * RMAX;                              // [NP][RMAX]
+    float* const sD = reinterpret_cast<float*>(sQ0 + NP * RMAX);  // [RMAX]
     __shared__ double s_red[(TB_THREADS / 32) * 2 * NV];
 
-    const float2* __restrict__ in_prev = static_cast<const float2*>(a.in_prev);
-    const float2* __restrict__ in_cur = static_cast<const float2*>(a.in_cur);
-    float2* __restrict__ out_prev = static_cast<float2*>(a.out_prev);
-    float2* __restrict__ out_cur = static_cast<float2*>(a.out_cur);
-    float2* __restrict__ accE = static_cast<float2*>(a.acc_main);
-    float2* __restrict__ tail = static_cast<float2*>(a.tail);
-    float2* __restrict__ psi = static_cast<float2*>(a.psi);
+    // global vectors seen as NP plane elements per site
+    const PT* __restrict__ in_prev = static_cast<const PT*>(a.in_prev);
+    const PT* __restrict__ in_cur = static_cast<const PT*>(a.in_cur);
+    PT* __restrict__ out_prev = static_cast<PT*>(a.out_prev);
+    PT* __restrict__ out_cur = static_cast<PT*>(a.out_cur);
+    PT* __restrict__ accE = static_cast<PT*>(a.acc_main);
+    PT* __restrict__ tail = static_cast<PT*>(a.tail);
+    PT* __restrict__ psi = static_cast<PT*>(a.psi);
     const float* __restrict__ diag = static_cast<const float*>(a.diag);
     const float2* __restrict__ qc = static_cast<const float2*>(a.qcoef);
     const int tid = threadIdx.x;
@@ -132,13 +171,13 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
         // grid reductions that follow are FP64
         float part[FIRST ? 2 * NV : 1];
 #pragma unroll
-        for (int s = 0; s < (FIRST ? 2 * NV : 1); ++s) part[s] = 0.f;
+        for (int q = 0; q < (FIRST ? 2 * NV : 1); ++q) part[q] = 0.f;
         if (a.ka <= B.M) {
             const int ke = min(a.kb, B.M);
             const bool done = (ke == B.M);
             const int RW = T.C1 - T.C0, RH = T.R1 - T.R0;
             const int nreg = RW * RH;
-            // region coordinates of this thread's positions tid + j * 256 (row-major region)
+            // region coordinates of this thread's positions tid + j * TPB (row-major region)
             int srr[SPT], scc[SPT];
 #pragma unroll
             for (int j = 0; j < SPT; ++j) {
@@ -154,10 +193,10 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                 if (idx < nreg) {
                     const int64_t g = B.offset + (int64_t)(T.R0 + srr[j]) * B.L + (T.C0 + scc[j]);
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        cp_async8(&sQ0[v * RMAX + idx], &in_cur[g * NV + v]);
-                        if (first) sP0[v * RMAX + idx] = make_float2(0.f, 0.f);
-                        else cp_async8(&sP0[v * RMAX + idx], &in_prev[g * NV + v]);
+                    for (int p = 0; p < NP; ++p) {
+                        cp_async_el(&sQ0[p * RMAX + idx], &in_cur[g * NP + p]);
+                        if (first) sP0[p * RMAX + idx] = tb_zero<PT>();
+                        else cp_async_el(&sP0[p * RMAX + idx], &in_prev[g * NP + p]);
                     }
                     cp_async4(&sD[idx], &diag[g]);
                 }
@@ -184,20 +223,24 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                     if (!inter[j]) continue;
                     const int idx = tid + j * TB_THREADS;
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) tb_accum(acc[j][v], q0, sQ0[v * RMAX + idx], 0);
+                    for (int p = 0; p < NP; ++p) {
+                        const PT x = sQ0[p * RMAX + idx];
+#pragma unroll
+                        for (int c = 0; c < PER; ++c) tb_accum(acc[j][p * PER + c], q0, tb_get(x, c), 0);
+                    }
                 }
             }
             // ---- s recurrence orders in shared memory -------------------------------------
-            float2* sP = sP0;
-            float2* sQ = sQ0;
+            PT* sP = sP0;
+            PT* sQ = sQ0;
             const bool open_t = T.R0 > 0, open_b = T.R1 < B.W, open_l = T.C0 > 0, open_r = T.C1 < B.L;
             for (int k = a.ka; k <= ke; ++k) {
                 const int sh = k - a.ka + 1;
                 const int rlo = open_t ? sh : 0, rhi = RH - (open_b ? sh : 0);
                 const int clo = open_l ? sh : 0, chi = RW - (open_r ? sh : 0);
                 const float2 qk = qc[B.coef_off + k];
-                float2* __restrict__ Pw = sP;        // T_{k-2} in, T_k out (own site only)
-                const float2* __restrict__ Qr = sQ;  // T_{k-1}, read at the site and neighbours
+                PT* __restrict__ Pw = sP;        // T_{k-2} in, T_k out (own site only)
+                const PT* __restrict__ Qr = sQ;  // T_{k-1}, read at the site and neighbours
 #pragma unroll
                 for (int j = 0; j < SPT; ++j) {
                     const int rr = srr[j], cc = scc[j];
@@ -211,39 +254,48 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                     const int vidx = up ? idx - RW : idx + RW;
                     const float d = sD[idx];
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        const float2* Q = Qr + v * RMAX;
-                        const float2 x = Q[idx];
-                        const float2 yl = hl ? Q[il] : make_float2(0.f, 0.f);
-                        const float2 yr = hr ? Q[ir] : make_float2(0.f, 0.f);
-                        const float2 yv = hv ? Q[vidx] : make_float2(0.f, 0.f);
-                        const float2 p = Pw[v * RMAX + idx];
-                        const float sx = (yl.x + yr.x) + yv.x;
-                        const float sy = (yl.y + yr.y) + yv.y;
-                        float hx = fmaf(bl, sx, -p.x), hy = fmaf(bl, sy, -p.y);
-                        hx = fmaf(bh, sx, hx);
-                        hy = fmaf(bh, sy, hy);
-                        hx = fmaf(d, x.x, hx);
-                        hy = fmaf(d, x.y, hy);
-                        if (k == 1) {  // T_1 = H~ T_0 (p = 0)
-                            hx *= 0.5f;
-                            hy *= 0.5f;
-                        }
-                        const float2 h = make_float2(hx, hy);
-                        Pw[v * RMAX + idx] = h;
-                        if (inter[j]) {
-                            tb_accum(acc[j][v], qk, h, k);
-                            if constexpr (FIRST) {
-                                if (k == 1) {
-                                    part[2 * v + 0] = fmaf(x.x, x.x, fmaf(x.y, x.y, part[2 * v + 0]));
-                                    part[2 * v + 1] = fmaf(x.x, h.x, fmaf(x.y, h.y, part[2 * v + 1]));
+                    for (int p = 0; p < NP; ++p) {
+                        const PT* Q = Qr + p * RMAX;
+                        const PT xP = Q[idx];
+                        const PT ylP = hl ? Q[il] : tb_zero<PT>();
+                        const PT yrP = hr ? Q[ir] : tb_zero<PT>();
+                        const PT yvP = hv ? Q[vidx] : tb_zero<PT>();
+                        const PT pP = Pw[p * RMAX + idx];
+                        PT hP;
+#pragma unroll
+                        for (int cv = 0; cv < PER; ++cv) {
+                            const float2 x = tb_get(xP, cv), yl = tb_get(ylP, cv);
+                            const float2 yr = tb_get(yrP, cv), yv = tb_get(yvP, cv);
+                            const float2 pv = tb_get(pP, cv);
+                            const float sx = (yl.x + yr.x) + yv.x;
+                            const float sy = (yl.y + yr.y) + yv.y;
+                            float hx = fmaf(bl, sx, -pv.x), hy = fmaf(bl, sy, -pv.y);
+                            hx = fmaf(bh, sx, hx);
+                            hy = fmaf(bh, sy, hy);
+                            hx = fmaf(d, x.x, hx);
+                            hy = fmaf(d, x.y, hy);
+                            if (k == 1) {  // T_1 = H~ T_0 (p = 0)
+                                hx *= 0.5f;
+                                hy *= 0.5f;
+                            }
+                            const float2 h = make_float2(hx, hy);
+                            tb_set(hP, cv, h);
+                            if (inter[j]) {
+                                const int v = p * PER + cv;
+                                tb_accum(acc[j][v], qk, h, k);
+                                if constexpr (FIRST) {
+                                    if (k == 1) {
+                                        part[2 * v + 0] = fmaf(x.x, x.x, fmaf(x.y, x.y, part[2 * v + 0]));
+                                        part[2 * v + 1] = fmaf(x.x, h.x, fmaf(x.y, h.y, part[2 * v + 1]));
+                                    }
                                 }
                             }
                         }
+                        Pw[p * RMAX + idx] = hP;
                     }
                 }
                 __syncthreads();
-                float2* tmp = sP;
+                PT* tmp = sP;
                 sP = sQ;
                 sQ = tmp;
             }
@@ -257,27 +309,43 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                 const int idx = tid + j * TB_THREADS;
                 const int64_t g = B.offset + (int64_t)(T.R0 + srr[j]) * B.L + (T.C0 + scc[j]);
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    const float2 tk = sQ[v * RMAX + idx];
+                for (int p = 0; p < NP; ++p) {
+                    const PT tkP = sQ[p * RMAX + idx];
                     if (!first) {  // E (and the tail) this launch continues
-                        float2 e = make_float2(0.f, 0.f);
-                        if (to_main || done) e = accE[g * NV + v];
-                        if (!to_main && tail_has) {
-                            const float2 t2 = tail[g * NV + v];
-                            e = done ? make_float2(e.x + t2.x, e.y + t2.y) : t2;
+                        PT eP = tb_zero<PT>(), tP = tb_zero<PT>();
+                        if (to_main || done) eP = accE[g * NP + p];
+                        if (!to_main && tail_has) tP = tail[g * NP + p];
+#pragma unroll
+                        for (int cv = 0; cv < PER; ++cv) {
+                            float2 e = tb_get(eP, cv);
+                            if (!to_main && tail_has) {
+                                const float2 t2 = tb_get(tP, cv);
+                                e = done ? make_float2(e.x + t2.x, e.y + t2.y) : t2;
+                            }
+                            float2& av = acc[j][p * PER + cv];
+                            av = make_float2(e.x + av.x, e.y + av.y);
                         }
-                        acc[j][v] = make_float2(e.x + acc[j][v].x, e.y + acc[j][v].y);
                     }
+                    PT aP;
+#pragma unroll
+                    for (int cv = 0; cv < PER; ++cv) tb_set(aP, cv, acc[j][p * PER + cv]);
                     if (!done) {
-                        out_cur[g * NV + v] = tk;
-                        out_prev[g * NV + v] = sP[v * RMAX + idx];
-                        if (to_main) accE[g * NV + v] = acc[j][v];
-                        else tail[g * NV + v] = acc[j][v];
+                        out_cur[g * NP + p] = tkP;
+                        out_prev[g * NP + p] = sP[p * RMAX + idx];
+                        if (to_main) accE[g * NP + p] = aP;
+                        else tail[g * NP + p] = aP;
                     } else {
-                        psi[g * NV + v] = tb_phase(acc[j][v], ph, pl);  // E + tail + partial
-                        const double t2 = (double)tk.x * tk.x + (double)tk.y * tk.y;
-                        const double lim = 4.0 * a.norm2[((size_t)T.block * NV + v) * 2];
-                        if (!(t2 <= lim)) atomicOr(a.errflag, 1);
+                        PT oP;
+#pragma unroll
+                        for (int cv = 0; cv < PER; ++cv) {
+                            const int v = p * PER + cv;
+                            tb_set(oP, cv, tb_phase(acc[j][v], ph, pl));  // E + tail + partial
+                            const float2 tk = tb_get(tkP, cv);
+                            const double t2 = (double)tk.x * tk.x + (double)tk.y * tk.y;
+                            const double lim = 4.0 * a.norm2[((size_t)T.block * NV + v) * 2];
+                            if (!(t2 <= lim)) atomicOr(a.errflag, 1);
+                        }
+                        psi[g * NP + p] = oP;
                     }
                 }
             }
@@ -286,10 +354,10 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
             // per-tile partials of ||T_0||^2 and <T_0|H~ T_0>, fixed-order block reduction
             const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-            for (int s = 0; s < 2 * NV; ++s) {
-                double xs = (double)part[s];
+            for (int q = 0; q < 2 * NV; ++q) {
+                double xs = (double)part[q];
                 for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
-                if (lane == 0) s_red[warp * 2 * NV + s] = xs;
+                if (lane == 0) s_red[warp * 2 * NV + q] = xs;
             }
             __syncthreads();
             if (tid < 2 * NV) {
