@@ -267,7 +267,8 @@ static int tb_set_for(Plan* p, int s)
 }
 
 // Launch schedule of one step with temporal blocking: orders 1..s0 (s0 < min M, so the first
-// launch, which reads psi as T_0, never writes psi), then blocks of tb_s orders up to max M.
+// launch, which reads psi as T_0, never writes psi), then blocks of tb_s orders up to max M,
+// the last block lengthened instead of followed by a short one.
 // Builds the tile sets and buffers it needs (outside any stream capture).  On failure the
 // plan falls back to single-order launches (tb_s = 0).
 static int tb_prepare(Plan* p)
@@ -285,18 +286,29 @@ static int tb_prepare(Plan* p)
         return rc0;
     }
     const int s0 = std::max(1, std::min(p->tb_s, minM - 1));
+    // order ranges [ka, kb] of the launches; a last range shorter than half a block is merged
+    // into the one before (a launch costs its region loads and stores however few orders it
+    // runs), unless that is the first launch, which must stay below min M
+    std::vector<std::pair<int, int>> ranges;
+    for (int ka = 1, kb = s0; ka <= maxM; ka = kb + 1, kb = std::min(ka + p->tb_s - 1, maxM))
+        ranges.push_back({ka, kb});
+    if (ranges.size() >= 3 && 2 * (ranges.back().second - ranges.back().first + 1) < p->tb_s) {
+        const int len = ranges.back().second - ranges[ranges.size() - 2].first + 1;
+        if (tb_set_for(p, len) >= 0) {  // else the ribbons do not fit the wider halo: keep both
+            ranges[ranges.size() - 2].second = ranges.back().second;
+            ranges.pop_back();
+        }
+    }
     std::vector<Plan::TBLaunch> sched;
-    int ka = 1, kb = s0, prev = 0;
-    while (ka <= maxM) {
-        const int set = tb_set_for(p, kb - ka + 1);
+    int prev = 0;
+    for (const auto& rg : ranges) {
+        const int set = tb_set_for(p, rg.second - rg.first + 1);
         if (set < 0) {
             p->tb_s = 0;
             return set == -2 ? fail(CHEB_ERR_NOMEM, "temporal blocking tiles") : CHEB_OK;
         }
-        sched.push_back({ka, kb, prev, set});
-        prev = ka;
-        ka = kb + 1;
-        kb = std::min(ka + p->tb_s - 1, maxM);
+        sched.push_back({rg.first, rg.second, prev, set});
+        prev = rg.first;
     }
     const size_t vb = p->vec_bytes();
     for (void** b : {&p->d_C, &p->d_D, &p->d_E}) {

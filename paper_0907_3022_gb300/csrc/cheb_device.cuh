@@ -86,6 +86,35 @@ __device__ __forceinline__ void block_reduce_groups(double (&val)[NSUM], int nvg
     __syncthreads();
 }
 
+// The same for FP32 per-thread values (complex64 plans): the warp-level tree runs in FP32
+// (fixed pairwise order, relative error <= 5 ulp of the warp's sum of magnitudes), the
+// block-level sum in FP64.  FP64 arithmetic runs at ~1/64 of the FP32 rate on this GPU, and
+// a butterfly of NSUM doubles per thread cost more than the kernels' own site updates.
+template <int NSUM>
+__device__ __forceinline__ void block_reduce_groups_f(float (&val)[NSUM], int nvg, double* smem,
+                                                      double* gout)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int s = 0; s < NSUM; ++s) {
+        float x = val[s];
+        for (int off = 16; off >= nvg; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        val[s] = x;
+    }
+    if (lane < nvg) {
+#pragma unroll
+        for (int s = 0; s < NSUM; ++s) smem[(warp * nvg + lane) * NSUM + s] = (double)val[s];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nvg * NSUM) {
+        const int g = threadIdx.x / NSUM, s = threadIdx.x % NSUM;
+        double acc = 0.0;
+        for (int w = 0; w < nwarps; ++w) acc += smem[(w * nvg + g) * NSUM + s];
+        gout[threadIdx.x] = acc;
+    }
+    __syncthreads();
+}
+
 // ---- the fused recurrence: shared per-site update ----------------------------------------
 // complex64 plans carry the per-block constants (q_k, beta, e^{-i b dt}) as unevaluated sums
 // hi + lo of two floats: rounding each to one float would make every step's propagator

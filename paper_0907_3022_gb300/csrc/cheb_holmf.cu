@@ -222,8 +222,13 @@ __global__ void __launch_bounds__(MINB > 1 ? 256 : 512, MINB) k_rec_holmf(RecArg
             }
         }
         if (FIRST) {
-            double dpart[2] = {(double)part0, (double)part1};
-            block_reduce_groups<2>(dpart, nv, s_red, a.partials + (size_t)t * nv * 2);
+            if constexpr (Split<R>::on) {  // complex64: FP32 warp tree, FP64 block sum
+                float fpart[2] = {(float)part0, (float)part1};
+                block_reduce_groups_f<2>(fpart, nv, s_red, a.partials + (size_t)t * nv * 2);
+            } else {
+                double dpart[2] = {(double)part0, (double)part1};
+                block_reduce_groups<2>(dpart, nv, s_red, a.partials + (size_t)t * nv * 2);
+            }
         }
     }
     if (FIRST) holmf_finalize(a, m, B, s_red);

@@ -247,10 +247,14 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
         }
         if (first) {
             // partials[w][vec][2] = (||x||^2, <x|H~x>) of this tile; (g, v, comp) -> g*2VPT + 2v + comp
-            double dpart[2 * VPT];
+            if constexpr (Split<R>::on) {  // complex64: FP32 warp tree, FP64 block sum
+                block_reduce_groups_f<2 * VPT>(part, nvg, s_red, a.partials + (size_t)w * nv * 2);
+            } else {
+                double dpart[2 * VPT];
 #pragma unroll
-            for (int s = 0; s < 2 * VPT; ++s) dpart[s] = (double)part[s];
-            block_reduce_groups<2 * VPT>(dpart, nvg, s_red, a.partials + (size_t)w * nv * 2);
+                for (int s = 0; s < 2 * VPT; ++s) dpart[s] = (double)part[s];
+                block_reduce_groups<2 * VPT>(dpart, nvg, s_red, a.partials + (size_t)w * nv * 2);
+            }
         }
     }
     if (first) finalize_first(a);

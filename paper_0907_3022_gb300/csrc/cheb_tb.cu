@@ -205,12 +205,39 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
             float2 acc[SPT][NV];
             const bool to_main = first || (a.ka <= B.ksplit);
             const bool tail_has = a.prev_ka > B.ksplit;  // an earlier launch wrote the tail
+            // the accumulator this launch continues, read now so that its latency hides behind
+            // the region copies: E (main), the tail, or E + tail at the ribbon's last order
+            const bool read_e = !first && (to_main || done);
+            const bool read_t = !first && !to_main && tail_has;
 #pragma unroll
             for (int j = 0; j < SPT; ++j) {
                 const int r = T.R0 + srr[j], c = T.C0 + scc[j];
                 inter[j] = (r >= T.r0) && (r < T.r1) && (c >= T.c0) && (c < T.c1);
+                PT eP[NP], tP[NP];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) acc[j][v] = make_float2(0.f, 0.f);
+                for (int p = 0; p < NP; ++p) {
+                    eP[p] = tb_zero<PT>();
+                    tP[p] = tb_zero<PT>();
+                }
+                if (inter[j] && (read_e || read_t)) {
+                    const int64_t g = B.offset + (int64_t)r * B.L + c;
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        if (read_e) eP[p] = accE[g * NP + p];
+                        if (read_t) tP[p] = tail[g * NP + p];
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+#pragma unroll
+                    for (int cv = 0; cv < PER; ++cv) {
+                        const float2 e = tb_get(eP[p], cv), t2 = tb_get(tP[p], cv);
+                        // the tail alone for a tail launch; E + tail when the ribbon ends here
+                        acc[j][p * PER + cv] = (read_e && read_t)
+                                                   ? make_float2(e.x + t2.x, e.y + t2.y)
+                                                   : (read_t ? t2 : e);
+                    }
+                }
             }
             float bh, bl;
             tb_split(B.beta, bh, bl);
@@ -311,21 +338,6 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
                     const PT tkP = sQ[p * RMAX + idx];
-                    if (!first) {  // E (and the tail) this launch continues
-                        PT eP = tb_zero<PT>(), tP = tb_zero<PT>();
-                        if (to_main || done) eP = accE[g * NP + p];
-                        if (!to_main && tail_has) tP = tail[g * NP + p];
-#pragma unroll
-                        for (int cv = 0; cv < PER; ++cv) {
-                            float2 e = tb_get(eP, cv);
-                            if (!to_main && tail_has) {
-                                const float2 t2 = tb_get(tP, cv);
-                                e = done ? make_float2(e.x + t2.x, e.y + t2.y) : t2;
-                            }
-                            float2& av = acc[j][p * PER + cv];
-                            av = make_float2(e.x + av.x, e.y + av.y);
-                        }
-                    }
                     PT aP;
 #pragma unroll
                     for (int cv = 0; cv < PER; ++cv) tb_set(aP, cv, acc[j][p * PER + cv]);
@@ -351,13 +363,15 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
             }
         }
         if constexpr (FIRST) {
-            // per-tile partials of ||T_0||^2 and <T_0|H~ T_0>, fixed-order block reduction
+            // per-tile partials of ||T_0||^2 and <T_0|H~ T_0>, fixed-order reduction: FP32
+            // tree inside each warp (FP64 runs at ~1/64 of the FP32 rate here), FP64 across
+            // the warps
             const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
             for (int q = 0; q < 2 * NV; ++q) {
-                double xs = (double)part[q];
+                float xs = part[q];
                 for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
-                if (lane == 0) s_red[warp * 2 * NV + q] = xs;
+                if (lane == 0) s_red[warp * 2 * NV + q] = (double)xs;
             }
             __syncthreads();
             if (tid < 2 * NV) {

@@ -355,9 +355,16 @@ def test_graph_replay_equals_single_steps_and_tuning_keeps_results():
     Ms = [plan.block(q)["M"] for q in range(6)]
     if blk == 0:
         expect = max(Ms)
-    else:
+    else:  # orders 1..s0, then blocks of blk; a last block shorter than blk/2 joins the one before
         s0 = min(blk, min(Ms) - 1)
-        expect = 1 + -(-(max(Ms) - s0) // blk)
+        ranges = [(1, s0)]
+        while ranges[-1][1] < max(Ms):
+            ka = ranges[-1][1] + 1
+            ranges.append((ka, min(ka + blk - 1, max(Ms))))
+        if len(ranges) >= 3 and 2 * (ranges[-1][1] - ranges[-1][0] + 1) < blk:
+            ranges[-2] = (ranges[-2][0], ranges[-1][1])
+            ranges.pop()
+        expect = len(ranges)
     assert plan.launches() - n0 == 2 * expect
 
 
