@@ -29,10 +29,11 @@
 namespace cheb {
 
 // Shared memory of one CTA: two float2 planes per vector and the float on-site plane, for a
-// region of TPB * SPT sites.
+// region of TPB * SPT sites (plus one zero element per plane).
 __host__ __device__ constexpr size_t tb_smem(int nv, int spt, int tpb)
 {
-    return 2 * (size_t)nv * tpb * spt * sizeof(float2) + (size_t)tpb * spt * sizeof(float);
+    // each plane holds tpb * spt sites and one zero element (the neighbour outside a ribbon)
+    return 2 * (size_t)nv * ((size_t)tpb * spt + 1) * sizeof(float2) + (size_t)tpb * spt * sizeof(float);
 }
 
 // CTAs per SM the launch bounds ask for: 256-thread CTAs as tuned (3 up to 4 sites per
@@ -144,10 +145,11 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
     constexpr int NP = TBPlane<NV>::NP, PER = TBPlane<NV>::PER;
     constexpr int TB_THREADS = TPB;
     constexpr int RMAX = TB_THREADS * SPT;
+    constexpr int RP = RMAX + 1;  // plane stride; element RMAX of every plane stays zero
     extern __shared__ float4 tb_smem_raw[];
-    PT* const sP0 = reinterpret_cast<PT*>(tb_smem_raw);         // [NP][RMAX]
-    PT* const sQ0 = sP0 + NP * RMAX;                              // [NP][RMAX]
-    float* const sD = reinterpret_cast<float*>(sQ0 + NP * RMAX);  // [RMAX]
+    PT* const sP0 = reinterpret_cast<PT*>(tb_smem_raw);       // [NP][RP]
+    PT* const sQ0 = sP0 + NP * RP;                              // [NP][RP]
+    float* const sD = reinterpret_cast<float*>(sQ0 + NP * RP);  // [RMAX]
     __shared__ double s_red[(TB_THREADS / 32) * 2 * NV];
 
     // global vectors seen as NP plane elements per site
@@ -162,6 +164,7 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
     const float2* __restrict__ qc = static_cast<const float2*>(a.qcoef);
     const int tid = threadIdx.x;
     constexpr bool first = FIRST;  // ka == 1: T_0 = psi, no T_{-1}; norm and energy partials
+    if (tid < 2 * NP) sP0[(tid / NP) * NP * RP + (tid % NP) * RP + RMAX] = tb_zero<PT>();
 
     for (int w = blockIdx.x; w < a.ntiles; w += gridDim.x) {
         const TBTile T = a.tiles[w];
@@ -177,31 +180,46 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
             const bool done = (ke == B.M);
             const int RW = T.C1 - T.C0, RH = T.R1 - T.R0;
             const int nreg = RW * RH;
-            // region coordinates of this thread's positions tid + j * TPB (row-major region)
-            int srr[SPT], scc[SPT];
+            const bool open_t = T.R0 > 0, open_b = T.R1 < B.W, open_l = T.C0 > 0, open_r = T.C1 < B.L;
+            // per position tid + j * TPB of the row-major region: the shared-memory indices of
+            // its three neighbours (RMAX, the zero element, where the ribbon has none) and
+            // the last halo shrink at which it is still computed (its distance to the open
+            // sides of the region; -1 outside the region)
+            int nbl[SPT], nbr[SPT], nbv[SPT], dlim[SPT];
+            bool inter[SPT];
 #pragma unroll
             for (int j = 0; j < SPT; ++j) {
                 const int idx = tid + j * TB_THREADS;
-                srr[j] = idx / RW;
-                scc[j] = idx - srr[j] * RW;
-                if (idx >= nreg) srr[j] = 1 << 20;  // never inside a rectangle
+                const int rr = idx / RW, cc = idx - rr * RW;
+                const int r = T.R0 + rr, c = T.C0 + cc;
+                const bool up = (r + c) & 1;  // vertical neighbour r-1 (else r+1)
+                nbl[j] = c > 0 ? idx - 1 : RMAX;
+                nbr[j] = c + 1 < B.L ? idx + 1 : RMAX;
+                nbv[j] = up ? (r > 0 ? idx - RW : RMAX) : (r + 1 < B.W ? idx + RW : RMAX);
+                int dl = 1 << 20;
+                if (open_t) dl = min(dl, rr);
+                if (open_b) dl = min(dl, RH - 1 - rr);
+                if (open_l) dl = min(dl, cc);
+                if (open_r) dl = min(dl, RW - 1 - cc);
+                dlim[j] = idx < nreg ? dl : -1;
+                inter[j] = idx < nreg && (r >= T.r0) && (r < T.r1) && (c >= T.c0) && (c < T.c1);
             }
             // ---- load the region: asynchronous copies straight into shared memory ---------
 #pragma unroll
             for (int j = 0; j < SPT; ++j) {
                 const int idx = tid + j * TB_THREADS;
                 if (idx < nreg) {
-                    const int64_t g = B.offset + (int64_t)(T.R0 + srr[j]) * B.L + (T.C0 + scc[j]);
+                    const int rr = idx / RW, cc = idx - rr * RW;
+                    const int64_t g = B.offset + (int64_t)(T.R0 + rr) * B.L + (T.C0 + cc);
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
-                        cp_async_el(&sQ0[p * RMAX + idx], &in_cur[g * NP + p]);
-                        if (first) sP0[p * RMAX + idx] = tb_zero<PT>();
-                        else cp_async_el(&sP0[p * RMAX + idx], &in_prev[g * NP + p]);
+                        cp_async_el(&sQ0[p * RP + idx], &in_cur[g * NP + p]);
+                        if (first) sP0[p * RP + idx] = tb_zero<PT>();
+                        else cp_async_el(&sP0[p * RP + idx], &in_prev[g * NP + p]);
                     }
                     cp_async4(&sD[idx], &diag[g]);
                 }
             }
-            bool inter[SPT];
             float2 acc[SPT][NV];
             const bool to_main = first || (a.ka <= B.ksplit);
             const bool tail_has = a.prev_ka > B.ksplit;  // an earlier launch wrote the tail
@@ -211,8 +229,6 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
             const bool read_t = !first && !to_main && tail_has;
 #pragma unroll
             for (int j = 0; j < SPT; ++j) {
-                const int r = T.R0 + srr[j], c = T.C0 + scc[j];
-                inter[j] = (r >= T.r0) && (r < T.r1) && (c >= T.c0) && (c < T.c1);
                 PT eP[NP], tP[NP];
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
@@ -220,7 +236,9 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                     tP[p] = tb_zero<PT>();
                 }
                 if (inter[j] && (read_e || read_t)) {
-                    const int64_t g = B.offset + (int64_t)r * B.L + c;
+                    const int idx = tid + j * TB_THREADS;
+                    const int rr = idx / RW, cc = idx - rr * RW;
+                    const int64_t g = B.offset + (int64_t)(T.R0 + rr) * B.L + (T.C0 + cc);
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
                         if (read_e) eP[p] = accE[g * NP + p];
@@ -251,7 +269,7 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                     const int idx = tid + j * TB_THREADS;
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
-                        const PT x = sQ0[p * RMAX + idx];
+                        const PT x = sQ0[p * RP + idx];
 #pragma unroll
                         for (int c = 0; c < PER; ++c) tb_accum(acc[j][p * PER + c], q0, tb_get(x, c), 0);
                     }
@@ -260,34 +278,24 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
             // ---- s recurrence orders in shared memory -------------------------------------
             PT* sP = sP0;
             PT* sQ = sQ0;
-            const bool open_t = T.R0 > 0, open_b = T.R1 < B.W, open_l = T.C0 > 0, open_r = T.C1 < B.L;
             for (int k = a.ka; k <= ke; ++k) {
-                const int sh = k - a.ka + 1;
-                const int rlo = open_t ? sh : 0, rhi = RH - (open_b ? sh : 0);
-                const int clo = open_l ? sh : 0, chi = RW - (open_r ? sh : 0);
+                const int sh = k - a.ka + 1;  // order k is computed on the region shrunk by sh
                 const float2 qk = qc[B.coef_off + k];
                 PT* __restrict__ Pw = sP;        // T_{k-2} in, T_k out (own site only)
                 const PT* __restrict__ Qr = sQ;  // T_{k-1}, read at the site and neighbours
 #pragma unroll
                 for (int j = 0; j < SPT; ++j) {
-                    const int rr = srr[j], cc = scc[j];
-                    if (rr < rlo || rr >= rhi || cc < clo || cc >= chi) continue;
+                    if (dlim[j] < sh) continue;
                     const int idx = tid + j * TB_THREADS;
-                    const int r = T.R0 + rr, c = T.C0 + cc;
-                    const bool up = (r + c) & 1;  // vertical neighbour r-1 (else r+1)
-                    const bool hl = c > 0, hr = c + 1 < B.L;
-                    const bool hv = up ? (r > 0) : (r + 1 < B.W);
-                    const int il = idx - 1, ir = idx + 1;
-                    const int vidx = up ? idx - RW : idx + RW;
                     const float d = sD[idx];
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
-                        const PT* Q = Qr + p * RMAX;
+                        const PT* Q = Qr + p * RP;
                         const PT xP = Q[idx];
-                        const PT ylP = hl ? Q[il] : tb_zero<PT>();
-                        const PT yrP = hr ? Q[ir] : tb_zero<PT>();
-                        const PT yvP = hv ? Q[vidx] : tb_zero<PT>();
-                        const PT pP = Pw[p * RMAX + idx];
+                        const PT ylP = Q[nbl[j]];
+                        const PT yrP = Q[nbr[j]];
+                        const PT yvP = Q[nbv[j]];
+                        const PT pP = Pw[p * RP + idx];
                         PT hP;
 #pragma unroll
                         for (int cv = 0; cv < PER; ++cv) {
@@ -318,7 +326,7 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                                 }
                             }
                         }
-                        Pw[p * RMAX + idx] = hP;
+                        Pw[p * RP + idx] = hP;
                     }
                 }
                 __syncthreads();
@@ -326,7 +334,7 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                 sP = sQ;
                 sQ = tmp;
             }
-            // ---- write back: sQ = T_ke, sP = T_{ke-1}; the accumulators are read here --------
+            // ---- write back: sQ = T_ke, sP = T_{ke-1} ----------------------------------------
             float2 ph, pl;
             tb_split(B.ph_re, ph.x, pl.x);
             tb_split(B.ph_im, ph.y, pl.y);
@@ -334,16 +342,17 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
             for (int j = 0; j < SPT; ++j) {
                 if (!inter[j]) continue;
                 const int idx = tid + j * TB_THREADS;
-                const int64_t g = B.offset + (int64_t)(T.R0 + srr[j]) * B.L + (T.C0 + scc[j]);
+                const int rr = idx / RW, cc = idx - rr * RW;
+                const int64_t g = B.offset + (int64_t)(T.R0 + rr) * B.L + (T.C0 + cc);
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
-                    const PT tkP = sQ[p * RMAX + idx];
+                    const PT tkP = sQ[p * RP + idx];
                     PT aP;
 #pragma unroll
                     for (int cv = 0; cv < PER; ++cv) tb_set(aP, cv, acc[j][p * PER + cv]);
                     if (!done) {
                         out_cur[g * NP + p] = tkP;
-                        out_prev[g * NP + p] = sP[p * RMAX + idx];
+                        out_prev[g * NP + p] = sP[p * RP + idx];
                         if (to_main) accE[g * NP + p] = aP;
                         else tail[g * NP + p] = aP;
                     } else {
