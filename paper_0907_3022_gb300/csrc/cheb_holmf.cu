@@ -207,9 +207,10 @@ __global__ void __launch_bounds__(MINB > 1 ? 256 : 512, MINB) k_rec_holmf(RecArg
                             if (ag.last) {
                                 if (ag.read_psi_last) ac = V2<R>::make(ps[i].x + ac.x, ps[i].y + ac.y);
                                 ac = U::phase(ac, ph, pl);
-                                const double t2 = (double)h.x * h.x + (double)h.y * h.y;
+                                // growth check |T_M|^2 <= 4 ||psi||^2 in the vector precision
+                                const R t2 = fma(h.x, h.x, h.y * h.y);
                                 const int v = (int)(col[i] & (nv - 1));
-                                if (!(t2 <= 4.0 * a.norm2[(size_t)v * 2])) atomicOr(a.errflag, 1);
+                                if (!(t2 <= (R)(4.0 * a.norm2[(size_t)v * 2]))) atomicOr(a.errflag, 1);
                                 psi[base] = ac;
                             } else {
                                 accp[base] = ac;

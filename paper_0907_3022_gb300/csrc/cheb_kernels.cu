@@ -233,8 +233,9 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
 #pragma unroll
                             for (int v = 0; v < VPT; ++v) {
                                 acc[v] = U::phase(acc[v], ph, pl);
-                                const double t2 = (double)h[v].x * h[v].x + (double)h[v].y * h[v].y;
-                                const double lim = 4.0 * a.norm2[((size_t)it.block * nv + g * VPT + v) * 2];
+                                // growth check |T_M|^2 <= 4 ||psi||^2 in the vector precision
+                                const R t2 = fma(h[v].x, h[v].x, h[v].y * h[v].y);
+                                const R lim = (R)(4.0 * a.norm2[((size_t)it.block * nv + g * VPT + v) * 2]);
                                 if (!(t2 <= lim)) atomicOr(a.errflag, 1);
                             }
                             IO::store(psi + base, acc);

@@ -335,6 +335,10 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                 sQ = tmp;
             }
             // ---- write back: sQ = T_ke, sP = T_{ke-1} ----------------------------------------
+            float lim4[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                lim4[v] = done ? (float)(4.0 * a.norm2[((size_t)T.block * NV + v) * 2]) : 0.f;
             float2 ph, pl;
             tb_split(B.ph_re, ph.x, pl.x);
             tb_split(B.ph_im, ph.y, pl.y);
@@ -361,10 +365,10 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                         for (int cv = 0; cv < PER; ++cv) {
                             const int v = p * PER + cv;
                             tb_set(oP, cv, tb_phase(acc[j][v], ph, pl));  // E + tail + partial
+                            // growth check |T_M|^2 <= 4 ||psi||^2, in FP32 (a divergence test)
                             const float2 tk = tb_get(tkP, cv);
-                            const double t2 = (double)tk.x * tk.x + (double)tk.y * tk.y;
-                            const double lim = 4.0 * a.norm2[((size_t)T.block * NV + v) * 2];
-                            if (!(t2 <= lim)) atomicOr(a.errflag, 1);
+                            const float t2 = fmaf(tk.x, tk.x, tk.y * tk.y);
+                            if (!(t2 <= lim4[v])) atomicOr(a.errflag, 1);
                         }
                         psi[g * NP + p] = oP;
                     }
