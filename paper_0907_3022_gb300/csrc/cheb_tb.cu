@@ -180,6 +180,9 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
             const bool done = (ke == B.M);
             const int RW = T.C1 - T.C0, RH = T.R1 - T.R0;
             const int nreg = RW * RH;
+            // idx / RW as (idx * ceil(2^32 / RW)) >> 32: exact because idx * (RW - 1) stays far
+            // below 2^32 (idx < RMAX <= 8192)
+            const unsigned long long invRW = ((1ull << 32) + (unsigned)RW - 1u) / (unsigned)RW;
             const bool open_t = T.R0 > 0, open_b = T.R1 < B.W, open_l = T.C0 > 0, open_r = T.C1 < B.L;
             // per position tid + j * TPB of the row-major region: the shared-memory indices of
             // its three neighbours (RMAX, the zero element, where the ribbon has none) and
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
 #pragma unroll
             for (int j = 0; j < SPT; ++j) {
                 const int idx = tid + j * TB_THREADS;
-                const int rr = idx / RW, cc = idx - rr * RW;
+                const int rr = (int)(((unsigned long long)idx * invRW) >> 32), cc = idx - rr * RW;
                 const int r = T.R0 + rr, c = T.C0 + cc;
                 const bool up = (r + c) & 1;  // vertical neighbour r-1 (else r+1)
                 nbl[j] = c > 0 ? idx - 1 : RMAX;
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
             for (int j = 0; j < SPT; ++j) {
                 const int idx = tid + j * TB_THREADS;
                 if (idx < nreg) {
-                    const int rr = idx / RW, cc = idx - rr * RW;
+                    const int rr = (int)(((unsigned long long)idx * invRW) >> 32), cc = idx - rr * RW;
                     const int64_t g = B.offset + (int64_t)(T.R0 + rr) * B.L + (T.C0 + cc);
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                 }
                 if (inter[j] && (read_e || read_t)) {
                     const int idx = tid + j * TB_THREADS;
-                    const int rr = idx / RW, cc = idx - rr * RW;
+                    const int rr = (int)(((unsigned long long)idx * invRW) >> 32), cc = idx - rr * RW;
                     const int64_t g = B.offset + (int64_t)(T.R0 + rr) * B.L + (T.C0 + cc);
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
@@ -346,7 +349,7 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
             for (int j = 0; j < SPT; ++j) {
                 if (!inter[j]) continue;
                 const int idx = tid + j * TB_THREADS;
-                const int rr = idx / RW, cc = idx - rr * RW;
+                const int rr = (int)(((unsigned long long)idx * invRW) >> 32), cc = idx - rr * RW;
                 const int64_t g = B.offset + (int64_t)(T.R0 + rr) * B.L + (T.C0 + cc);
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
