@@ -79,7 +79,9 @@ __device__ void holmf_finalize(const RecArgs& a, const HolMFArgs& m, const DevBl
 // each thread advances NR phonon configurations in lockstep (NR = 2 doubles the loads in
 // flight per thread).  MINB > 1 caps the registers so that MINB blocks of 256 threads fit
 // on an SM (more warps to hide the gather latency; launches then use <= 256 threads).
-template <typename R, int MODE, int NR, int MINB>
+// LT > 0 compiles the walk over the electron sites for a chain of exactly LT sites (the
+// 12-site configuration and the paper's 18 sites): offsets and site tests become constants.
+template <typename R, int MODE, int NR, int MINB, int LT>
 __global__ void __launch_bounds__(MINB > 1 ? 256 : 512, MINB) k_rec_holmf(RecArgs a, HolMFArgs m)
 {
     using C = typename V2<R>::C;
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 256 : 512, MINB) k_rec_holmf(RecArg
     __syncthreads();
     const HolG G{sG, w};
     const int nv = a.nvec, lnv = m.log2_nvec;
-    const int L = m.L, nph = m.nph;
+    const int L = LT > 0 ? LT : m.L, nph = m.nph;  // LT > 0: chain length fixed at compile time
     const bool periodic = m.periodic != 0;
     // element offsets fit 32 bits (rows * nvec < 2^32 is checked at plan creation)
     const uint32_t units = (uint32_t)m.dph << lnv;
@@ -145,6 +147,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 256 : 512, MINB) k_rec_holmf(RecArg
                 xr[i] = periodic ? cur[col[i]] : zero;  // T_j at e + 1 (e = L-1: site 0)
                 xc[i] = xlast[i];                        // T_j at e
             }
+#pragma unroll (LT > 0 ? LT : 1)
             for (int e = L - 1; e >= 0; --e) {
                 C xl[NR], p[NR], acc[NR], ps[NR], xu[NR], xd[NR];
                 int ne[NR];
@@ -295,12 +298,22 @@ int holmf_build(Plan* p)
     return CHEB_OK;
 }
 
+template <typename R, int NR, int MINB, int LT>
+static void launch_lt(const RecArgs& a, const HolMFArgs& m, int grid, int th, cudaStream_t s)
+{
+    if (a.mode == REC_FIRST) k_rec_holmf<R, REC_FIRST, NR, MINB, LT><<<grid, th, 0, s>>>(a, m);
+    else if (a.mode == REC_SECOND) k_rec_holmf<R, REC_SECOND, NR, MINB, LT><<<grid, th, 0, s>>>(a, m);
+    else k_rec_holmf<R, REC_GENERAL, NR, MINB, LT><<<grid, th, 0, s>>>(a, m);
+}
+
 template <typename R, int NR, int MINB>
 static void launch_nr(const RecArgs& a, const HolMFArgs& m, int grid, int th, cudaStream_t s)
 {
-    if (a.mode == REC_FIRST) k_rec_holmf<R, REC_FIRST, NR, MINB><<<grid, th, 0, s>>>(a, m);
-    else if (a.mode == REC_SECOND) k_rec_holmf<R, REC_SECOND, NR, MINB><<<grid, th, 0, s>>>(a, m);
-    else k_rec_holmf<R, REC_GENERAL, NR, MINB><<<grid, th, 0, s>>>(a, m);
+    if constexpr (NR == 1) {
+        if (m.L == 12) return launch_lt<R, NR, MINB, 12>(a, m, grid, th, s);
+        if (m.L == 18) return launch_lt<R, NR, MINB, 18>(a, m, grid, th, s);
+    }
+    launch_lt<R, NR, MINB, 0>(a, m, grid, th, s);
 }
 
 // variants: 0 = one configuration per thread, 1 = the same with 5 blocks of 256 threads
