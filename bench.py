@@ -63,7 +63,7 @@ TB_DRAM_BYTES_PER_STEP = {(8, 6, 512): 6.99e9, (5, 3, 512): 10.07e9, (6, 3, 512)
 
 # DRAM bytes of one step of the paper's polaron run with the matrix-free operator, by
 # (precision, M), same capture method
-POLARON_MF_DRAM_BYTES_PER_STEP = {}
+POLARON_MF_DRAM_BYTES_PER_STEP = {("c64", 24): 497.5e9}
 
 
 def parse():
