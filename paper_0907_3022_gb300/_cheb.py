@@ -98,6 +98,8 @@ _SIGS = {
     "cheb_autotune": ([_vp], _c.c_int),
     "cheb_plan_launch": ([_vp, _ip, _ip, _ip, _ip], _c.c_int),
     "cheb_plan_set_blocking": ([_vp, _c.c_int, _c.c_int, _c.c_int], _c.c_int),
+    "cheb_plan_set_cluster": ([_vp, _c.c_int], _c.c_int),
+    "cheb_plan_cluster": ([_vp, _ip], _c.c_int),
     "cheb_plan_blocking": ([_vp, _ip, _ip, _ip], _c.c_int),
     "cheb_plan_export_csr": ([_vp, _i64p, _i64p, _dp, _i64p], _c.c_int),
     "cheb_plan_launches": ([_vp], _c.c_int64),
@@ -337,6 +339,14 @@ class Plan:
     def set_blocking(self, orders_per_launch: int, sites_per_thread: int = 4, threads: int = 256):
         check(lib().cheb_plan_set_blocking(self.handle, orders_per_launch, sites_per_thread,
                                            threads), "cheb_plan_set_blocking")
+
+    def set_cluster(self, on: bool):
+        check(lib().cheb_plan_set_cluster(self.handle, int(on)), "cheb_plan_set_cluster")
+
+    def cluster(self) -> bool:
+        v = ctypes.c_int()
+        check(lib().cheb_plan_cluster(self.handle, ctypes.byref(v)), "cheb_plan_cluster")
+        return bool(v.value)
 
     def blocking(self):
         """(orders per launch, sites per thread); (0, 0) when off."""

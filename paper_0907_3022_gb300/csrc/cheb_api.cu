@@ -353,8 +353,33 @@ static double tb_launch_bytes(const Plan* p, const Plan::TBLaunch& L)
 static int enqueue_step_tb(Plan* p, void* psi, cudaStream_t st);
 
 // Enqueue the M_max fused kernels of one step on stream s.
+// One step on the thread-block cluster (all M orders in one launch), timed like the others.
+static int enqueue_step_cluster(Plan* p, void* psi, cudaStream_t s)
+{
+    if (p->timing) {
+        if (p->ev_used + 2 > p->ev_pool.size()) {
+            for (int e = 0; e < 64; ++e) {
+                cudaEvent_t ev;
+                CHEB_CUDA(cudaEventCreate(&ev));
+                p->ev_pool.push_back(ev);
+            }
+        }
+        CHEB_CUDA(cudaEventRecord(p->ev_pool[p->ev_used], s));
+    }
+    int rc = cluster_launch(p, psi, s);
+    if (rc) return rc;
+    if (p->timing) {
+        CHEB_CUDA(cudaEventRecord(p->ev_pool[p->ev_used + 1], s));
+        p->ev_used += 2;
+        // DRAM operands of the whole step: psi in and out, the scaled diagonal
+        p->ev_bytes.push_back((double)p->n_sites * (2.0 * p->cplx_size() + p->real_size()));
+    }
+    return CHEB_OK;
+}
+
 static int enqueue_step(Plan* p, void* psi, cudaStream_t s)
 {
+    if (p->cluster && cluster_eligible(p)) return enqueue_step_cluster(p, psi, s);
     if (!p->tb_sched.empty()) return enqueue_step_tb(p, psi, s);
     RecArgs a = base_args(p);
     if (p->timing && p->ev_used > 4096) {  // keep the event pool bounded
@@ -1111,6 +1136,34 @@ extern "C" int cheb_autotune(cheb_plan* plan)
         if (!rc) rc = rc3;
         CHEB_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream));
     }
+    // whole steps: single-order launches against one cluster launch per step (small 1D grids)
+    if (!rc && cluster_eligible(p)) {
+        auto time_steps = [&](float* out_ms) -> int {
+            cudaEvent_t t0, t1;
+            cudaEventCreate(&t0);
+            cudaEventCreate(&t1);
+            int r = enqueue_step(p, scratch, p->stream);  // warm-up
+            cudaEventRecord(t0, p->stream);
+            for (int rep = 0; rep < 3 && !r; ++rep) r = enqueue_step(p, scratch, p->stream);
+            cudaEventRecord(t1, p->stream);
+            cudaEventSynchronize(t1);
+            cudaEventElapsedTime(out_ms, t0, t1);
+            cudaEventDestroy(t0);
+            cudaEventDestroy(t1);
+            return r;
+        };
+        float ms_off = 0.0f, ms_on = 0.0f;
+        p->cluster = 0;
+        rc = time_steps(&ms_off);
+        if (!rc) rc = cluster_configure(p);
+        if (!rc) {
+            p->cluster = 1;
+            rc = time_steps(&ms_on);
+        }
+        p->cluster = (!rc && ms_on < ms_off) ? 1 : 0;
+        p->shape_epoch++;
+        CHEB_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream));
+    }
     p->launches = launches0;
     cudaFree(scratch);
     if (rc) return rc;
@@ -1219,6 +1272,30 @@ extern "C" int cheb_plan_set_blocking(cheb_plan* plan, int s, int spt, int threa
     if (rc) return rc;
     if (s > 0 && p->have_dt && p->tb_sched.empty())
         return fail(CHEB_ERR_INVALID, "temporal blocking: a ribbon does not fit the tile budget");
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_set_cluster(cheb_plan* plan, int on)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    if (on && !cluster_eligible(p))
+        return fail(CHEB_ERR_UNSUPPORTED, "cluster steps need a 1D grid plan (CHEB_LAT1D, nvec 1, "
+                                          "shared potential) of at most 32768 points");
+    if (on) {
+        int rc = cluster_configure(p);
+        if (rc) return rc;
+    }
+    p->cluster = on ? 1 : 0;
+    p->shape_epoch++;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_cluster(const cheb_plan* plan, int* on)
+{
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    if (!p || !on) return fail(CHEB_ERR_INVALID, "cheb_plan_cluster: NULL argument");
+    *on = (p->cluster && cluster_eligible(p)) ? 1 : 0;
     return CHEB_OK;
 }
 

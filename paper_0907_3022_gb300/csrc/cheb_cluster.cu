@@ -1,0 +1,257 @@
+// One whole time step of a small 1D grid (Sec. 3.1; Eqs. U_1 and rec) in a single launch on a
+// thread-block cluster.
+//
+// The 3-point chain of n sites is split over the CL CTAs of one cluster (a contiguous chunk per
+// CTA).  T_{k-1} lives in shared memory (two buffers, read T_{k-1} / write T_k), T_{k-2} and the
+// accumulators of Eq. U_1 of a thread's own sites stay in registers, and a CTA reads the two
+// neighbouring values beyond its chunk straight from the neighbour CTA's shared memory
+// (distributed shared memory).  One cluster barrier separates consecutive orders, so the M
+// orders of a step cost M barriers instead of M kernel launches, and the DRAM sees psi once
+// in and once out.  Every thread runs the same number of barriers (no early exit).
+//
+// Spreading the chain over several SMs matters for complex128: one SM does about two FP64
+// fused multiply-adds per clock on this GPU.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "cheb_device.cuh"
+#include "cheb_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace cheb {
+
+static constexpr int CL_CTAS = 8;       // CTAs per cluster (portable cluster size)
+static constexpr int CL_MAX_SPT = 4;    // sites per thread
+static constexpr int CL_THREADS = 1024;
+
+struct ClusterArgs {
+    void* psi;                // [n] in: T_0; out: psi(t + dt)
+    const void* diag;         // R [n]: 2 (H_ii - b) / a
+    const void* qcoef;        // C (hi, lo) per order
+    const DevBlock* blocks;   // block 0: M, ksplit, beta, a, b, phase
+    int32_t n;
+    int32_t chunk;            // sites per CTA
+    double* red_out;          // [2]: ||psi||^2, <psi|H|psi>
+    int* errflag;
+};
+
+template <typename R, int SPT>
+__global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
+    k_step_cluster(ClusterArgs a)
+{
+    using C = typename V2<R>::C;
+    using U = SiteUpdate<R>;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ float4 cl_smem_raw[];
+    C* const buf0 = reinterpret_cast<C*>(cl_smem_raw);  // [chunk]
+    C* const buf1 = buf0 + a.chunk;                       // [chunk]
+    __shared__ double s_red[32 * 2];
+    __shared__ double s_tot[2];
+
+    const int rank = (int)cluster.block_rank();
+    const int lo = rank * a.chunk;
+    const int cnt = max(0, min(a.n, lo + a.chunk) - lo);
+    const bool has_left = rank > 0 && lo > 0;
+    const bool has_right = rank + 1 < CL_CTAS && lo + cnt < a.n;
+    // the neighbours' buffers, seen through distributed shared memory
+    C* const l0 = has_left ? cluster.map_shared_rank(buf0, rank - 1) : buf0;
+    C* const l1 = has_left ? cluster.map_shared_rank(buf1, rank - 1) : buf1;
+    C* const r0 = has_right ? cluster.map_shared_rank(buf0, rank + 1) : buf0;
+    C* const r1 = has_right ? cluster.map_shared_rank(buf1, rank + 1) : buf1;
+
+    const DevBlock B = a.blocks[0];
+    const C* __restrict__ qc = static_cast<const C*>(a.qcoef);
+    const R* __restrict__ diag = static_cast<const R*>(a.diag);
+    C* __restrict__ psi = static_cast<C*>(a.psi);
+    R bh, bl;
+    split_const<R>(B.beta, bh, bl);
+    C ph, pl;
+    split_const<R>(B.ph_re, ph.x, pl.x);
+    split_const<R>(B.ph_im, ph.y, pl.y);
+    const int tid = threadIdx.x;
+    const C zero = V2<R>::make(0, 0);
+
+    // own sites li = tid + j * blockDim.x: T_0 into shared memory, d and the accumulators
+    C p[SPT], acc[SPT], tl[SPT];
+    R d[SPT];
+    const C q0 = qc[B.coef_off + 0];
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        const int li = tid + j * (int)blockDim.x;
+        p[j] = zero;
+        acc[j] = zero;
+        tl[j] = zero;
+        d[j] = 0;
+        if (li < cnt) {
+            const C x = psi[lo + li];
+            buf0[li] = x;
+            d[j] = diag[lo + li];
+            U::accum(acc[j], q0, x, 0);
+        }
+    }
+    cluster.sync();
+
+    // orders k = 1 .. M: T_k from T_{k-1} (shared, buffer (k-1) & 1) and T_{k-2} (registers)
+    R part0 = 0, part1 = 0;
+    for (int k = 1; k <= B.M; ++k) {
+        const C* cur = (k & 1) ? buf0 : buf1;
+        C* nxt = (k & 1) ? buf1 : buf0;
+        const C* curl = (k & 1) ? l0 : l1;
+        const C* curr = (k & 1) ? r0 : r1;
+        const C qk = qc[B.coef_off + k];
+        const bool to_tail = k > B.ksplit;
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) {
+            const int li = tid + j * (int)blockDim.x;
+            if (li < cnt) {
+                const C x = cur[li];
+                const C yl = li > 0 ? cur[li - 1] : (has_left ? curl[a.chunk - 1] : zero);
+                const C yr = li + 1 < cnt ? cur[li + 1] : (has_right ? curr[0] : zero);
+                const R sx = yl.x + yr.x, sy = yl.y + yr.y;
+                R hx = fma(bl, sx, -p[j].x), hy = fma(bl, sy, -p[j].y);
+                hx = fma(bh, sx, hx);
+                hy = fma(bh, sy, hy);
+                hx = fma(d[j], x.x, hx);
+                hy = fma(d[j], x.y, hy);
+                if (k == 1) {  // T_1 = H~ T_0
+                    hx *= (R)0.5;
+                    hy *= (R)0.5;
+                    part0 = fma(x.x, x.x, fma(x.y, x.y, part0));
+                    part1 = fma(x.x, hx, fma(x.y, hy, part1));
+                }
+                const C h = V2<R>::make(hx, hy);
+                nxt[li] = h;
+                p[j] = x;
+                U::accum(to_tail ? tl[j] : acc[j], qk, h, k);
+                if (k == B.M) {  // growth check |T_M|^2 <= 4 ||psi||^2 (after the k = 1 sums)
+                    const R t2 = fma(h.x, h.x, h.y * h.y);
+                    if (!(t2 <= (R)(4.0 * s_tot[0]))) atomicOr(a.errflag, 1);
+                }
+            }
+        }
+        if (k == 1) {
+            // ||T_0||^2 and <T_0|H~ T_0>: warp tree, CTA sum, then every CTA adds the
+            // cluster's partials read from the other CTAs' shared memory
+            double v0 = (double)part0, v1 = (double)part1;
+            for (int off = 16; off > 0; off >>= 1) {
+                v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+                v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+            }
+            if ((tid & 31) == 0) {
+                s_red[(tid >> 5) * 2 + 0] = v0;
+                s_red[(tid >> 5) * 2 + 1] = v1;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double t0 = 0.0, t1 = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    t0 += s_red[w * 2 + 0];
+                    t1 += s_red[w * 2 + 1];
+                }
+                s_red[62] = t0;
+                s_red[63] = t1;
+            }
+            cluster.sync();
+            if (tid == 0) {
+                double t0 = 0.0, t1 = 0.0;
+                for (int r = 0; r < CL_CTAS; ++r) {
+                    const double* rs = cluster.map_shared_rank(s_red, r);
+                    t0 += rs[62];
+                    t1 += rs[63];
+                }
+                s_tot[0] = t0;
+                s_tot[1] = t1;
+                if (rank == 0) {
+                    a.red_out[0] = t0;
+                    a.red_out[1] = B.a * t1 + B.b * t0;  // <H> = a <H~> + b ||psi||^2
+                }
+            }
+        }
+        cluster.sync();  // T_k complete everywhere (and the k = 1 sums read) before order k + 1
+    }
+    // psi(t + dt) = e^{-i b dt} (accumulator + tail)
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        const int li = tid + j * (int)blockDim.x;
+        if (li < cnt) {
+            const C s = V2<R>::make(acc[j].x + tl[j].x, acc[j].y + tl[j].y);
+            psi[lo + li] = U::phase(s, ph, pl);
+        }
+    }
+}
+
+// 1D grids of at most CL_CTAS * CL_THREADS * CL_MAX_SPT sites, one vector
+bool cluster_eligible(const Plan* p)
+{
+    return p->desc.kind == CHEB_LAT1D && p->nvec == 1 && !p->desc.onsite_per_vec &&
+           p->n_sites <= (int64_t)CL_CTAS * CL_THREADS * CL_MAX_SPT;
+}
+
+// chunk of sites per CTA, threads per CTA (one per site up to 1024) and sites per thread
+static void cluster_shape(const Plan* p, int* chunk, int* threads, int* spt, size_t* smem)
+{
+    const int n = (int)p->n_sites;
+    *chunk = (n + CL_CTAS - 1) / CL_CTAS;
+    *threads = std::max(32, std::min(CL_THREADS, (*chunk + 31) / 32 * 32));
+    const int need = (*chunk + *threads - 1) / *threads;
+    *spt = need <= 1 ? 1 : (need <= 2 ? 2 : 4);
+    *smem = 2 * (size_t)(*chunk) * p->cplx_size();
+}
+
+template <typename R, int SPT>
+static int cluster_attr(size_t smem)
+{
+    CHEB_CUDA(cudaFuncSetAttribute(k_step_cluster<R, SPT>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return CHEB_OK;
+}
+
+template <typename R>
+static int cluster_attr_r(int spt, size_t smem)
+{
+    if (spt == 1) return cluster_attr<R, 1>(smem);
+    if (spt == 2) return cluster_attr<R, 2>(smem);
+    return cluster_attr<R, 4>(smem);
+}
+
+int cluster_configure(Plan* p)
+{
+    int chunk, threads, spt;
+    size_t smem;
+    cluster_shape(p, &chunk, &threads, &spt, &smem);
+    return p->prec == CHEB_C128 ? cluster_attr_r<double>(spt, smem) : cluster_attr_r<float>(spt, smem);
+}
+
+template <typename R>
+static void cluster_go(const ClusterArgs& a, int spt, int threads, size_t smem, cudaStream_t s)
+{
+    if (spt == 1) k_step_cluster<R, 1><<<CL_CTAS, threads, smem, s>>>(a);
+    else if (spt == 2) k_step_cluster<R, 2><<<CL_CTAS, threads, smem, s>>>(a);
+    else k_step_cluster<R, 4><<<CL_CTAS, threads, smem, s>>>(a);
+}
+
+int cluster_launch(Plan* p, void* psi, cudaStream_t s)
+{
+    int chunk, threads, spt;
+    size_t smem;
+    cluster_shape(p, &chunk, &threads, &spt, &smem);
+    ClusterArgs a{};
+    a.psi = psi;
+    a.diag = p->d_diag;
+    a.qcoef = p->d_qcoef;
+    a.blocks = p->d_blocks;
+    a.n = (int32_t)p->n_sites;
+    a.chunk = chunk;
+    a.red_out = p->d_red;
+    a.errflag = p->d_err;
+    if (p->prec == CHEB_C128) cluster_go<double>(a, spt, threads, smem, s);
+    else cluster_go<float>(a, spt, threads, smem, s);
+    p->launches++;
+    CHEB_CUDA(cudaGetLastError());
+    return CHEB_OK;
+}
+
+}  // namespace cheb
