@@ -291,13 +291,16 @@ int cheb_plan_set_blocking(cheb_plan* plan, int orders_per_launch, int sites_per
                            int threads);
 
 /* Whole steps on a thread-block cluster (1D grid plans, CHEB_LAT1D with nvec 1, a shared
-   potential and at most 32768 points): on != 0 runs all M orders of a step in one launch of
-   8 CTAs that keep the recurrence vectors in shared memory and exchange the chunk borders
-   through distributed shared memory, with one cluster barrier per order (the grid's
-   single-order launches are latency-bound: M = 6353 at N = 2048, dt = 0.5).
-   CHEB_ERR_UNSUPPORTED for other plans.  cheb_autotune also decides this. */
-int cheb_plan_set_cluster(cheb_plan* plan, int on);
-int cheb_plan_cluster(const cheb_plan* plan, int* on);
+   potential and at most 32768 points): ctas = 8 or 16 runs all M orders of a step in one
+   launch of a cluster of that many CTAs that keep the recurrence vectors in shared memory and
+   exchange the chunk borders through distributed shared memory, with one cluster barrier per
+   order (the grid's single-order launches are latency-bound: M = 6353 at N = 2048,
+   dt = 0.5); ctas = 0 returns to single-order launches.  CHEB_ERR_UNSUPPORTED for other plans
+   or a cluster the device cannot schedule (16 CTAs is a non-portable size),
+   CHEB_ERR_INVALID for other values.  cheb_plan_cluster reports the size in use (0: off).
+   cheb_autotune also decides this. */
+int cheb_plan_set_cluster(cheb_plan* plan, int ctas);
+int cheb_plan_cluster(const cheb_plan* plan, int* ctas);
 
 /* Launch shape chosen for the plan: threads per block, sites per thread, grid size, and
    vectors handled per thread (of the nvec at each site).  Matrix-free Holstein plans report

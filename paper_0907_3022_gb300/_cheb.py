@@ -340,13 +340,15 @@ class Plan:
         check(lib().cheb_plan_set_blocking(self.handle, orders_per_launch, sites_per_thread,
                                            threads), "cheb_plan_set_blocking")
 
-    def set_cluster(self, on: bool):
-        check(lib().cheb_plan_set_cluster(self.handle, int(on)), "cheb_plan_set_cluster")
+    def set_cluster(self, ctas: int = 8):
+        """Whole steps on a cluster of `ctas` CTAs (8 or 16; 0 or False: off)."""
+        check(lib().cheb_plan_set_cluster(self.handle, int(ctas)), "cheb_plan_set_cluster")
 
-    def cluster(self) -> bool:
+    def cluster(self) -> int:
+        """CTAs of the cluster running whole steps (0: off)."""
         v = ctypes.c_int()
         check(lib().cheb_plan_cluster(self.handle, ctypes.byref(v)), "cheb_plan_cluster")
-        return bool(v.value)
+        return v.value
 
     def blocking(self):
         """(orders per launch, sites per thread); (0, 0) when off."""

@@ -1152,15 +1152,23 @@ extern "C" int cheb_autotune(cheb_plan* plan)
             cudaEventDestroy(t1);
             return r;
         };
-        float ms_off = 0.0f, ms_on = 0.0f;
+        float best_ms = 0.0f;
+        int best = 0;
         p->cluster = 0;
-        rc = time_steps(&ms_off);
-        if (!rc) rc = cluster_configure(p);
-        if (!rc) {
-            p->cluster = 1;
-            rc = time_steps(&ms_on);
+        rc = time_steps(&best_ms);
+        for (int ctas : {8, 16}) {
+            if (rc) break;
+            if (cluster_configure(p, ctas) != CHEB_OK) continue;  // not schedulable here
+            p->cluster = ctas;
+            float ms = 0.0f;
+            rc = time_steps(&ms);
+            if (!rc && ms < best_ms) {
+                best_ms = ms;
+                best = ctas;
+            }
         }
-        p->cluster = (!rc && ms_on < ms_off) ? 1 : 0;
+        p->cluster = best;
+        if (!rc && best) rc = cluster_configure(p, best);  // attributes of the chosen size
         p->shape_epoch++;
         CHEB_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream));
     }
@@ -1275,27 +1283,29 @@ extern "C" int cheb_plan_set_blocking(cheb_plan* plan, int s, int spt, int threa
     return CHEB_OK;
 }
 
-extern "C" int cheb_plan_set_cluster(cheb_plan* plan, int on)
+extern "C" int cheb_plan_set_cluster(cheb_plan* plan, int ctas)
 {
     Plan* p = reinterpret_cast<Plan*>(plan);
     if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
-    if (on && !cluster_eligible(p))
+    if (ctas != 0 && ctas != 8 && ctas != 16)
+        return fail(CHEB_ERR_INVALID, "cheb_plan_set_cluster: ctas must be 0, 8 or 16");
+    if (ctas && !cluster_eligible(p))
         return fail(CHEB_ERR_UNSUPPORTED, "cluster steps need a 1D grid plan (CHEB_LAT1D, nvec 1, "
                                           "shared potential) of at most 32768 points");
-    if (on) {
-        int rc = cluster_configure(p);
+    if (ctas) {
+        int rc = cluster_configure(p, ctas);
         if (rc) return rc;
     }
-    p->cluster = on ? 1 : 0;
+    p->cluster = ctas;
     p->shape_epoch++;
     return CHEB_OK;
 }
 
-extern "C" int cheb_plan_cluster(const cheb_plan* plan, int* on)
+extern "C" int cheb_plan_cluster(const cheb_plan* plan, int* ctas)
 {
     const Plan* p = reinterpret_cast<const Plan*>(plan);
-    if (!p || !on) return fail(CHEB_ERR_INVALID, "cheb_plan_cluster: NULL argument");
-    *on = (p->cluster && cluster_eligible(p)) ? 1 : 0;
+    if (!p || !ctas) return fail(CHEB_ERR_INVALID, "cheb_plan_cluster: NULL argument");
+    *ctas = (p->cluster && cluster_eligible(p)) ? p->cluster : 0;
     return CHEB_OK;
 }
 

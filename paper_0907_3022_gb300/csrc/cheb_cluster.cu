@@ -23,9 +23,10 @@ namespace cg = cooperative_groups;
 
 namespace cheb {
 
-static constexpr int CL_CTAS = 8;       // CTAs per cluster (portable cluster size)
+static constexpr int CL_MAX_CTAS = 16;  // CTAs per cluster: 8 (portable) or 16
 static constexpr int CL_MAX_SPT = 4;    // sites per thread
 static constexpr int CL_THREADS = 1024;
+static constexpr int64_t CL_MAX_SITES = (int64_t)8 * CL_THREADS * CL_MAX_SPT;
 
 struct ClusterArgs {
     void* psi;                // [n] in: T_0; out: psi(t + dt)
@@ -39,8 +40,7 @@ struct ClusterArgs {
 };
 
 template <typename R, int SPT>
-__global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
-    k_step_cluster(ClusterArgs a)
+__global__ void __launch_bounds__(CL_THREADS) k_step_cluster(ClusterArgs a)
 {
     using C = typename V2<R>::C;
     using U = SiteUpdate<R>;
@@ -52,10 +52,11 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
     __shared__ double s_tot[2];
 
     const int rank = (int)cluster.block_rank();
+    const int nctas = (int)cluster.num_blocks();
     const int lo = rank * a.chunk;
     const int cnt = max(0, min(a.n, lo + a.chunk) - lo);
     const bool has_left = rank > 0 && lo > 0;
-    const bool has_right = rank + 1 < CL_CTAS && lo + cnt < a.n;
+    const bool has_right = rank + 1 < nctas && lo + cnt < a.n;
     // the neighbours' buffers, seen through distributed shared memory
     C* const l0 = has_left ? cluster.map_shared_rank(buf0, rank - 1) : buf0;
     C* const l1 = has_left ? cluster.map_shared_rank(buf1, rank - 1) : buf1;
@@ -111,7 +112,11 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
                 const C yl = li > 0 ? cur[li - 1] : (has_left ? curl[a.chunk - 1] : zero);
                 const C yr = li + 1 < cnt ? cur[li + 1] : (has_right ? curr[0] : zero);
                 const R sx = yl.x + yr.x, sy = yl.y + yr.y;
-                R hx = fma(bl, sx, -p[j].x), hy = fma(bl, sy, -p[j].y);
+                R hx = -p[j].x, hy = -p[j].y;
+                if constexpr (Split<R>::on) {  // complex64: beta as a float-float pair
+                    hx = fma(bl, sx, hx);
+                    hy = fma(bl, sy, hy);
+                }
                 hx = fma(bh, sx, hx);
                 hy = fma(bh, sy, hy);
                 hx = fma(d[j], x.x, hx);
@@ -157,7 +162,7 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
             cluster.sync();
             if (tid == 0) {
                 double t0 = 0.0, t1 = 0.0;
-                for (int r = 0; r < CL_CTAS; ++r) {
+                for (int r = 0; r < nctas; ++r) {
                     const double* rs = cluster.map_shared_rank(s_red, r);
                     t0 += rs[62];
                     t1 += rs[63];
@@ -183,18 +188,18 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
     }
 }
 
-// 1D grids of at most CL_CTAS * CL_THREADS * CL_MAX_SPT sites, one vector
+// 1D grids of at most 8 * 1024 * 4 sites, one vector
 bool cluster_eligible(const Plan* p)
 {
     return p->desc.kind == CHEB_LAT1D && p->nvec == 1 && !p->desc.onsite_per_vec &&
-           p->n_sites <= (int64_t)CL_CTAS * CL_THREADS * CL_MAX_SPT;
+           p->n_sites <= CL_MAX_SITES;
 }
 
 // chunk of sites per CTA, threads per CTA (one per site up to 1024) and sites per thread
-static void cluster_shape(const Plan* p, int* chunk, int* threads, int* spt, size_t* smem)
+static void cluster_shape(const Plan* p, int ctas, int* chunk, int* threads, int* spt, size_t* smem)
 {
     const int n = (int)p->n_sites;
-    *chunk = (n + CL_CTAS - 1) / CL_CTAS;
+    *chunk = (n + ctas - 1) / ctas;
     *threads = std::max(32, std::min(CL_THREADS, (*chunk + 31) / 32 * 32));
     const int need = (*chunk + *threads - 1) / *threads;
     *spt = need <= 1 ? 1 : (need <= 2 ? 2 : 4);
@@ -204,40 +209,96 @@ static void cluster_shape(const Plan* p, int* chunk, int* threads, int* spt, siz
 template <typename R, int SPT>
 static int cluster_attr(size_t smem)
 {
+    // never below the default 48 KB: a later launch with a larger chunk must not be refused
     CHEB_CUDA(cudaFuncSetAttribute(k_step_cluster<R, SPT>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)std::max<size_t>(smem, 48 * 1024)));
+    CHEB_CUDA(cudaFuncSetAttribute(k_step_cluster<R, SPT>,
+                                   cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    return CHEB_OK;
+}
+
+template <typename R, int SPT>
+static int cluster_fits(int ctas, int threads, size_t smem, int* fits)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    CHEB_CUDA(cudaOccupancyMaxActiveClusters(&n, k_step_cluster<R, SPT>, &cfg));
+    *fits = n > 0;
     return CHEB_OK;
 }
 
 template <typename R>
-static int cluster_attr_r(int spt, size_t smem)
+static int cluster_prepare_r(int ctas, int spt, int threads, size_t smem, int* fits)
 {
-    if (spt == 1) return cluster_attr<R, 1>(smem);
-    if (spt == 2) return cluster_attr<R, 2>(smem);
-    return cluster_attr<R, 4>(smem);
+    int rc = CHEB_OK;
+    if (spt == 1) rc = cluster_attr<R, 1>(smem);
+    else if (spt == 2) rc = cluster_attr<R, 2>(smem);
+    else rc = cluster_attr<R, 4>(smem);
+    if (rc) return rc;
+    if (spt == 1) return cluster_fits<R, 1>(ctas, threads, smem, fits);
+    if (spt == 2) return cluster_fits<R, 2>(ctas, threads, smem, fits);
+    return cluster_fits<R, 4>(ctas, threads, smem, fits);
 }
 
-int cluster_configure(Plan* p)
+// Set the kernel's attributes for a cluster of `ctas` CTAs; CHEB_ERR_UNSUPPORTED if the
+// device cannot schedule such a cluster.
+int cluster_configure(Plan* p, int ctas)
 {
-    int chunk, threads, spt;
+    if (ctas != 8 && ctas != 16) return fail(CHEB_ERR_INVALID, "cluster size must be 8 or 16");
+    int chunk, threads, spt, fits = 0;
     size_t smem;
-    cluster_shape(p, &chunk, &threads, &spt, &smem);
-    return p->prec == CHEB_C128 ? cluster_attr_r<double>(spt, smem) : cluster_attr_r<float>(spt, smem);
+    cluster_shape(p, ctas, &chunk, &threads, &spt, &smem);
+    const int rc = p->prec == CHEB_C128 ? cluster_prepare_r<double>(ctas, spt, threads, smem, &fits)
+                                        : cluster_prepare_r<float>(ctas, spt, threads, smem, &fits);
+    if (rc) return rc;
+    return fits ? CHEB_OK : fail(CHEB_ERR_UNSUPPORTED, "the device cannot schedule this cluster");
+}
+
+template <typename R, int SPT>
+static cudaError_t cluster_go_t(const ClusterArgs& a, int ctas, int threads, size_t smem,
+                                cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step_cluster<R, SPT>, a);
 }
 
 template <typename R>
-static void cluster_go(const ClusterArgs& a, int spt, int threads, size_t smem, cudaStream_t s)
+static cudaError_t cluster_go(const ClusterArgs& a, int ctas, int spt, int threads, size_t smem,
+                              cudaStream_t s)
 {
-    if (spt == 1) k_step_cluster<R, 1><<<CL_CTAS, threads, smem, s>>>(a);
-    else if (spt == 2) k_step_cluster<R, 2><<<CL_CTAS, threads, smem, s>>>(a);
-    else k_step_cluster<R, 4><<<CL_CTAS, threads, smem, s>>>(a);
+    if (spt == 1) return cluster_go_t<R, 1>(a, ctas, threads, smem, s);
+    if (spt == 2) return cluster_go_t<R, 2>(a, ctas, threads, smem, s);
+    return cluster_go_t<R, 4>(a, ctas, threads, smem, s);
 }
 
 int cluster_launch(Plan* p, void* psi, cudaStream_t s)
 {
+    const int ctas = p->cluster;
     int chunk, threads, spt;
     size_t smem;
-    cluster_shape(p, &chunk, &threads, &spt, &smem);
+    cluster_shape(p, ctas, &chunk, &threads, &spt, &smem);
     ClusterArgs a{};
     a.psi = psi;
     a.diag = p->d_diag;
@@ -247,10 +308,13 @@ int cluster_launch(Plan* p, void* psi, cudaStream_t s)
     a.chunk = chunk;
     a.red_out = p->d_red;
     a.errflag = p->d_err;
-    if (p->prec == CHEB_C128) cluster_go<double>(a, spt, threads, smem, s);
-    else cluster_go<float>(a, spt, threads, smem, s);
+    const cudaError_t e = p->prec == CHEB_C128 ? cluster_go<double>(a, ctas, spt, threads, smem, s)
+                                               : cluster_go<float>(a, ctas, spt, threads, smem, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // a refused launch leaves no error behind for later calls
+        return cuda_fail(e, "cluster step launch");
+    }
     p->launches++;
-    CHEB_CUDA(cudaGetLastError());
     return CHEB_OK;
 }
 

@@ -168,7 +168,7 @@ int launch_scale_diag(Plan* p, const double* onsite, cudaStream_t s);
 
 // one step of a small 1D grid on a thread-block cluster (cheb_cluster.cu)
 bool cluster_eligible(const Plan* p);
-int cluster_configure(Plan* p);
+int cluster_configure(Plan* p, int ctas);
 int cluster_launch(Plan* p, void* psi, cudaStream_t s);
 
 // Holstein (cheb_holstein.cu: stored SELL matrix; cheb_holmf.cu: matrix-free operator)
@@ -276,7 +276,7 @@ struct Plan {
 
     // temporal blocking (complex64 stencils): orders per launch (0: off), sites per thread
     int tb_s = 0;
-    int cluster = 0;          // 1: whole steps on a thread-block cluster (small 1D grids)
+    int cluster = 0;          // CTAs of the cluster running whole steps (small 1D grids); 0: off
     int tb_spt = 4;
     int tb_tpb = 256;         // threads per CTA of the blocked kernel
     int tb_grid_cap = 0;

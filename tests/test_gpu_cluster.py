@@ -18,9 +18,10 @@ def _grid(n):
     return d
 
 
+@pytest.mark.parametrize("ctas", [8, 16])
 @pytest.mark.parametrize("prec", [C128, C64])
 @pytest.mark.parametrize("n", [2, 5, 33, 257, 2048, 4100, 32768])
-def test_cluster_steps_equal_single_order_launches(prec, n):
+def test_cluster_steps_equal_single_order_launches(prec, n, ctas):
     import paper_0907_3022_gb300 as cb
 
     d = _grid(n)
@@ -32,8 +33,12 @@ def test_cluster_steps_equal_single_order_launches(prec, n):
     a = dev_vec(d.packet(), prec)
     ref_plan.evolve(a, dt, nsteps)
     plan = cb.Plan(cb.desc_lat1d(d.n, d.dx, V), [lo], [hi], 0.01, prec, 1, keep=(V,))
-    plan.set_cluster(True)
-    assert plan.cluster()
+    try:
+        plan.set_cluster(ctas)
+    except cb.ChebError as e:  # a 16-CTA cluster is a non-portable size
+        assert ctas == 16 and e.status == cb.CHEB_ERR_UNSUPPORTED
+        pytest.skip("16-CTA clusters cannot be scheduled on this device")
+    assert plan.cluster() == ctas
     b = dev_vec(d.packet(), prec)
     n0 = plan.launches()
     plan.evolve(b, dt, nsteps)
@@ -60,7 +65,7 @@ def test_cluster_paper_double_well_and_step_observables():
     lo, hi = d.bounds()
     V = dev_f64(d.potential())
     plan = cb.Plan(cb.desc_lat1d(d.n, d.dx, V), [lo], [hi], 0.01, C128, 1, keep=(V,))
-    plan.set_cluster(True)
+    plan.set_cluster(8)
     psi = dev_vec(d.packet(), C128)
     obs = torch.zeros((d.nsteps, 1, 1, 2), dtype=torch.float64, device="cuda:0")
     plan.evolve(psi, d.dt, d.nsteps, obs_every=1, obs=obs)
@@ -83,26 +88,55 @@ def test_cluster_unsupported_and_growth_check():
     lo, hi = d.bounds()
     p2 = cb.Plan(cb.desc_lat1d(d.n, d.dx, V), [lo], [hi], 0.01, C128, 2, keep=(V,))
     with pytest.raises(cb.ChebError) as e:
-        p2.set_cluster(True)
+        p2.set_cluster(8)
     assert e.value.status == cb.CHEB_ERR_UNSUPPORTED
     big = _grid(32770)
     Vb = dev_f64(big.potential())
     pb = cb.Plan(cb.desc_lat1d(big.n, big.dx, Vb), [0.0], [1e5], 0.01, C128, 1, keep=(Vb,))
     with pytest.raises(cb.ChebError) as e:
-        pb.set_cluster(True)
+        pb.set_cluster(8)
     assert e.value.status == cb.CHEB_ERR_UNSUPPORTED
     rb = wl.Ribbon(W=4, L=20)
     eps = dev_f64(rb.onsite())
     desc, keep = cb.desc_ribbons([rb.W], [rb.L], 1.0, eps)
     pr = cb.Plan(desc, [rb.bounds()[0]], [rb.bounds()[1]], 0.0, C128, 1, keep=keep)
     with pytest.raises(cb.ChebError) as e:
-        pr.set_cluster(True)
+        pr.set_cluster(8)
     assert e.value.status == cb.CHEB_ERR_UNSUPPORTED
+    with pytest.raises(cb.ChebError) as e:
+        cb.Plan(cb.desc_lat1d(d.n, d.dx, V), [lo], [hi], 0.01, C128, 1, keep=(V,)).set_cluster(4)
+    assert e.value.status == cb.CHEB_ERR_INVALID
     # bounds far too tight: the recurrence grows and the step reports it
     tight = cb.Plan(cb.desc_lat1d(d.n, d.dx, V), [lo], [lo + 0.1 * (hi - lo)], 0.0, C128, 1,
                     keep=(V,))
-    tight.set_cluster(True)
+    tight.set_cluster(8)
     psi = dev_vec(d.packet(), C128)
     with pytest.raises(cb.ChebError) as e:
         tight.evolve(psi, 0.5, 2)
     assert e.value.status == cb.CHEB_ERR_DIVERGED
+
+
+@pytest.mark.parametrize("prec", [C128, C64])
+def test_cluster_after_autotune_and_switching_sizes(prec):
+    """The tuner tries every cluster size; whatever it keeps, and any size set afterwards,
+    must launch (the kernel attributes follow the size in use)."""
+    import paper_0907_3022_gb300 as cb
+
+    d = wl.PaperDoubleWell()
+    lo, hi = d.bounds()
+    V = dev_f64(d.potential())
+    plan = cb.Plan(cb.desc_lat1d(d.n, d.dx, V), [lo], [hi], 0.01, prec, 1, keep=(V,))
+    psi = dev_vec(d.packet(), prec)
+    plan.evolve(psi, d.dt, 0)
+    plan.autotune()
+    plan.step(psi, d.dt)
+    plan.evolve(psi, d.dt, 2)
+    for c in (16, 8, 0, 8):
+        try:
+            plan.set_cluster(c)
+        except cb.ChebError as e:
+            assert c == 16 and e.status == cb.CHEB_ERR_UNSUPPORTED
+            continue
+        plan.evolve(psi, d.dt, 1)
+        plan.step(psi, d.dt)
+    plan.sync()
