@@ -639,6 +639,10 @@ def run_single(args, world, rank, local):
         rtype = "double" if prec == cb.CHEB_C128 else "float"
         if cfg["matrix_free"] and cfg["kind"] == "holstein":
             kname = "k_rec_holmf<%s>" % rtype
+        elif cfg["kind"] == "doublewell" and plan.cluster():
+            kname = "k_step_cluster<%s> (%d-CTA cluster, one launch per step)" % (rtype, plan.cluster())
+        elif cfg["kind"] == "ribbon" and plan.blocking()[0]:
+            kname = "k_rec_tb<1,%d,%d> (temporal blocking)" % tuple(plan.blocking_shape()[1:])
         else:
             kname = "k_rec<%s,1,%s>" % (rtype, "SellOp" if cfg["kind"] == "holstein" else "StencilOp")
         roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s",
