@@ -1074,24 +1074,29 @@ extern "C" int cheb_autotune(cheb_plan* plan)
         cudaFree(scratch);
         return rc2;
     }
-    // whole steps: single-order launches against temporal blocking (complex64 stencils)
+    // whole steps as cheb_evolve runs them: the step's graph replayed (one warm-up, 3 timed)
+    auto time_steps = [&](float* out_ms) -> int {
+        Plan::StepGraph* g = nullptr;
+        int r = ensure_graph(p, scratch, &g);
+        if (r) return r;
+        cudaEvent_t t0, t1;
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        cudaGraphLaunch(g->exec, p->stream);
+        cudaEventRecord(t0, p->stream);
+        for (int rep = 0; rep < 3; ++rep) cudaGraphLaunch(g->exec, p->stream);
+        cudaEventRecord(t1, p->stream);
+        cudaError_t e = cudaEventSynchronize(t1);
+        cudaEventElapsedTime(out_ms, t0, t1);
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        return e == cudaSuccess ? CHEB_OK : cuda_fail(e, "autotune step timing");
+    };
+    // single-order launches against temporal blocking (complex64 stencils)
     if (tb_eligible(p)) {
-        auto time_steps = [&](float* out_ms) -> int {
-            cudaEvent_t t0, t1;
-            cudaEventCreate(&t0);
-            cudaEventCreate(&t1);
-            int r = enqueue_step(p, scratch, p->stream);  // warm-up
-            cudaEventRecord(t0, p->stream);
-            for (int rep = 0; rep < 2 && !r; ++rep) r = enqueue_step(p, scratch, p->stream);
-            cudaEventRecord(t1, p->stream);
-            cudaEventSynchronize(t1);
-            cudaEventElapsedTime(out_ms, t0, t1);
-            cudaEventDestroy(t0);
-            cudaEventDestroy(t1);
-            return r;
-        };
         p->tb_s = 0;
         p->tb_sched.clear();
+        p->shape_epoch++;
         float best_ms = 0.0f;
         rc = time_steps(&best_ms);
         int best_s = 0, best_spt = p->tb_spt, best_tpb = p->tb_tpb;
@@ -1138,28 +1143,16 @@ extern "C" int cheb_autotune(cheb_plan* plan)
     }
     // whole steps: single-order launches against one cluster launch per step (small 1D grids)
     if (!rc && cluster_eligible(p)) {
-        auto time_steps = [&](float* out_ms) -> int {
-            cudaEvent_t t0, t1;
-            cudaEventCreate(&t0);
-            cudaEventCreate(&t1);
-            int r = enqueue_step(p, scratch, p->stream);  // warm-up
-            cudaEventRecord(t0, p->stream);
-            for (int rep = 0; rep < 3 && !r; ++rep) r = enqueue_step(p, scratch, p->stream);
-            cudaEventRecord(t1, p->stream);
-            cudaEventSynchronize(t1);
-            cudaEventElapsedTime(out_ms, t0, t1);
-            cudaEventDestroy(t0);
-            cudaEventDestroy(t1);
-            return r;
-        };
         float best_ms = 0.0f;
         int best = 0;
         p->cluster = 0;
+        p->shape_epoch++;
         rc = time_steps(&best_ms);
         for (int ctas : {8, 16}) {
             if (rc) break;
             if (cluster_configure(p, ctas) != CHEB_OK) continue;  // not schedulable here
             p->cluster = ctas;
+            p->shape_epoch++;
             float ms = 0.0f;
             rc = time_steps(&ms);
             if (!rc && ms < best_ms) {
@@ -1173,6 +1166,13 @@ extern "C" int cheb_autotune(cheb_plan* plan)
         CHEB_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream));
     }
     p->launches = launches0;
+    cudaStreamSynchronize(p->stream);
+    for (Plan::StepGraph& g : p->graphs)  // graphs of the scratch buffer are not reused
+        if (g.exec && g.psi == scratch) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            g.psi = nullptr;
+        }
     cudaFree(scratch);
     if (rc) return rc;
     p->tuned = true;
