@@ -281,8 +281,9 @@ int cheb_holstein_phonon_neighbors(int L, int nph, int64_t p0, int64_t count, in
 int cheb_autotune(cheb_plan* plan);
 /* Temporal blocking (complex64 lattice plans with nvec 1, 2 or 4 and a shared on-site
    array): orders_per_launch s > 0 makes each launch run s recurrence orders out of shared
-   memory on 2-D tiles of each ribbon with an s-site halo; a CTA of `threads` threads holds a
-   region of threads x sites_per_thread sites.  Compiled shapes (nvec: sites_per_thread x
+   memory on 2-D tiles of each ribbon with a halo of s columns and ceil(s / 2) rows (a site d
+   rows away is at least 2d - 1 bonds away on the brick wall); a CTA of `threads` threads
+   holds a region of threads x sites_per_thread sites.  Compiled shapes (nvec: sites_per_thread x
    threads): 256 threads with 4, 6 or 8 (8 only for nvec <= 2); nvec 4 also 3, 4, 6 x 512 and
    2, 3 x 1024; nvec 2 also 6 x 1024; nvec 1 also 8 x 1024.  threads = 0 means 256.  s = 0
    returns to one order per launch.  CHEB_ERR_UNSUPPORTED for other plans, CHEB_ERR_INVALID

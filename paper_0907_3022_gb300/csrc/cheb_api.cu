@@ -1106,7 +1106,7 @@ extern "C" int cheb_autotune(cheb_plan* plan)
             if (rc) break;
             const int spt = sh[0], tpb = sh[1];
             if (!tb_supported(p->nvec, spt, tpb)) continue;
-            for (int s_try : {2, 3, 4, 5, 6, 8}) {
+            for (int s_try : {2, 3, 4, 5, 6, 7, 8, 10, 12}) {
                 p->tb_s = s_try;
                 p->tb_spt = spt;
                 p->tb_tpb = tpb;

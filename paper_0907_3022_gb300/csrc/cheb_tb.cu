@@ -2,11 +2,13 @@
 // Eqs. U_1 and rec; ribbons of Sec. 3.2, the 1D grid as W = 1).
 //
 // One launch forms s consecutive orders k = ka .. kb for every ribbon.  A CTA owns a tile
-// of one ribbon: the interior [r0, r1) x [c0, c1) plus a halo of s sites on every side that
-// is not a ribbon edge (the region [R0, R1) x [C0, C1)).  It loads T_{ka-2}, T_{ka-1} and
-// the on-site data d of the region into shared memory once, then runs the s recurrence
-// orders there: order i is computed on the region shrunk by i+1 on its open sides, which is
-// exactly where its inputs are still valid, and the interior is the region shrunk by s.  The
+// of one ribbon: the interior [r0, r1) x [c0, c1) plus a halo on every side that is not a
+// ribbon edge (the region [R0, R1) x [C0, C1)): s columns left and right, ceil(s / 2) rows
+// above and below, since on the brick wall a site d rows away is at least 2d - 1 bonds away.
+// It loads T_{ka-2}, T_{ka-1} and the on-site data d of the region into shared memory once,
+// then runs the s recurrence orders there: the i-th order is computed at the sites whose
+// bond distance to the open sides exceeds i, which is exactly where its inputs are still
+// valid, and the interior keeps all s.  The
 // weighted sum of the s new orders for the interior sites stays in registers.  At the end
 // the interior's last two vectors go to the other global buffer pair (the neighbouring CTAs
 // are still reading this pair as their halo) and the partial sum goes to an accumulator:
@@ -199,9 +201,13 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                 nbl[j] = c > 0 ? idx - 1 : RMAX;
                 nbr[j] = c + 1 < B.L ? idx + 1 : RMAX;
                 nbv[j] = up ? (r > 0 ? idx - RW : RMAX) : (r + 1 < B.W ? idx + RW : RMAX);
+                // bond distance to the open sides, less one: a site d rows from an open row
+                // side is 2d - 1 bonds from it when its vertical bond points that way, else 2d
+                // (the vertical bonds alternate), so rows stay valid about twice as long as
+                // columns; sites never computed (dl = 0) never read their neighbours
                 int dl = 1 << 20;
-                if (open_t) dl = min(dl, rr);
-                if (open_b) dl = min(dl, RH - 1 - rr);
+                if (open_t) dl = min(dl, 2 * rr + (up ? 0 : 1));
+                if (open_b) dl = min(dl, 2 * (RH - 1 - rr) + (up ? 1 : 0));
                 if (open_l) dl = min(dl, cc);
                 if (open_r) dl = min(dl, RW - 1 - cc);
                 dlim[j] = idx < nreg ? dl : -1;
@@ -491,6 +497,9 @@ int tb_launch(Plan* p, const TBArgs& a, cudaStream_t s)
 bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vector<int32_t>& begin)
 {
     const int rmax = p->tb_tpb * p->tb_spt;
+    // halo widths for s orders: s columns, but only ceil(s / 2) rows, since d rows away is at
+    // least 2d - 1 bonds on the brick wall (the kernel's validity distance counts the same way)
+    const int hr = (s + 1) / 2;
     tiles.clear();
     begin.assign(p->nblocks + 1, 0);
     for (int q = 0; q < p->nblocks; ++q) {
@@ -501,7 +510,7 @@ bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vecto
         double best_eff = 0.0;
         for (int nbr = 1; nbr <= B.W; ++nbr) {
             const int tr = (B.W + nbr - 1) / nbr;
-            const int rh = std::min(B.W, tr + (nbr > 1 ? 2 * s : 0));  // worst band
+            const int rh = std::min(B.W, tr + (nbr > 1 ? 2 * hr : 0));  // worst band
             const int tcmax = rmax / rh - (B.L > rmax / rh ? 2 * s : 0);
             if (tcmax < 1) continue;
             const int tc = std::min(tcmax, B.L);
@@ -510,13 +519,13 @@ bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vecto
                 best_eff = eff;
                 best_nbr = nbr;
             }
-            if (tr <= 2 * s) break;
+            if (tr <= 2 * hr) break;
         }
         if (best_nbr < 0) return false;
         const int tr = (B.W + best_nbr - 1) / best_nbr;
         for (int r0 = 0; r0 < B.W; r0 += tr) {
             const int r1 = std::min(B.W, r0 + tr);
-            const int R0 = std::max(0, r0 - s), R1 = std::min(B.W, r1 + s);
+            const int R0 = std::max(0, r0 - hr), R1 = std::min(B.W, r1 + hr);
             const int rh = R1 - R0;
             int tc = rmax / rh;
             if (tc < B.L) tc -= 2 * s;  // halo on both column sides
