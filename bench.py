@@ -59,7 +59,7 @@ ALG_BYTES_PER_UNIT = {
 # DRAM bytes of one step of the default ensemble (dram__bytes_read.sum +
 # dram__bytes_write.sum over all launches of a step, one ncu pass), by blocking (orders per
 # launch, sites per thread, threads per CTA); the launches per step follow from the schedule.
-TB_DRAM_BYTES_PER_STEP = {(8, 6, 512): 6.99e9}
+TB_DRAM_BYTES_PER_STEP = {(8, 6, 512): 6.99e9, (10, 6, 512): 4.01e9}
 
 # DRAM bytes of one step of the paper's polaron run with the matrix-free operator, by
 # (precision, M), same capture method
