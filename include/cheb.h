@@ -177,7 +177,8 @@ int cheb_evolve(cheb_plan* plan, void* psi, double dt, int nsteps, int obs_every
    propagated nsteps steps of dt and copied back to (char*)out + j * out_stride.  Strides are
    in bytes, 0 (every job reads / writes the same state) or >= vec_bytes.  The host-to-device
    copy of job j + 1 and the device-to-host copy of job j - 1 overlap the propagation of job j
-   (two device buffers of the plan; one stream per copy direction); the copies overlap only
+   and each other (three device buffers of the plan; one stream per copy direction); the
+   copies overlap only
    with pinned host memory (cudaHostAlloc / cudaHostRegister).  in and out may be the same
    buffer only with equal nonzero strides (CHEB_ERR_INVALID otherwise); other overlaps are the
    caller's error.  Host buffers are owned by the caller and must hold every addressed state.

@@ -525,7 +525,7 @@ static void free_plan(Plan* p)
     for (Plan::StepGraph& g : p->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < Plan::kJobBuffers; ++b) {
         if (p->d_job[b]) cudaFree(p->d_job[b]);
         for (cudaEvent_t e : {p->ev_in[b], p->ev_done[b], p->ev_out[b]})
             if (e) cudaEventDestroy(e);
@@ -852,7 +852,8 @@ extern "C" int cheb_evolve_host(cheb_plan* plan, const void* in, int64_t in_stri
     int rc = set_dt(p, dt);
     if (rc) return rc;
     if (njobs == 0) return CHEB_OK;
-    for (int b = 0; b < 2; ++b) {
+    constexpr int NB = Plan::kJobBuffers;
+    for (int b = 0; b < NB; ++b) {
         if (!p->d_job[b] && cudaMalloc(&p->d_job[b], jb) != cudaSuccess)
             return fail(CHEB_ERR_NOMEM, "cheb_evolve_host: job buffers");
         for (cudaEvent_t* e : {&p->ev_in[b], &p->ev_done[b], &p->ev_out[b]})
@@ -860,9 +861,9 @@ extern "C" int cheb_evolve_host(cheb_plan* plan, const void* in, int64_t in_stri
     }
     if (!p->h2d_stream) CHEB_CUDA(cudaStreamCreateWithFlags(&p->h2d_stream, cudaStreamNonBlocking));
     if (!p->d2h_stream) CHEB_CUDA(cudaStreamCreateWithFlags(&p->d2h_stream, cudaStreamNonBlocking));
-    Plan::StepGraph* graph[2] = {nullptr, nullptr};
+    Plan::StepGraph* graph[NB] = {};
     if (!p->timing && nsteps > 0) {
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NB; ++b) {
             rc = ensure_graph(p, p->d_job[b], &graph[b]);
             if (rc) return rc;
         }
@@ -870,8 +871,8 @@ extern "C" int cheb_evolve_host(cheb_plan* plan, const void* in, int64_t in_stri
     const char* src = static_cast<const char*>(in);
     char* dst = static_cast<char*>(out);
     auto copy_in = [&](int64_t j) -> int {
-        const int b = (int)(j & 1);
-        if (j >= 2) CHEB_CUDA(cudaStreamWaitEvent(p->h2d_stream, p->ev_out[b], 0));  // buffer free
+        const int b = (int)(j % NB);
+        if (j >= NB) CHEB_CUDA(cudaStreamWaitEvent(p->h2d_stream, p->ev_out[b], 0));  // buffer free
         CHEB_CUDA(cudaMemcpyAsync(p->d_job[b], src + (size_t)j * (size_t)in_stride, jb,
                                   cudaMemcpyHostToDevice, p->h2d_stream));
         CHEB_CUDA(cudaEventRecord(p->ev_in[b], p->h2d_stream));
@@ -880,7 +881,7 @@ extern "C" int cheb_evolve_host(cheb_plan* plan, const void* in, int64_t in_stri
     rc = copy_in(0);
     if (rc) return rc;
     for (int64_t j = 0; j < njobs; ++j) {
-        const int b = (int)(j & 1);
+        const int b = (int)(j % NB);
         if (j + 1 < njobs) {
             rc = copy_in(j + 1);
             if (rc) return rc;

@@ -265,12 +265,14 @@ struct Plan {
     cudaStream_t cap_stream = nullptr;
     int64_t shape_epoch = 0;  // bumped whenever items / launch shape / coefficients change
 
-    // batches of jobs from host memory (cheb_evolve_host): two device buffers, a stream per
-    // copy direction and their events (created on first use)
-    void* d_job[2] = {nullptr, nullptr};
+    // batches of jobs from host memory (cheb_evolve_host): three device buffers (one being
+    // propagated while the next job's state arrives and the previous one's leaves), a stream
+    // per copy direction and their events (created on first use)
+    static constexpr int kJobBuffers = 3;
+    static_assert(kJobBuffers <= kGraphSlots, "every job buffer needs its own step graph");
+    void* d_job[kJobBuffers] = {};
     cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
-    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr},
-                ev_out[2] = {nullptr, nullptr};
+    cudaEvent_t ev_in[kJobBuffers] = {}, ev_done[kJobBuffers] = {}, ev_out[kJobBuffers] = {};
 
     int64_t launches = 0;
 

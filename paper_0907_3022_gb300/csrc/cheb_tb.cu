@@ -287,9 +287,11 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
             // ---- s recurrence orders in shared memory -------------------------------------
             PT* sP = sP0;
             PT* sQ = sQ0;
+            float2 qn = qc[B.coef_off + a.ka];  // q_k read one order ahead
             for (int k = a.ka; k <= ke; ++k) {
                 const int sh = k - a.ka + 1;  // order k is computed on the region shrunk by sh
-                const float2 qk = qc[B.coef_off + k];
+                const float2 qk = qn;
+                if (k < ke) qn = qc[B.coef_off + k + 1];
                 PT* __restrict__ Pw = sP;        // T_{k-2} in, T_k out (own site only)
                 const PT* __restrict__ Qr = sQ;  // T_{k-1}, read at the site and neighbours
 #pragma unroll
