@@ -270,6 +270,9 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
             tb_split(B.beta, bh, bl);
             cp_async_wait_all();
             __syncthreads();
+            float dreg[SPT];  // the on-site values of this thread's sites, read once per tile
+#pragma unroll
+            for (int j = 0; j < SPT; ++j) dreg[j] = sD[min(tid + j * TB_THREADS, RMAX - 1)];
             if (first) {  // q_0 T_0
                 const float2 q0 = qc[B.coef_off + 0];
 #pragma unroll
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                 for (int j = 0; j < SPT; ++j) {
                     if (dlim[j] < sh) continue;
                     const int idx = tid + j * TB_THREADS;
-                    const float d = sD[idx];
+                    const float d = dreg[j];
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
                         const PT* Q = Qr + p * RP;
