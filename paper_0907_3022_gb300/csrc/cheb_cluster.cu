@@ -255,7 +255,7 @@ static int cluster_prepare_r(int ctas, int spt, int threads, size_t smem, int* f
 // device cannot schedule such a cluster.
 int cluster_configure(Plan* p, int ctas)
 {
-    if (ctas != 8 && ctas != 16) return fail(CHEB_ERR_INVALID, "cluster size must be 8 or 16");
+    if (ctas != 8 && ctas != CL_MAX_CTAS) return fail(CHEB_ERR_INVALID, "cluster size must be 8 or 16");
     int chunk, threads, spt, fits = 0;
     size_t smem;
     cluster_shape(p, ctas, &chunk, &threads, &spt, &smem);
