@@ -1007,8 +1007,66 @@ extern "C" int cheb_autotune(cheb_plan* plan)
     // matrix-free Holstein: its kernel variants (configurations per thread, register cap)
     std::vector<int> nr_c = {p->holmf_variant};
     if (p->op == OP_HOLMF) nr_c = {0, 1, 2};
+    // mean time of one single-order launch: a warm-up launch timed with events; launches of
+    // 0.2 ms or more are timed three more times with events, shorter ones (L2-resident
+    // vectors, where launch gaps and event jitter dominate) as 16 launches captured in a graph
+    // and replayed twice
+    auto time_launch = [&](const RecArgs& a, float* out_ms) -> int {
+        cudaEventRecord(e0, p->stream);
+        int r = launch_recurrence(p, a, p->op, p->prec, p->stream);
+        cudaEventRecord(e1, p->stream);
+        if (r) return r;
+        CHEB_CUDA(cudaEventSynchronize(e1));
+        float ms0 = 0.0f;
+        cudaEventElapsedTime(&ms0, e0, e1);
+        if (ms0 >= 0.2f) {
+            float tot = 0.0f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, p->stream);
+                r = launch_recurrence(p, a, p->op, p->prec, p->stream);
+                cudaEventRecord(e1, p->stream);
+                if (r) return r;
+                CHEB_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                tot += ms;
+            }
+            *out_ms = tot / 3.0f;
+            return CHEB_OK;
+        }
+        constexpr int kRep = 16;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        CHEB_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < kRep && !r; ++i) r = launch_recurrence(p, a, p->op, p->prec, p->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+        if (!r && ce == cudaSuccess) ce = cudaGraphInstantiate(&ge, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (r) {
+            if (ge) cudaGraphExecDestroy(ge);
+            return r;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "autotune launch graph");
+        cudaGraphLaunch(ge, p->stream);  // warm-up
+        cudaEventRecord(e0, p->stream);
+        cudaGraphLaunch(ge, p->stream);
+        cudaGraphLaunch(ge, p->stream);
+        cudaEventRecord(e1, p->stream);
+        ce = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaGraphExecDestroy(ge);
+        if (ce != cudaSuccess) return cuda_fail(ce, "autotune launch graph");
+        *out_ms = ms / (2.0f * kRep);
+        return CHEB_OK;
+    };
     float best = 1e30f;
     int bt = p->threads, bs = p->spt, bc = p->grid_cap, bv = p->vpt, bn = p->holmf_variant;
+    struct Cand {
+        float ms;
+        int th, spt, cap, vpt, nr;
+    };
+    std::vector<Cand> cands;
     int rc = CHEB_OK;
     const int64_t launches0 = p->launches;
     for (int nr : nr_c) {
@@ -1031,17 +1089,9 @@ extern "C" int cheb_autotune(cheb_plan* plan)
                         a.prev = p->d_B;
                         a.psi = scratch;
                         float tot = 0.0f;
-                        for (int rep = 0; rep < 4; ++rep) {
-                            cudaEventRecord(e0, p->stream);
-                            rc = launch_recurrence(p, a, p->op, p->prec, p->stream);
-                            cudaEventRecord(e1, p->stream);
-                            if (rc) break;
-                            cudaEventSynchronize(e1);
-                            float ms = 0.0f;
-                            cudaEventElapsedTime(&ms, e0, e1);
-                            if (rep > 0) tot += ms;  // first launch is warm-up
-                        }
+                        rc = time_launch(a, &tot);
                         if (rc) break;
+                        cands.push_back({tot, th, spt, p->grid_cap, vpt, nr});
                         if (tot < best) {
                             best = tot;
                             bt = th;
@@ -1058,22 +1108,6 @@ extern "C" int cheb_autotune(cheb_plan* plan)
             if (rc) break;
         }
         if (rc) break;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    p->threads = bt;
-    p->spt = bs;
-    p->grid_cap = bc;
-    p->vpt = bv;
-    p->holmf_variant = bn;
-    int rc2 = plan_build_items(p);
-    if (rc) {
-        cudaFree(scratch);
-        return rc;
-    }
-    if (rc2) {
-        cudaFree(scratch);
-        return rc2;
     }
     // whole steps as cheb_evolve runs them: the step's graph replayed (one warm-up, 3 timed)
     auto time_steps = [&](float* out_ms) -> int {
@@ -1093,6 +1127,58 @@ extern "C" int cheb_autotune(cheb_plan* plan)
         cudaEventDestroy(t1);
         return e == cudaSuccess ? CHEB_OK : cuda_fail(e, "autotune step timing");
     };
+    // a short step (small, L2-resident plans) mixes launch kinds whose best shapes differ and
+    // lasts about as long as the launch gaps, and one launch's time ranks the shapes poorly:
+    // there the shapes (at most 48, fastest single launch first) are compared as whole steps,
+    // single-order launches only
+    std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
+    if (!rc && cands.size() > 1 && cands[0].ms * (float)p->max_M < 2.0f) {
+        const int saved_s = p->tb_s, saved_cluster = p->cluster;
+        p->tb_s = 0;
+        p->tb_sched.clear();
+        p->cluster = 0;
+        float best_step = 1e30f;
+        for (size_t i = 0; i < cands.size() && i < 48 && !rc; ++i) {
+            const Cand& c = cands[i];
+            p->threads = c.th;
+            p->spt = c.spt;
+            p->vpt = c.vpt;
+            p->holmf_variant = c.nr;
+            rc = plan_build_items(p);
+            if (rc) break;
+            p->grid_cap = c.cap;
+            p->shape_epoch++;
+            float ms = 0.0f;
+            rc = time_steps(&ms);
+            if (!rc && ms < best_step) {
+                best_step = ms;
+                bt = c.th;
+                bs = c.spt;
+                bc = c.cap;
+                bv = c.vpt;
+                bn = c.nr;
+            }
+        }
+        p->tb_s = saved_s;
+        p->cluster = saved_cluster;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->threads = bt;
+    p->spt = bs;
+    p->grid_cap = bc;
+    p->vpt = bv;
+    p->holmf_variant = bn;
+    p->shape_epoch++;
+    int rc2 = plan_build_items(p);
+    if (rc) {
+        cudaFree(scratch);
+        return rc;
+    }
+    if (rc2) {
+        cudaFree(scratch);
+        return rc2;
+    }
     // single-order launches against temporal blocking (complex64 stencils)
     if (tb_eligible(p)) {
         p->tb_s = 0;
