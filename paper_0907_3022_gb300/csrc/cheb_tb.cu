@@ -417,16 +417,27 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
         __syncthreads();
         if (s_last) {
             __threadfence();
-            for (int slot = tid; slot < a.nblocks * NV; slot += blockDim.x) {
+            // one warp per (ribbon, vector) slot: lane l sums tiles l, l + 32, ..., then a
+            // fixed xor tree (the order depends on the tile count only, not on timing)
+            const int lane = tid & 31, warp = tid >> 5;
+            for (int slot = warp; slot < a.nblocks * NV; slot += TB_THREADS / 32) {
                 const int q = slot / NV, v = slot % NV;
+                const int it1 = a.block_tile_begin[q + 1];
                 double n2 = 0.0, eh = 0.0;
-                for (int it = a.block_tile_begin[q]; it < a.block_tile_begin[q + 1]; ++it) {
+#pragma unroll 4
+                for (int it = a.block_tile_begin[q] + lane; it < it1; it += 32) {
                     n2 += __ldcg(a.partials + ((size_t)it * NV + v) * 2 + 0);
                     eh += __ldcg(a.partials + ((size_t)it * NV + v) * 2 + 1);
                 }
-                const DevBlock Bq = a.blocks[q];
-                a.red_out[(size_t)slot * 2 + 0] = n2;
-                a.red_out[(size_t)slot * 2 + 1] = Bq.a * eh + Bq.b * n2;
+                for (int off = 16; off > 0; off >>= 1) {
+                    n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+                    eh += __shfl_xor_sync(0xffffffffu, eh, off);
+                }
+                if (lane == 0) {
+                    const DevBlock Bq = a.blocks[q];
+                    a.red_out[(size_t)slot * 2 + 0] = n2;
+                    a.red_out[(size_t)slot * 2 + 1] = Bq.a * eh + Bq.b * n2;
+                }
             }
             if (tid == 0) *a.done_counter = 0u;
         }
