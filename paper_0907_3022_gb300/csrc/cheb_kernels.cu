@@ -31,7 +31,10 @@
 namespace cheb {
 
 // Finalize FIRST-mode reductions: the last CTA to finish sums the per-item partials of each
-// block in item order and writes (||psi||^2, <psi|H|psi>) per (block, vec).
+// block and writes (||psi||^2, <psi|H|psi>) per (block, vec).  One warp per (block, vec)
+// slot: lane l sums items l, l + 32, ... in order, then a fixed xor tree, so the summation
+// order depends on the item count only (a single thread per slot walked thousands of
+// partials out of L2 one after another).
 __device__ void finalize_first(const RecArgs& a)
 {
     __shared__ unsigned int s_last;
@@ -45,16 +48,25 @@ __device__ void finalize_first(const RecArgs& a)
     if (!s_last) return;
     __threadfence();
     const int nv = a.nvec;
-    for (int slot = threadIdx.x; slot < a.nblocks * nv; slot += blockDim.x) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int slot = warp; slot < a.nblocks * nv; slot += nwarps) {
         const int q = slot / nv, v = slot % nv;
+        const int it1 = a.block_item_begin[q + 1];
         double n2 = 0.0, eh = 0.0;
-        for (int it = a.block_item_begin[q]; it < a.block_item_begin[q + 1]; ++it) {
+#pragma unroll 8
+        for (int it = a.block_item_begin[q] + lane; it < it1; it += 32) {
             n2 += __ldcg(a.partials + ((size_t)it * nv + v) * 2 + 0);
             eh += __ldcg(a.partials + ((size_t)it * nv + v) * 2 + 1);
         }
-        const DevBlock B = a.blocks[q];
-        a.red_out[(size_t)slot * 2 + 0] = n2;
-        a.red_out[(size_t)slot * 2 + 1] = B.a * eh + B.b * n2;  // <H> = a <H~> + b ||psi||^2
+        for (int off = 16; off > 0; off >>= 1) {
+            n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+            eh += __shfl_xor_sync(0xffffffffu, eh, off);
+        }
+        if (lane == 0) {
+            const DevBlock B = a.blocks[q];
+            a.red_out[(size_t)slot * 2 + 0] = n2;
+            a.red_out[(size_t)slot * 2 + 1] = B.a * eh + B.b * n2;  // <H> = a <H~> + b ||psi||^2
+        }
     }
     if (threadIdx.x == 0) *a.done_counter = 0u;  // ready for the next FIRST launch
 }
