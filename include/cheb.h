@@ -275,9 +275,14 @@ int cheb_holstein_phonon_neighbors(int L, int nph, int64_t p0, int64_t count, in
                                    int64_t* dn);
 
 /* ---- tuning --------------------------------------------------------------------------- */
-/* Times the plan's recurrence kernel over launch shapes (threads per block, sites per
-   thread, vectors per thread, grid size) on the plan's own workspace and keeps the fastest;
-   the choice is kept in the plan.  Needs a time step set (CHEB_ERR_STATE otherwise).
+/* Times the plan's recurrence over launch shapes on the plan's own workspace and keeps the
+   fastest; the choice is kept in the plan.  Three passes: single-order launch shapes
+   (threads per block, sites per thread, vectors per thread, grid size; the matrix-free
+   Holstein variants), one launch timed as a captured graph of 16 when it is short, and the
+   shapes of short steps (best launch x M < 2 ms) ranked again by whole steps; then temporal
+   blocking (complex64 lattice plans) and cluster steps (small 1D grids) against single-order
+   launches, by whole steps replayed from the step's CUDA graph.  Allocates one scratch
+   vector for the duration of the call.  Needs a time step set (CHEB_ERR_STATE otherwise).
    Optional: plans start from a fixed default. */
 int cheb_autotune(cheb_plan* plan);
 /* Temporal blocking (complex64 lattice plans with nvec 1, 2 or 4 and a shared on-site
