@@ -321,6 +321,17 @@ int cheb_plan_blocking(const cheb_plan* plan, int* orders_per_launch, int* sites
                        int* threads);
 
 /* ---- introspection for tests ---------------------------------------------------------- */
+/* The tiles temporal blocking uses for one W x L brick-wall ribbon with orders_per_launch
+   orders per launch and region_sites sites per CTA (threads x sites_per_thread): per tile 8
+   int32 (R0, R1, C0, C1, r0, r1, c0, c1), the region [R0, R1) x [C0, C1) and its interior
+   [r0, r1) x [c0, c1) in ribbon rows and columns.  The halo is orders_per_launch columns and
+   ceil(orders_per_launch / 2) rows on every side that is not a ribbon edge (Sec. 3.2
+   lattice; the bound on the rows follows from the alternating vertical bonds).  *ntiles gets
+   the count; up to `capacity` tiles are written to the caller's out (capacity 0: count only).
+   Host-only, no device memory; CHEB_ERR_INVALID for bad arguments or a ribbon whose single
+   interior column would not fit. */
+int cheb_tb_tiles(int W, int L, int orders_per_launch, int region_sites, int32_t* out,
+                  int64_t capacity, int64_t* ntiles);
 /* Copies of the plan's device data to host memory, for checking the construction:
    the SELL matrix of a Holstein plan as CSR in original row order (rowptr [n+1] int64,
    col [nnz] int64, val [nnz] double with the unscaled H entries); nnz_out gets the count.

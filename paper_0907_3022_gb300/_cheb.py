@@ -95,6 +95,8 @@ _SIGS = {
     "cheb_holstein_unrank": ([_c.c_int, _c.c_int, _c.c_int64, _u8p, _ip], _c.c_int),
     "cheb_holstein_phonon_neighbors": ([_c.c_int, _c.c_int, _c.c_int64, _c.c_int64, _i64p,
                                         _i64p], _c.c_int),
+    "cheb_tb_tiles": ([_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_int32),
+                       _c.c_int64, _i64p], _c.c_int),
     "cheb_autotune": ([_vp], _c.c_int),
     "cheb_plan_launch": ([_vp, _ip, _ip, _ip, _ip], _c.c_int),
     "cheb_plan_set_blocking": ([_vp, _c.c_int, _c.c_int, _c.c_int], _c.c_int),
@@ -199,6 +201,21 @@ def cheb_holstein_phonon_neighbors(L: int, nph: int, p0: int, count: int):
                                                dn.ctypes.data_as(_i64p)),
           "cheb_holstein_phonon_neighbors")
     return up, dn
+
+
+def cheb_tb_tiles(W: int, L: int, orders_per_launch: int, region_sites: int):
+    """int32 [ntiles, 8]: (R0, R1, C0, C1, r0, r1, c0, c1) of each temporal-blocking tile of a
+    W x L ribbon (region, then interior; rows and columns half-open)."""
+    import numpy as np
+
+    n = ctypes.c_int64()
+    check(lib().cheb_tb_tiles(W, L, orders_per_launch, region_sites, None, 0, ctypes.byref(n)),
+          "cheb_tb_tiles")
+    out = np.zeros((n.value, 8), dtype=np.int32)
+    check(lib().cheb_tb_tiles(W, L, orders_per_launch, region_sites,
+                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n.value,
+                              ctypes.byref(n)), "cheb_tb_tiles")
+    return out
 
 
 # ---- plans ---------------------------------------------------------------------------------

@@ -1266,6 +1266,25 @@ extern "C" int cheb_autotune(cheb_plan* plan)
     return CHEB_OK;
 }
 
+extern "C" int cheb_tb_tiles(int W, int L, int orders_per_launch, int region_sites,
+                             int32_t* out, int64_t capacity, int64_t* ntiles)
+{
+    if (!ntiles) return fail(CHEB_ERR_INVALID, "cheb_tb_tiles: NULL count");
+    if (W < 1 || L < 1 || orders_per_launch < 1 || region_sites < 1)
+        return fail(CHEB_ERR_INVALID, "cheb_tb_tiles: W, L, orders_per_launch, region_sites >= 1");
+    if (capacity > 0 && !out) return fail(CHEB_ERR_INVALID, "cheb_tb_tiles: NULL out");
+    std::vector<TBTile> tiles;
+    if (!tb_tiles_of_ribbon(W, L, orders_per_launch, region_sites, 0, tiles))
+        return fail(CHEB_ERR_INVALID, "cheb_tb_tiles: the ribbon does not fit the region budget");
+    *ntiles = (int64_t)tiles.size();
+    for (size_t i = 0; i < tiles.size() && (int64_t)i < capacity; ++i) {
+        const TBTile& t = tiles[i];
+        const int32_t v[8] = {t.R0, t.R1, t.C0, t.C1, t.r0, t.r1, t.c0, t.c1};
+        std::memcpy(out + 8 * i, v, sizeof(v));
+    }
+    return CHEB_OK;
+}
+
 extern "C" int cheb_plan_export_csr(cheb_plan* plan, int64_t* rowptr, int64_t* col, double* val,
                                     int64_t* nnz_out)
 {

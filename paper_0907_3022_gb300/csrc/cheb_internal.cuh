@@ -159,6 +159,9 @@ bool tb_supported(int nv, int spt, int tpb);
 int tb_launch(Plan* p, const TBArgs& a, cudaStream_t s);
 int tb_configure(int nv, int spt, int tpb);
 bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vector<int32_t>& begin);
+// the tiles of one W x L ribbon for s orders per launch and rmax region sites per CTA
+// (appended to tiles); false if one interior column does not fit
+bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TBTile>& tiles);
 
 // kernel launchers (cheb_kernels.cu)
 int launch_recurrence(Plan* p, const RecArgs& a, int op, int prec, cudaStream_t s);

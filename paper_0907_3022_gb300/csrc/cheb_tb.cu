@@ -510,60 +510,66 @@ int tb_launch(Plan* p, const TBArgs& a, cudaStream_t s)
 // Tiles for a halo of s: row bands chosen for the least halo waste, then as many interior
 // columns as the region budget (threads * spt sites) allows.  Returns false if a ribbon cannot be
 // tiled (the region of one interior column would not fit).
-bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vector<int32_t>& begin)
+bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TBTile>& tiles)
 {
-    const int rmax = p->tb_tpb * p->tb_spt;
     // halo widths for s orders: s columns, but only ceil(s / 2) rows, since d rows away is at
     // least 2d - 1 bonds on the brick wall (the kernel's validity distance counts the same way)
     const int hr = (s + 1) / 2;
+    // row bands: pick the band count whose tiles waste the least region on halos
+    int best_nbr = -1;
+    double best_eff = 0.0;
+    for (int nbr = 1; nbr <= W; ++nbr) {
+        const int tr = (W + nbr - 1) / nbr;
+        const int rh = std::min(W, tr + (nbr > 1 ? 2 * hr : 0));  // worst band
+        const int tcmax = rmax / rh - (L > rmax / rh ? 2 * s : 0);
+        if (tcmax < 1) continue;
+        const int tc = std::min(tcmax, L);
+        const double eff = (double)tr * tc / ((double)rh * (tc + (L > tc ? 2 * s : 0)));
+        if (eff > best_eff * 1.02) {
+            best_eff = eff;
+            best_nbr = nbr;
+        }
+        if (tr <= 2 * hr) break;
+    }
+    if (best_nbr < 0) return false;
+    const int tr = (W + best_nbr - 1) / best_nbr;
+    for (int r0 = 0; r0 < W; r0 += tr) {
+        const int r1 = std::min(W, r0 + tr);
+        const int R0 = std::max(0, r0 - hr), R1 = std::min(W, r1 + hr);
+        const int rh = R1 - R0;
+        int tc = rmax / rh;
+        if (tc < L) tc -= 2 * s;  // halo on both column sides
+        if (tc < 1) return false;
+        const int nbc = (L + tc - 1) / tc;
+        tc = (L + nbc - 1) / nbc;
+        for (int c0 = 0; c0 < L; c0 += tc) {
+            const int c1 = std::min(L, c0 + tc);
+            TBTile t{};
+            t.block = block;
+            t.R0 = R0;
+            t.R1 = R1;
+            t.C0 = std::max(0, c0 - s);
+            t.C1 = std::min(L, c1 + s);
+            t.r0 = r0;
+            t.r1 = r1;
+            t.c0 = c0;
+            t.c1 = c1;
+            if ((int64_t)(t.R1 - t.R0) * (t.C1 - t.C0) > rmax) return false;
+            tiles.push_back(t);
+        }
+    }
+    return true;
+}
+
+bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vector<int32_t>& begin)
+{
+    const int rmax = p->tb_tpb * p->tb_spt;
     tiles.clear();
     begin.assign(p->nblocks + 1, 0);
     for (int q = 0; q < p->nblocks; ++q) {
         begin[q] = (int32_t)tiles.size();
         const DevBlock& B = p->hblocks[q];
-        // row bands: pick the band count whose tiles waste the least region on halos
-        int best_nbr = -1;
-        double best_eff = 0.0;
-        for (int nbr = 1; nbr <= B.W; ++nbr) {
-            const int tr = (B.W + nbr - 1) / nbr;
-            const int rh = std::min(B.W, tr + (nbr > 1 ? 2 * hr : 0));  // worst band
-            const int tcmax = rmax / rh - (B.L > rmax / rh ? 2 * s : 0);
-            if (tcmax < 1) continue;
-            const int tc = std::min(tcmax, B.L);
-            const double eff = (double)tr * tc / ((double)rh * (tc + (B.L > tc ? 2 * s : 0)));
-            if (eff > best_eff * 1.02) {
-                best_eff = eff;
-                best_nbr = nbr;
-            }
-            if (tr <= 2 * hr) break;
-        }
-        if (best_nbr < 0) return false;
-        const int tr = (B.W + best_nbr - 1) / best_nbr;
-        for (int r0 = 0; r0 < B.W; r0 += tr) {
-            const int r1 = std::min(B.W, r0 + tr);
-            const int R0 = std::max(0, r0 - hr), R1 = std::min(B.W, r1 + hr);
-            const int rh = R1 - R0;
-            int tc = rmax / rh;
-            if (tc < B.L) tc -= 2 * s;  // halo on both column sides
-            if (tc < 1) return false;
-            const int nbc = (B.L + tc - 1) / tc;
-            tc = (B.L + nbc - 1) / nbc;
-            for (int c0 = 0; c0 < B.L; c0 += tc) {
-                const int c1 = std::min(B.L, c0 + tc);
-                TBTile t{};
-                t.block = q;
-                t.R0 = R0;
-                t.R1 = R1;
-                t.C0 = std::max(0, c0 - s);
-                t.C1 = std::min(B.L, c1 + s);
-                t.r0 = r0;
-                t.r1 = r1;
-                t.c0 = c0;
-                t.c1 = c1;
-                if ((int64_t)(t.R1 - t.R0) * (t.C1 - t.C0) > rmax) return false;
-                tiles.push_back(t);
-            }
-        }
+        if (!tb_tiles_of_ribbon(B.W, B.L, s, rmax, q, tiles)) return false;
     }
     begin[p->nblocks] = (int32_t)tiles.size();
     return true;

@@ -9,6 +9,8 @@ a bond (so a site computed at order i reads neighbours valid at order i - 1)."""
 import collections
 import random
 
+import pytest
+
 
 def _neighbours(r, c, W, L):
     out = []
@@ -95,3 +97,64 @@ def test_row_halo_of_half_the_orders_suffices():
         for r in range(R0 + hr, R1 - hr):
             for c in range(L):
                 assert _limit(r, c, W, L, R0, R1, 0, L) >= s
+
+
+# ---- the library's tile builder (host code, no GPU) -----------------------------------------
+def _tiles(W, L, s, budget):
+    import paper_0907_3022_gb300 as cb
+
+    return cb.cheb_tb_tiles(W, L, s, budget)
+
+
+def _check_tiles(W, L, s, budget):
+    import numpy as np
+
+    tiles = _tiles(W, L, s, budget)
+    hr = (s + 1) // 2
+    cover = np.zeros((W, L), dtype=np.int32)
+    for R0, R1, C0, C1, r0, r1, c0, c1 in tiles.tolist():
+        assert 0 <= R0 <= r0 < r1 <= R1 <= W and 0 <= C0 <= c0 < c1 <= C1 <= L
+        assert (R1 - R0) * (C1 - C0) <= budget
+        # halo: ceil(s/2) rows and s columns wherever the side is not a ribbon edge
+        assert r0 - R0 == min(hr, r0) and R1 - r1 == min(hr, W - r1)
+        assert c0 - C0 == min(s, c0) and C1 - c1 == min(s, L - c1)
+        cover[r0:r1, c0:c1] += 1
+        # every interior site keeps all s orders under the kernel's validity limit
+        for r in range(r0, r1):
+            for c in range(c0, c1):
+                assert _limit(r, c, W, L, R0, R1, C0, C1) >= s
+    assert (cover == 1).all()  # the interiors partition the ribbon
+    return len(tiles)
+
+
+def test_tiles_partition_the_ribbon_with_valid_interiors():
+    for W, L in [(1, 1), (1, 300), (2, 3), (3, 5), (7, 230), (50, 60), (97, 41), (130, 30),
+                 (160, 400), (77, 900), (40, 500)]:
+        for s in (1, 2, 3, 5, 8, 10, 12):
+            for budget in (1024, 3072, 8192):
+                _check_tiles(W, L, s, budget)
+
+
+def test_tiles_of_the_ensemble_ribbons():
+    """All 64 ribbons of the default ensemble at the tuned shape (10 orders, 512 x 6 sites):
+    the tile count the tuned launches process."""
+    import workloads as wl
+
+    ens = wl.RibbonEnsemble()
+    total = 0
+    for W, L in ens.sizes:
+        total += len(_tiles(W, L, 10, 3072))
+    for W, L in ens.sizes[:4]:  # the full per-site checks on a few of them
+        _check_tiles(W, L, 10, 3072)
+    assert total == 8445  # the first launch's CTA count in the DRAM capture of the profile
+
+
+def test_tiles_rejected_when_one_column_does_not_fit():
+    import paper_0907_3022_gb300 as cb
+
+    with pytest.raises(cb.ChebError) as e:
+        # a one-row band needs 1 + 2 x 5 rows and 1 + 2 x 10 columns: 231 > 100 sites
+        cb.cheb_tb_tiles(300, 5000, 10, 100)
+    assert e.value.status == cb.CHEB_ERR_INVALID
+    with pytest.raises(cb.ChebError):
+        cb.cheb_tb_tiles(0, 10, 4, 1024)
