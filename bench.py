@@ -56,11 +56,6 @@ ALG_BYTES_PER_UNIT = {
     ("holstein-mf", "c64"): 40.0, ("holstein-mf", "f64"): 80.0,     # vectors only
 }
 
-# DRAM bytes of one step of the default ensemble (dram__bytes_read.sum +
-# dram__bytes_write.sum over all launches of a step, one ncu pass), by blocking (orders per
-# launch, sites per thread, threads per CTA); the launches per step follow from the schedule.
-TB_DRAM_BYTES_PER_STEP = {(8, 6, 512): 6.99e9, (10, 6, 512): 4.01e9}
-
 # DRAM bytes of one step of the paper's polaron run with the matrix-free operator, by
 # (precision, M), same capture method
 POLARON_MF_DRAM_BYTES_PER_STEP = {("c64", 24): 497.5e9}
@@ -252,7 +247,7 @@ def run_reference(args, world, rank):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": "4 ribbons x 4 packets per step"},
         "site_steps_per_s": ss / tt,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_nproc": os.cpu_count(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -275,6 +270,65 @@ def make_plan(cb, ens, prec, nvec, packets):
     dt = torch.complex64 if prec == cb.CHEB_C64 else torch.complex128
     psi = torch.from_numpy(packets).to(dt).to("cuda").contiguous()
     return plan, psi
+
+
+def blocked_roofline(cb, plan, kms, kcount, steps, alg_per_unit, unit_definition):
+    """Roofline of the recurrence launches of the timed region (their CUDA-event time).
+
+    Temporal blocking (k_rec_tb): the launches reuse every vector element for s orders out of
+    shared memory, so their bound is the shared-memory pipe, not HBM.  achieved = the
+    shared-memory bytes the launches move (cheb_plan_step_model: per formed site-order the
+    own-site, neighbour and T_{k-2} loads and the T_k store, plus region copies and read-back)
+    / their event time, against the shared-memory load bandwidth measured in this run by the
+    library's probe.  Beside it: DRAM bytes derived from the tile set (every operand once per
+    launch) against HBM, and the streaming-equivalent rate (the per-unit bytes an unblocked
+    kernel would move for the same useful site-orders) against HBM.
+    Single-order launches: bound HBM, achieved = their algorithmic DRAM bytes / time."""
+    peak_hbm, hbm_kind = measured_peaks()
+    model = plan.step_model()
+    lps = model["launches"]
+    ms_per_launch = kms / max(kcount, 1)
+    sec = ms_per_launch / 1e3
+    useful_pl = model["useful_site_orders"] / lps
+    stream_equiv = alg_per_unit * useful_pl / sec / 1e9
+    dram_pl = model["dram_bytes"] / lps
+    blk = tuple(plan.blocking_shape())
+    common = {"launches": kcount, "launches_per_step": lps, "kernel_ms_total": kms,
+              "ms_per_launch": ms_per_launch, "unit_definition": unit_definition,
+              "useful_site_orders_per_launch": useful_pl,
+              "streaming_equivalent": {"achieved": stream_equiv, "peak": peak_hbm,
+                                       "frac": stream_equiv / peak_hbm, "unit": "GB/s",
+                                       "alg_bytes_per_unit": alg_per_unit,
+                                       "note": "per-unit bytes of an unblocked kernel x useful "
+                                               "site-orders / time; above 1 when data is reused "
+                                               "on chip"}}
+    if blk[0]:
+        smem_peak = cb.cheb_measure_peak(cb.CHEB_PEAK_SMEM_LOAD_GBS)
+        smem_pl = model["smem_bytes"] / lps
+        achieved = smem_pl / sec / 1e9
+        r = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
+             "frac": achieved / smem_peak, "traffic": dram_pl,
+             "kernel": "k_rec_tb<%d,%d,%d> (all launches of the step)" % (plan.nvec, blk[1], blk[2]),
+             "peak_kind": "shared-memory load bandwidth measured in this run by the library's "
+                          "probe (cheb_measure_peak; MEASURED_PEAKS.json has no shared-memory "
+                          "figure)",
+             "smem_bytes_per_launch": smem_pl,
+             "computed_over_useful": model["computed_site_orders"] / model["useful_site_orders"],
+             "traffic_source": "derived from the tile set: every operand crossing DRAM once per "
+                               "launch, halo re-reads served by L2 (ncu cross-check in profiles/)",
+             "l2_bytes_per_launch": model["l2_bytes"] / lps,
+             "dram": {"achieved": dram_pl / sec / 1e9, "peak": peak_hbm,
+                      "frac": dram_pl / sec / 1e9 / peak_hbm, "unit": "GB/s",
+                      "peak_kind": f"{hbm_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}}
+    else:
+        achieved = dram_pl / sec / 1e9
+        r = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+             "frac": achieved / peak_hbm, "traffic": dram_pl,
+             "kernel": "k_rec<float,%d,StencilOp> (all launches of the step)" % plan.launch_shape()[3],
+             "peak_kind": f"{hbm_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+             "traffic_source": "algorithmic: every operand read or written once per launch"}
+    r.update(common)
+    return r
 
 
 def run_ours(args, world, rank, local):
@@ -330,31 +384,9 @@ def run_ours(args, world, rank, local):
     value = sum_over_ranks(mv_per_step * args.steps, world) / (ms / 1e3)
     site_steps = sum_over_ranks(ss_per_step * args.steps, world) / (ms / 1e3)
 
-    peak, peak_kind = measured_peaks()
-    # per launch: the unblocked algorithmic bytes of the site-orders it forms
-    launches_per_step = kcount / args.steps
-    alg_per_launch = ALG_BYTES_PER_UNIT[("ensemble", "c64")] * (ss_per_step / ens.nvec) / launches_per_step
-    ms_per_launch = kms / kcount
-    achieved = alg_per_launch / (ms_per_launch / 1e3) / 1e9  # GB/s
-    blk = tuple(plan.blocking_shape())
-    traffic = None
-    if blk in TB_DRAM_BYTES_PER_STEP and sorted(set(Ms)) == [20, 21]:
-        traffic = TB_DRAM_BYTES_PER_STEP[blk] / launches_per_step
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": ("k_rec_tb<4,%d,%d> (all launches of the step)" % (blk[1], blk[2])
-                           if blk[0] else
-                           "k_rec<float,%d,StencilOp> (all launches of the step)"
-                           % plan.launch_shape()[3]),
-                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "launches": kcount, "kernel_ms_total": kms,
-                "alg_bytes_per_launch": alg_per_launch,
-                "alg_bytes_per_unit": ALG_BYTES_PER_UNIT[("ensemble", "c64")],
-                "unit_definition": "one site (4 packets) and one Chebyshev order",
-                "kernel_bytes_per_launch": kbytes / max(kcount, 1),
-                "kernel_bytes_note": "operands the blocked launches themselves must move "
-                                     "(region inputs once per interior site)",
-                "dram_achieved": (traffic / (ms_per_launch / 1e3) / 1e9) if traffic else None}
+    roofline = blocked_roofline(cb, plan, kms, kcount, args.steps,
+                                ALG_BYTES_PER_UNIT[("ensemble", "c64")],
+                                "one site (4 packets) and one Chebyshev order")
 
     out = {}
     if not args.lean:
@@ -423,22 +455,36 @@ def run_ours(args, world, rank, local):
         f_ms = f0.elapsed_time(f1)
         k64ms, k64n, k64b = plan64.kernel_stats(reset=True)
         ss64 = sum(m * s for m, s in zip(Ms, sites)) * k64 / (f_ms / 1e3)
+        # FP64 roofline of the single-order kernel k_rec<double,1,StencilOp>: per site-order it
+        # issues 4 DADD (neighbour sums) + 4 DFMA (2 H~ x - p) on the FP64 pipe, plus 6 DFMA
+        # of the psi accumulation every third order: 10 FP64 pipe instructions on average,
+        # against the FP64 FMA rate measured in this run by the library's probe
+        fp64_peak = cb.cheb_measure_peak(cb.CHEB_PEAK_FP64_GFLOPS)  # GFLOP/s, 2 per DFMA
+        ss64_k = sum(m * s for m, s in zip(Ms, sites)) * k64 / (k64ms / 1e3)  # kernel time only
+        inst_rate = 10.0 * ss64_k / 1e9  # G FP64 instructions / s
         out["fp64_single_vector"] = {
             "matvec_steps_per_s": sum(Ms) * k64 / (f_ms / 1e3),
             "site_steps_per_s": ss64,
             "complex64_batched_site_vector_steps_per_s": site_steps,
             "speedup_c64_batched_over_fp64": site_steps / ss64,
             "kernel_achieved_gbs": k64b / (k64ms / 1e3) / 1e9,
+            "roofline": {"bound": "fp64", "achieved": inst_rate, "peak": fp64_peak / 2.0,
+                         "unit": "G FP64 pipe instructions/s", "frac": inst_rate / (fp64_peak / 2.0),
+                         "kernel": "k_rec<double,1,StencilOp>",
+                         "per_unit": "10 FP64 instructions per site-order (4 DADD + 4 DFMA, "
+                                     "6 DFMA every third order)",
+                         "peak_kind": "DFMA rate measured in this run by the library's probe "
+                                      "(cheb_measure_peak)",
+                         "hbm_frac": k64b / (k64ms / 1e3) / 1e9 / measured_peaks()[0]},
             "steps": k64,
-            "note": "same ensemble, one packet (k0 = pi/3), complex128; FP64 is ~1.2 TFLOP/s "
-                    "on GB300, so this path is bound by FP64 arithmetic",
+            "note": "same ensemble, one packet (k0 = pi/3), complex128",
         }
         plan64.close()
 
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         # bounded sample: one dt of the first 24 ribbons x 4 packets on one host core
         t, mv, ss = oracle_ensemble_sample(ens, list(range(24)))
-        out["cpu_baseline"] = {"value": mv / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+        out["cpu_baseline"] = {"value": mv / t, "unit": UNIT, "cores": 1, "host_nproc": os.cpu_count(), "kind": "oracle",
                                "sample": "one dt of ribbons 0-23 x 4 packets (FP64 oracle, "
                                          "single thread)",
                                "site_steps_per_s": ss / t, "seconds": t}
@@ -590,7 +636,7 @@ def run_single(args, world, rank, local):
             t0 = time.perf_counter()
             Pr, gref, _ = H.adjoint_region(a, b, C, 20, cfg["packet"], mask)
             tcpu = time.perf_counter() - t0
-            out["cpu_baseline"] = {"value": 20 * (4 * M + 1) / tcpu, "unit": UNIT, "cores": 1,
+            out["cpu_baseline"] = {"value": 20 * (4 * M + 1) / tcpu, "unit": UNIT, "cores": 1, "host_nproc": os.cpu_count(),
                                    "kind": "oracle", "sample": "gradient through 20 of the 300 "
                                    "time steps (FP64 oracle stores every v_k)"}
         line_cfg = {"workload": cfg["name"], "checkpointing": "ceil(sqrt(M+1)) pairs per step"}
@@ -652,6 +698,9 @@ def run_single(args, world, rank, local):
                     "alg_bytes_per_launch": alg_per_launch, "alg_bytes_per_unit": per_unit,
                     "unit_definition": "one row (site) and one Chebyshev order",
                     "kernel_bytes_per_launch": kbytes / max(kcount, 1), "note": note}
+        if cfg["kind"] == "ribbon" and plan.blocking()[0]:
+            roofline = blocked_roofline(cb, plan, kms, kcount, min(args.steps, 5), per_unit,
+                                        "one site and one Chebyshev order")
         # accuracy: against the oracle after min(steps done, config) steps from the packet
         nacc = {"holstein": 2, "ribbon": 50}.get(cfg["kind"], cfg["nsteps"])
         if args.lean:
@@ -683,7 +732,7 @@ def run_single(args, world, rank, local):
             t0 = time.perf_counter()
             H.step(a, b, C, psi0)
             tcpu = time.perf_counter() - t0
-            out["cpu_baseline"] = {"value": mv_per_step / tcpu, "unit": UNIT, "cores": 1,
+            out["cpu_baseline"] = {"value": mv_per_step / tcpu, "unit": UNIT, "cores": 1, "host_nproc": os.cpu_count(),
                                    "kind": "oracle", "sample": "one time step (FP64 oracle)",
                                    "site_steps_per_s": ss_per_step / tcpu}
         # e2e: every step one job from pinned host memory through cheb_evolve_host
@@ -741,7 +790,7 @@ def run_reference_single(args, world, rank):
             "ms_per_step": 1e3 * tt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["name"]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_nproc": os.cpu_count(), "kind": "oracle",
                              "sample": f"{args.steps} time steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -819,7 +868,7 @@ def run_driven(args, world, rank, local):
                                                           / np.linalg.norm(ref)),
                            "sample": f"{nacc} steps from the packet"}
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = {"value": M * nacc / tcpu, "unit": UNIT, "cores": 1,
+            out["cpu_baseline"] = {"value": M * nacc / tcpu, "unit": UNIT, "cores": 1, "host_nproc": os.cpu_count(),
                                    "kind": "oracle", "sample": f"{nacc} driven steps (operator "
                                    "rebuilt every step, FP64 oracle, single thread)"}
     line = {"metric": METRIC, "value": M * K / (ms / 1e3), "unit": UNIT, "n_gpus": world,
@@ -905,7 +954,7 @@ def run_armchair(args, world, rank, local):
         acc["rel_l2_vs_fp64_oracle_dt100"] = max(errs)
         if not args.no_cpu_baseline:
             mv100 = sum(runs["100"]["M"]) * 100
-            out["cpu_baseline"] = {"value": mv100 / tcpu, "unit": UNIT, "cores": 1,
+            out["cpu_baseline"] = {"value": mv100 / tcpu, "unit": UNIT, "cores": 1, "host_nproc": os.cpu_count(),
                                    "kind": "oracle", "sample": "both ribbons to t = 10^4 with "
                                    "dt = 100 (FP64 oracle, single thread)",
                                    "seconds_to_t1e4_dt100": tcpu}

@@ -164,8 +164,11 @@ int cheb_step(cheb_plan* plan, void* psi, double dt);
 /* nsteps calls of cheb_step, replayed from one CUDA graph.  If obs_every > 0 and obs is not
    NULL, before every obs_every-th step s (s = 0, obs_every, ...) the plan records
    [||psi||^2, <psi|H|psi>] per (block, vec) into the device array obs (double, layout
-   [record][block][vec][2], records = ceil(nsteps / obs_every)).  The energy comes from
-   the first recurrence kernel of that step (v_1 = H~ psi), so it costs no extra matvec.
+   [record][block][vec][2], records = ceil(nsteps / obs_every)).  Both are FP64 reductions
+   (FP64 products and sums): complex128 plans take them from the first recurrence kernel of
+   that step (v_1 = H~ psi, no extra matvec); complex64 plans run one extra FP64 pass over
+   psi before a recorded step (their first recurrence kernel sums its per-thread terms in
+   FP32, which serve only the growth check below), so unrecorded steps cost nothing extra.
    Synchronises the stream and returns CHEB_ERR_DIVERGED if a recurrence vector exceeded
    the bound |v_k| <= ||psi|| that holds when the spectrum lies inside [emin, emax]. */
 int cheb_evolve(cheb_plan* plan, void* psi, double dt, int nsteps, int obs_every,
@@ -220,8 +223,7 @@ int cheb_observables(cheb_plan* plan, const void* psi, int kind, double param, d
 
 /* ---- plan-free region norm that allocates no device memory -------------------------- */
 /* The paper has no counterpart: this serves callers that may not allocate device memory
-   where they need a norm -- code running while a stream is captured in global mode (no
-   cudaMalloc allowed), latency-critical loops that cannot take the device-wide
+   where they need a norm -- latency-critical loops that cannot take the device-wide
    synchronisation of cudaMalloc/cudaFree, and host programs whose own pool owns all device
    memory.  For one zigzag ribbon (or the 1D grid, L = n) held as psi (device, [site][vec],
    complex128 or complex64 by prec, n_sites = W * L), out[v] (device, nvec doubles) =
@@ -353,6 +355,48 @@ int64_t cheb_plan_launches(const cheb_plan* plan);
 int cheb_plan_set_timing(cheb_plan* plan, int enable);
 int cheb_plan_kernel_stats(cheb_plan* plan, double* ms, int64_t* launches, double* bytes,
                            int reset);
+
+/* ---- work model and peak probes (measurement; no counterpart in the paper) ----------- */
+/* What one step of the plan's current launch schedule does, counted on the host from the
+   launch shapes and tiles (no device work):
+     useful_site_orders    sites x Chebyshev orders the step must form (a site carries all
+                           nvec vectors), summed over blocks: sum_q W_q L_q M_q;
+     computed_site_orders  the ones the kernels actually form: with temporal blocking the
+                           halo sites of a tile are formed too, for as many orders as they
+                           stay valid (equal to useful_site_orders for single-order launches);
+     smem_bytes            shared-memory bytes the blocked kernel loads and stores (region
+                           copies in, neighbour and own-site reads and the new values of every
+                           order, interior read-back); 0 for single-order launches;
+     dram_bytes            DRAM bytes if every operand crosses DRAM once per launch (halo
+                           re-reads of a blocked launch served by L2);
+     l2_bytes              bytes the launches move between L2 and the SMs (blocked: every
+                           region's inputs including the halos; single-order: dram_bytes);
+     launches              recurrence kernel launches per step.
+   Needs a dt (after the first cheb_step / cheb_evolve).  Cluster steps report useful =
+   computed and psi in and out as their traffic. */
+typedef struct {
+    double useful_site_orders;
+    double computed_site_orders;
+    double smem_bytes;
+    double dram_bytes;
+    double l2_bytes;
+    int64_t launches;
+} cheb_step_model;
+int cheb_plan_step_model(const cheb_plan* plan, cheb_step_model* out);
+
+/* Peak rates measured on the current device by the library's own micro-kernels, for
+   rooflines that have no external reference figure: the shared-memory load bandwidth of all
+   SMs (16-byte loads without bank conflicts, GB/s), and the FP64 and FP32 fused
+   multiply-add rates (GFLOP/s, 2 flops per FMA).  Each probe runs on every SM, timed with
+   CUDA events on stream (NULL = legacy default stream) after a warm-up launch, best of three;
+   it allocates 64 bytes of device memory and synchronises.  CHEB_ERR_INVALID for an unknown
+   kind. */
+typedef enum {
+    CHEB_PEAK_SMEM_LOAD_GBS = 0,
+    CHEB_PEAK_FP64_GFLOPS = 1,
+    CHEB_PEAK_FP32_GFLOPS = 2
+} cheb_peak_kind;
+int cheb_measure_peak(int kind, void* stream, double* value);
 
 #ifdef __cplusplus
 }

@@ -54,6 +54,20 @@ class cheb_ham_desc(ctypes.Structure):
     ]
 
 
+class cheb_step_model(ctypes.Structure):
+    _fields_ = [
+        ("useful_site_orders", ctypes.c_double),
+        ("computed_site_orders", ctypes.c_double),
+        ("smem_bytes", ctypes.c_double),
+        ("dram_bytes", ctypes.c_double),
+        ("l2_bytes", ctypes.c_double),
+        ("launches", ctypes.c_int64),
+    ]
+
+
+CHEB_PEAK_SMEM_LOAD_GBS, CHEB_PEAK_FP64_GFLOPS, CHEB_PEAK_FP32_GFLOPS = 0, 1, 2
+
+
 class ChebError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: status {status} ({msg})")
@@ -107,6 +121,8 @@ _SIGS = {
     "cheb_plan_launches": ([_vp], _c.c_int64),
     "cheb_plan_set_timing": ([_vp, _c.c_int], _c.c_int),
     "cheb_plan_kernel_stats": ([_vp, _dp, _i64p, _dp, _c.c_int], _c.c_int),
+    "cheb_plan_step_model": ([_vp, _c.POINTER(cheb_step_model)], _c.c_int),
+    "cheb_measure_peak": ([_c.c_int, _vp, _dp], _c.c_int),
     "cheb_region_norm_noalloc": ([_vp, _c.c_int, _c.c_int64, _c.c_int32, _c.c_int, _c.c_int64, _vp,
                                   _vp], _c.c_int),
 }
@@ -391,6 +407,12 @@ class Plan:
                                            ctypes.byref(by), int(reset)), "cheb_plan_kernel_stats")
         return ms.value, n.value, by.value
 
+    def step_model(self) -> dict:
+        """cheb_plan_step_model as a dict (work of one step of the current schedule)."""
+        m = cheb_step_model()
+        check(lib().cheb_plan_step_model(self.handle, ctypes.byref(m)), "cheb_plan_step_model")
+        return {name: getattr(m, name) for name, _ in cheb_step_model._fields_}
+
     def export_csr(self):
         import numpy as np
 
@@ -404,6 +426,15 @@ class Plan:
                                          col.ctypes.data_as(_i64p), val.ctypes.data_as(_dp),
                                          ctypes.byref(nnz)), "cheb_plan_export_csr")
         return rp, col, val
+
+
+def cheb_measure_peak(kind: int, stream=None) -> float:
+    """Peak measured by the library's micro-kernels on the current device: CHEB_PEAK_SMEM_LOAD_GBS
+    (GB/s), CHEB_PEAK_FP64_GFLOPS or CHEB_PEAK_FP32_GFLOPS (GFLOP/s)."""
+    v = ctypes.c_double()
+    check(lib().cheb_measure_peak(int(kind), _stream_handle(stream), ctypes.byref(v)),
+          "cheb_measure_peak")
+    return v.value
 
 
 def cheb_region_norm_noalloc(psi, prec: int, n_sites: int, L: int, nvec: int, col_min: int, out,

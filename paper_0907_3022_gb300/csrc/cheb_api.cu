@@ -465,6 +465,9 @@ static int enqueue_step_tb(Plan* p, void* psi, cudaStream_t st)
 
 int plan_enqueue_step(Plan* p, void* psi, cudaStream_t s) { return enqueue_step(p, psi, s); }
 
+// bytes of one record of cheb_evolve's obs array: [block][vec][2] doubles
+static size_t rec_bytes(const Plan* p) { return (size_t)p->nblocks * p->nvec * 2 * sizeof(double); }
+
 static int check_psi(const Plan* p, const void* psi)
 {
     if (!psi) return fail(CHEB_ERR_INVALID, "psi is NULL");
@@ -542,7 +545,7 @@ static void free_plan(Plan* p)
     void* ptrs[] = {p->d_blocks, p->d_items, p->d_block_item_begin, p->d_diag, p->d_A, p->d_B,
                     p->d_tail,
                     p->d_qcoef, p->d_partials, p->d_counter, p->d_red, p->d_err,
-                    p->d_obs_scratch, p->d_sell_col, p->d_sell_val, p->d_sell_chunk_off,
+                    p->d_obs_scratch, p->d_rec_scratch, p->d_sell_col, p->d_sell_val, p->d_sell_chunk_off,
                     p->d_sell_chunk_len, p->d_hol_diag_raw, p->d_sell_val_raw, p->d_binom,
                     p->d_hol_rowlen, p->d_holmf_G, p->d_holmf_dtab, p->d_holmf_qtab,
                     p->d_holmf_partials};
@@ -817,8 +820,18 @@ extern "C" int cheb_evolve(cheb_plan* plan, void* psi, double dt, int nsteps, in
         rc = ensure_graph(p, psi, &graph);
         if (rc) return rc;
     }
-    const size_t rec_bytes = (size_t)p->nblocks * p->nvec * 2 * sizeof(double);
+    const bool recording = obs && obs_every > 0;
+    if (recording && p->prec == CHEB_C64) {
+        rc = record_prepare(p);
+        if (rc) return rc;
+    }
     for (int s = 0; s < nsteps; ++s) {
+        const bool rec = recording && s % obs_every == 0;
+        double* slot = rec ? obs + (size_t)(s / obs_every) * p->nblocks * p->nvec * 2 : nullptr;
+        if (rec && p->prec == CHEB_C64) {
+            rc = launch_record(p, psi, slot, p->stream);
+            if (rc) return rc;
+        }
         if (p->timing) {
             rc = enqueue_step(p, psi, p->stream);
             if (rc) return rc;
@@ -826,9 +839,9 @@ extern "C" int cheb_evolve(cheb_plan* plan, void* psi, double dt, int nsteps, in
             CHEB_CUDA(cudaGraphLaunch(graph->exec, p->stream));
             p->launches += graph->kernels;
         }
-        if (obs && obs_every > 0 && s % obs_every == 0) {
-            CHEB_CUDA(cudaMemcpyAsync(obs + (size_t)(s / obs_every) * p->nblocks * p->nvec * 2,
-                                      p->d_red, rec_bytes, cudaMemcpyDeviceToDevice, p->stream));
+        if (rec && p->prec == CHEB_C128) {  // the first launch's FP64 sums of this step
+            CHEB_CUDA(cudaMemcpyAsync(slot, p->d_red, rec_bytes(p), cudaMemcpyDeviceToDevice,
+                                      p->stream));
         }
     }
     return cheb_sync(plan);
@@ -929,15 +942,25 @@ extern "C" int cheb_evolve_td(cheb_plan* plan, void* psi, double dt, int nsteps,
     if (obs && !aligned16(obs)) return fail(CHEB_ERR_ALIGN, "obs must be 16-byte aligned");
     rc = set_dt(p, dt);
     if (rc) return rc;
-    const size_t rec_bytes = (size_t)p->nblocks * p->nvec * 2 * sizeof(double);
+    const bool recording = obs && obs_every > 0;
+    if (recording && p->prec == CHEB_C64) {
+        rc = record_prepare(p);
+        if (rc) return rc;
+    }
     for (int s = 0; s < nsteps; ++s) {
         rc = launch_scale_diag(p, onsite_seq + (size_t)s * (size_t)stride, p->stream);
         if (rc) return rc;
+        const bool rec = recording && s % obs_every == 0;
+        double* slot = rec ? obs + (size_t)(s / obs_every) * p->nblocks * p->nvec * 2 : nullptr;
+        if (rec && p->prec == CHEB_C64) {
+            rc = launch_record(p, psi, slot, p->stream);
+            if (rc) return rc;
+        }
         rc = enqueue_step(p, psi, p->stream);
         if (rc) return rc;
-        if (obs && obs_every > 0 && s % obs_every == 0) {
-            CHEB_CUDA(cudaMemcpyAsync(obs + (size_t)(s / obs_every) * p->nblocks * p->nvec * 2,
-                                      p->d_red, rec_bytes, cudaMemcpyDeviceToDevice, p->stream));
+        if (rec && p->prec == CHEB_C128) {
+            CHEB_CUDA(cudaMemcpyAsync(slot, p->d_red, rec_bytes(p), cudaMemcpyDeviceToDevice,
+                                      p->stream));
         }
     }
     return cheb_sync(plan);
@@ -1263,6 +1286,50 @@ extern "C" int cheb_autotune(cheb_plan* plan)
     cudaFree(scratch);
     if (rc) return rc;
     p->tuned = true;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_step_model(const cheb_plan* plan, cheb_step_model* out)
+{
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    if (!p || !out) return fail(CHEB_ERR_INVALID, "cheb_plan_step_model: NULL argument");
+    if (!p->have_dt) return fail(CHEB_ERR_STATE, "cheb_plan_step_model: no dt yet");
+    std::memset(out, 0, sizeof(*out));
+    double useful = 0.0;
+    for (const DevBlock& B : p->hblocks) {
+        const double sites = (p->op != OP_STENCIL) ? (double)p->n_sites : (double)B.W * B.L;
+        useful += sites * B.M;
+    }
+    out->useful_site_orders = useful;
+    if (p->cluster && cluster_eligible(p)) {
+        out->computed_site_orders = useful;
+        out->dram_bytes = out->l2_bytes = (double)p->n_sites * (2.0 * p->cplx_size() + p->real_size());
+        out->launches = 1;
+        return CHEB_OK;
+    }
+    if (!p->tb_sched.empty()) {
+        TBModel m;
+        double dram = 0.0;
+        for (const Plan::TBLaunch& L : p->tb_sched) {
+            std::vector<TBTile> tiles;
+            std::vector<int32_t> begin;
+            if (!tb_build_tiles(p, p->tb_sets[L.set].s, tiles, begin))
+                return fail(CHEB_ERR_STATE, "cheb_plan_step_model: tiles");
+            tb_model_launch(p, tiles, L.ka, L.kb, L.prev_ka, m);
+            dram += tb_launch_bytes(p, L);
+        }
+        out->computed_site_orders = m.computed;
+        out->smem_bytes = m.smem;
+        out->l2_bytes = m.l2;
+        out->dram_bytes = dram;
+        out->launches = (int64_t)p->tb_sched.size();
+        return CHEB_OK;
+    }
+    double dram = 0.0;
+    for (int k = 1; k <= p->max_M; ++k) dram += launch_bytes(p, k);
+    out->computed_site_orders = useful;
+    out->dram_bytes = out->l2_bytes = dram;
+    out->launches = p->max_M;
     return CHEB_OK;
 }
 

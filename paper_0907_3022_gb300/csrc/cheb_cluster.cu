@@ -131,7 +131,9 @@ __global__ void __launch_bounds__(CL_THREADS) k_step_cluster(ClusterArgs a)
                 nxt[li] = h;
                 p[j] = x;
                 U::accum(to_tail ? tl[j] : acc[j], qk, h, k);
-                if (k == B.M) {  // growth check |T_M|^2 <= 4 ||psi||^2 (after the k = 1 sums)
+                // growth check |T_M|^2 <= 4 ||psi||^2: s_tot is written by the k = 1 sums below
+                // and read from k = 2 on (every plan has M >= 2, cheb_coeffs raises M = 1)
+                if (k == B.M && k >= 2) {
                     const R t2 = fma(h.x, h.x, h.y * h.y);
                     if (!(t2 <= (R)(4.0 * s_tot[0]))) atomicOr(a.errflag, 1);
                 }

@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 256 : 512, MINB) k_rec_holmf(RecArg
     C* __restrict__ accp = ag.to_tail ? tail : psi;
     for (int t = blockIdx.x; t < m.ntiles; t += gridDim.x) {
         R part0 = 0, part1 = 0;
+        double dpart0 = 0.0, dpart1 = 0.0;  // energy-only launches (observables): FP64 terms
         const uint32_t ub = (uint32_t)t * m.tile_units;
         const uint32_t u1 = min(ub + m.tile_units, units);
         for (uint32_t u0 = ub + threadIdx.x; u0 < u1; u0 += NR * blockDim.x) {
@@ -195,10 +196,15 @@ __global__ void __launch_bounds__(MINB > 1 ? 256 : 512, MINB) k_rec_holmf(RecArg
                     h.y = fma(d, xc[i].y, h.y);
                     if (FIRST) {
                         const C t1 = V2<R>::make((R)0.5 * h.x, (R)0.5 * h.y);
-                        if (ok[i]) {
+                        if (ok[i] && store) {
                             part0 = fma(xc[i].x, xc[i].x, fma(xc[i].y, xc[i].y, part0));
                             part1 = fma(xc[i].x, t1.x, fma(xc[i].y, t1.y, part1));
-                            if (store) out1[base] = t1;
+                            out1[base] = t1;
+                        } else if (ok[i]) {
+                            // energy of psi for cheb_observables: the row of 2 H~ psi in the
+                            // vector precision, its products and sums with psi in FP64
+                            dpart0 += (double)xc[i].x * xc[i].x + (double)xc[i].y * xc[i].y;
+                            dpart1 += (double)xc[i].x * t1.x + (double)xc[i].y * t1.y;
                         }
                     } else if (ok[i]) {
                         prev[base] = h;  // T_k over T_{k-2}
@@ -226,12 +232,12 @@ __global__ void __launch_bounds__(MINB > 1 ? 256 : 512, MINB) k_rec_holmf(RecArg
             }
         }
         if (FIRST) {
-            if constexpr (Split<R>::on) {  // complex64: FP32 warp tree, FP64 block sum
+            if (!store || !Split<R>::on) {  // FP64 tree
+                double dpart[2] = {store ? (double)part0 : dpart0, store ? (double)part1 : dpart1};
+                block_reduce_groups<2>(dpart, nv, s_red, a.partials + (size_t)t * nv * 2);
+            } else {  // complex64 recurrence (divergence-check norm): FP32 warp tree, FP64 block sum
                 float fpart[2] = {(float)part0, (float)part1};
                 block_reduce_groups_f<2>(fpart, nv, s_red, a.partials + (size_t)t * nv * 2);
-            } else {
-                double dpart[2] = {(double)part0, (double)part1};
-                block_reduce_groups<2>(dpart, nv, s_red, a.partials + (size_t)t * nv * 2);
             }
         }
     }

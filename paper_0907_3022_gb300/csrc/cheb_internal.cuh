@@ -162,12 +162,21 @@ bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vecto
 // the tiles of one W x L ribbon for s orders per launch and rmax region sites per CTA
 // (appended to tiles); false if one interior column does not fit
 bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TBTile>& tiles);
+// host work model of one blocked launch over the given tiles (cheb_plan_step_model)
+struct TBModel {
+    double useful = 0.0, computed = 0.0, smem = 0.0, l2 = 0.0;
+};
+void tb_model_launch(const Plan* p, const std::vector<TBTile>& tiles, int ka, int kb,
+                     int prev_ka, TBModel& m);
 
 // kernel launchers (cheb_kernels.cu)
 int launch_recurrence(Plan* p, const RecArgs& a, int op, int prec, cudaStream_t s);
 int launch_observable(Plan* p, const void* psi, int kind, double param, double* out,
                       cudaStream_t s);
 int launch_scale_diag(Plan* p, const double* onsite, cudaStream_t s);
+// FP64 record [block][vec][2] = (||psi||^2, <psi|H|psi>) of psi (complex64 plans' records)
+int record_prepare(Plan* p);
+int launch_record(Plan* p, const void* psi, double* out, cudaStream_t s);
 
 // one step of a small 1D grid on a thread-block cluster (cheb_cluster.cu)
 bool cluster_eligible(const Plan* p);
@@ -222,6 +231,8 @@ struct Plan {
     int* d_err = nullptr;
     double* d_obs_scratch = nullptr; // observable partials
     size_t obs_scratch_cap = 0;
+    double* d_rec_scratch = nullptr; // partials of the FP64 records (complex64 plans)
+    size_t rec_scratch_cap = 0;
 
     // SELL (Holstein)
     int64_t sell_nnz_stored = 0;

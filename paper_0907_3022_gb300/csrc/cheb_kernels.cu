@@ -23,6 +23,7 @@
 // T_{j-1}, d_i; write T_{j+1}; every third order also read and write psi.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 
 #include "cheb_device.cuh"
@@ -423,8 +424,151 @@ __global__ void k_obs_finalize(const double* partials, const int32_t* block_item
     }
 }
 
+// ---- FP64 records of ||psi||^2 and <psi|H|psi> (complex64 plans) -----------------------------
+// cheb_evolve records the norm and energy of psi at the start of every obs_every-th step.
+// complex128 plans take them from their first recurrence launch (FP64 throughout); complex64
+// plans compute them here instead, with FP64 products and sums of the complex64 values, so
+// that the first launch of a complex64 step keeps its FP32 per-thread sums (they feed only the
+// divergence check |T_M|^2 <= 4 ||psi||^2) and unrecorded steps pay nothing.
+// Stencil kinds: per work item and vector the two sums, then per (block, vec) in item order.
+template <typename R>
+__global__ void k_rec_obs_stencil(const WorkItem* items, int nitems, const DevBlock* blocks,
+                                  const void* psi_, const void* diag_, int diag_per_vec, int nvec,
+                                  double* partials)
+{
+    using C = typename V2<R>::C;
+    const C* psi = static_cast<const C*>(psi_);
+    const R* diag = static_cast<const R*>(diag_);
+    __shared__ double s_red[32 * 2];
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const WorkItem it = items[w];
+        const DevBlock B = blocks[it.block];
+        for (int v = 0; v < nvec; ++v) {
+            double n2 = 0.0, eh = 0.0;  // ||x||^2 and <x|2H~ x>
+            for (int64_t u = threadIdx.x; u < it.count; u += blockDim.x) {
+                const int64_t sl = it.first + u;
+                const int r = (int)(sl / B.L);
+                const int c = (int)(sl - (int64_t)r * B.L);
+                const int64_t gs = B.offset + sl;
+                const C x = psi[gs * nvec + v];
+                const int vr = ((r + c) & 1) ? r - 1 : r + 1;
+                double sx = 0.0, sy = 0.0;
+                if (c > 0) { const C y = psi[(gs - 1) * nvec + v]; sx += y.x; sy += y.y; }
+                if (c + 1 < B.L) { const C y = psi[(gs + 1) * nvec + v]; sx += y.x; sy += y.y; }
+                if (vr >= 0 && vr < B.W) {
+                    const C y = psi[(gs + (int64_t)(vr - r) * B.L) * nvec + v];
+                    sx += y.x;
+                    sy += y.y;
+                }
+                const double d = (double)(diag_per_vec ? diag[gs * nvec + v] : diag[gs]);
+                const double hx = d * x.x + B.beta * sx, hy = d * x.y + B.beta * sy;
+                n2 += (double)x.x * x.x + (double)x.y * x.y;
+                eh += (double)x.x * hx + (double)x.y * hy;
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+                eh += __shfl_xor_sync(0xffffffffu, eh, off);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                s_red[(threadIdx.x >> 5) * 2 + 0] = n2;
+                s_red[(threadIdx.x >> 5) * 2 + 1] = eh;
+            }
+            __syncthreads();
+            if (threadIdx.x < 2) {
+                double t = 0.0;
+                for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s_red[q * 2 + threadIdx.x];
+                partials[((size_t)w * nvec + v) * 2 + threadIdx.x] = t;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// per (block, vec): one warp sums the block's item partials (lane-strided, fixed xor tree)
+__global__ void k_rec_obs_finalize(const double* partials, const int32_t* block_item_begin,
+                                   const DevBlock* blocks, int nblocks, int nvec, double* out)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int slot = warp; slot < nblocks * nvec; slot += nwarps) {
+        const int q = slot / nvec, v = slot % nvec;
+        double n2 = 0.0, eh = 0.0;
+        for (int it = block_item_begin[q] + lane; it < block_item_begin[q + 1]; it += 32) {
+            n2 += partials[((size_t)it * nvec + v) * 2 + 0];
+            eh += partials[((size_t)it * nvec + v) * 2 + 1];
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+            eh += __shfl_xor_sync(0xffffffffu, eh, off);
+        }
+        if (lane == 0) {
+            const DevBlock B = blocks[q];
+            out[(size_t)slot * 2 + 0] = n2;
+            out[(size_t)slot * 2 + 1] = 0.5 * B.a * eh + B.b * n2;  // <H> = (a/2) <2H~> + b n2
+        }
+    }
+}
+
+// out[v * 2 + 0] = n2[v], out[v * 2 + 1] = e[v]
+__global__ void k_rec_obs_interleave(const double* n2, const double* e, int nvec, double* out)
+{
+    const int v = threadIdx.x;
+    if (v < nvec) {
+        out[v * 2 + 0] = n2[v];
+        out[v * 2 + 1] = e[v];
+    }
+}
+
 int launch_holstein_observable(Plan* p, const void* psi, int kind, double* out, cudaStream_t s);
 int launch_holstein_energy(Plan* p, const void* psi, double* out, cudaStream_t s);
+
+int record_prepare(Plan* p)
+{
+    const size_t need = std::max(p->hitems.size() * (size_t)p->nvec * 2, (size_t)p->nvec * 2);
+    if (p->rec_scratch_cap < need) {
+        if (p->d_rec_scratch) cudaFree(p->d_rec_scratch);
+        p->d_rec_scratch = nullptr;
+        p->rec_scratch_cap = 0;
+        CHEB_CUDA(cudaMalloc(&p->d_rec_scratch, need * sizeof(double)));
+        p->rec_scratch_cap = need;
+    }
+    return p->desc.kind == CHEB_HOLSTEIN ? obs_prepare(p) : CHEB_OK;
+}
+
+int launch_record(Plan* p, const void* psi, double* out, cudaStream_t s)
+{
+    int rc = record_prepare(p);
+    if (rc) return rc;
+    if (p->desc.kind == CHEB_HOLSTEIN) {  // one block: the two FP64 observables, interleaved
+        double* n2 = p->d_rec_scratch;
+        double* e = p->d_rec_scratch + p->nvec;
+        rc = launch_observable(p, psi, CHEB_OBS_NORM2, 0.0, n2, s);
+        if (!rc) rc = launch_observable(p, psi, CHEB_OBS_ENERGY, 0.0, e, s);
+        if (rc) return rc;
+        k_rec_obs_interleave<<<1, 32, 0, s>>>(n2, e, p->nvec, out);
+        p->launches++;
+        CHEB_CUDA(cudaGetLastError());
+        return CHEB_OK;
+    }
+    const int nitems = (int)p->hitems.size();
+    const int grid = std::min(nitems, 65535);
+    if (p->prec == CHEB_C128)
+        k_rec_obs_stencil<double><<<grid, 256, 0, s>>>(p->d_items, nitems, p->d_blocks, psi,
+                                                       p->d_diag, p->desc.onsite_per_vec, p->nvec,
+                                                       p->d_rec_scratch);
+    else
+        k_rec_obs_stencil<float><<<grid, 256, 0, s>>>(p->d_items, nitems, p->d_blocks, psi,
+                                                      p->d_diag, p->desc.onsite_per_vec, p->nvec,
+                                                      p->d_rec_scratch);
+    const int slots = p->nblocks * p->nvec;
+    k_rec_obs_finalize<<<std::min((slots + 7) / 8, 1024), 256, 0, s>>>(
+        p->d_rec_scratch, p->d_block_item_begin, p->d_blocks, p->nblocks, p->nvec, out);
+    p->launches += 2;
+    CHEB_CUDA(cudaGetLastError());
+    return CHEB_OK;
+}
+
 
 // allocate the stencil observables' partials ahead of a stream capture
 int obs_prepare(Plan* p)

@@ -1,7 +1,6 @@
 // Plan-free region norm that allocates no device memory.
 //
-// Some callers may not allocate device memory at the point where they need a norm: code that
-// runs while a stream is being captured in global mode (cudaMalloc is not allowed then),
+// Some callers may not allocate device memory at the point where they need a norm:
 // latency-critical loops that cannot afford the device-wide synchronisation of cudaMalloc and
 // cudaFree, and host programs that own all device memory through their own pool and forbid
 // libraries from allocating behind their back.  cheb_region_norm_noalloc serves them: it is

@@ -50,6 +50,23 @@ __host__ __device__ constexpr int tb_min_blocks(int nv, int spt, int tpb)
     return b < 1 ? 1 : (int)b;
 }
 
+// The last halo shrink (order index within the launch) at which region position (rr, cc) of an
+// RH x RW region is still formed: its bond distance to the region's open sides less one.  A
+// site d rows from an open row side is 2d - 1 bonds from it when its vertical bond points that
+// way, else 2d (the vertical bonds alternate), so rows stay valid about twice as long as
+// columns.  1 << 20 where no side is open.  Used by the kernels and by the host work model.
+__host__ __device__ __forceinline__ int tb_limit(int rr, int cc, int RH, int RW, bool up,
+                                                 bool open_t, bool open_b, bool open_l,
+                                                 bool open_r)
+{
+    int dl = 1 << 20;
+    if (open_t) dl = min(dl, 2 * rr + (up ? 0 : 1));
+    if (open_b) dl = min(dl, 2 * (RH - 1 - rr) + (up ? 1 : 0));
+    if (open_l) dl = min(dl, cc);
+    if (open_r) dl = min(dl, RW - 1 - cc);
+    return dl;
+}
+
 // Shared-memory planes: one float2 plane for a single vector, else one float4 plane per pair
 // of vectors (vectors 2p and 2p + 1 of a site side by side), so that region loads, neighbour
 // reads and stores move 16 bytes at a time.
@@ -201,16 +218,9 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                 nbl[j] = c > 0 ? idx - 1 : RMAX;
                 nbr[j] = c + 1 < B.L ? idx + 1 : RMAX;
                 nbv[j] = up ? (r > 0 ? idx - RW : RMAX) : (r + 1 < B.W ? idx + RW : RMAX);
-                // bond distance to the open sides, less one: a site d rows from an open row
-                // side is 2d - 1 bonds from it when its vertical bond points that way, else 2d
-                // (the vertical bonds alternate), so rows stay valid about twice as long as
-                // columns; sites never computed (dl = 0) never read their neighbours
-                int dl = 1 << 20;
-                if (open_t) dl = min(dl, 2 * rr + (up ? 0 : 1));
-                if (open_b) dl = min(dl, 2 * (RH - 1 - rr) + (up ? 1 : 0));
-                if (open_l) dl = min(dl, cc);
-                if (open_r) dl = min(dl, RW - 1 - cc);
-                dlim[j] = idx < nreg ? dl : -1;
+                // sites never computed (limit 0) never read their neighbours
+                dlim[j] = idx < nreg ? tb_limit(rr, cc, RH, RW, up, open_t, open_b, open_l, open_r)
+                                     : -1;
                 inter[j] = idx < nreg && (r >= T.r0) && (r < T.r1) && (c >= T.c0) && (c < T.c1);
             }
             // ---- load the region: asynchronous copies straight into shared memory ---------
@@ -573,6 +583,51 @@ bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vecto
     }
     begin[p->nblocks] = (int32_t)tiles.size();
     return true;
+}
+
+// Host work model of one blocked launch (cheb_plan_step_model): the tiles of set `tiles`
+// forming orders ka..kb, counted the way k_rec_tb runs them.
+void tb_model_launch(const Plan* p, const std::vector<TBTile>& tiles, int ka, int kb,
+                     int prev_ka, TBModel& m)
+{
+    const int nv = p->nvec;
+    const double pt = nv >= 2 ? 16.0 : 8.0;  // bytes of one plane element
+    const double np = nv >= 2 ? nv / 2 : 1;   // planes
+    const int rmax = p->tb_tpb * p->tb_spt;
+    const bool first = ka == 1;
+    for (const TBTile& T : tiles) {
+        const DevBlock& B = p->hblocks[T.block];
+        if (ka > B.M) continue;
+        const int ke = std::min(kb, (int)B.M), ns = ke - ka + 1;
+        const bool done = ke == B.M;
+        const int RW = T.C1 - T.C0, RH = T.R1 - T.R0;
+        const double nreg = (double)RW * RH;
+        const double inter = (double)(T.r1 - T.r0) * (T.c1 - T.c0);
+        const bool ot = T.R0 > 0, ob = T.R1 < B.W, ol = T.C0 > 0, orr = T.C1 < B.L;
+        double computed = 0.0;
+        for (int rr = 0; rr < RH; ++rr)
+            for (int cc = 0; cc < RW; ++cc) {
+                const bool up = ((T.R0 + rr) + (T.C0 + cc)) & 1;
+                computed += std::min(ns, tb_limit(rr, cc, RH, RW, up, ot, ob, ol, orr));
+            }
+        m.useful += inter * ns;
+        m.computed += computed;
+        // per formed site-order and plane: own site, three neighbours and T_{k-2} read, T_k
+        // written; region copies (two planes and d in; the first launch zeroes T_{-1}); the
+        // on-site values read once per thread slot; q_0 T_0 (first launch); the interior read
+        // back for the write-out (both vectors, or T_M only at the ribbon's last order)
+        m.smem += computed * np * 6.0 * pt + nreg * (2.0 * np * pt + 4.0) + (double)rmax * 4.0 +
+                  (first ? inter * np * pt : 0.0) + inter * np * pt * (done ? 1.0 : 2.0);
+        // between L2 and the SM: the region's inputs, the interior's accumulator in and
+        // outputs (the algorithmic DRAM count takes the inputs once per interior site)
+        const double vin = first ? 1.0 : 2.0;
+        const bool to_main = first || ka <= B.ksplit;
+        const bool read_e = !first && (to_main || done);
+        const bool read_t = !first && !to_main && prev_ka > B.ksplit;
+        const double acc_in = (read_e ? 1.0 : 0.0) + (read_t ? 1.0 : 0.0);
+        const double outs = done ? 1.0 : 3.0;  // psi, or T_{ke-1}, T_ke and the accumulator
+        m.l2 += nreg * (vin * np * pt + 4.0) + inter * np * pt * (acc_in + outs);
+    }
 }
 
 }  // namespace cheb

@@ -158,3 +158,16 @@ def test_tiles_rejected_when_one_column_does_not_fit():
     assert e.value.status == cb.CHEB_ERR_INVALID
     with pytest.raises(cb.ChebError):
         cb.cheb_tb_tiles(0, 10, 4, 1024)
+
+
+def test_tiles_span_row_bands_and_column_tiles():
+    """At the shapes the ensemble benchmark times (8 or 10 orders; 6 x 512 or 3 x 1024 sites
+    per region) the large ribbons of the GPU parity test are cut into >= 2 row bands and >= 2 column
+    tiles (host-side tile builder of the library)."""
+    import paper_0907_3022_gb300 as cb
+
+    for s, spt, tpb in ((8, 6, 512), (10, 6, 512), (8, 3, 1024), (10, 3, 1024)):
+        for W, L in ((158, 3177), (154, 3426), (131, 1999)):
+            t = cb.cheb_tb_tiles(W, L, s, spt * tpb)
+            assert len(set(t[:, 4].tolist())) >= 2, (s, spt, tpb, W, L)
+            assert len(set(t[:, 6].tolist())) >= 2, (s, spt, tpb, W, L)

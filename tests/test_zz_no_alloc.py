@@ -1,8 +1,8 @@
 """The allocation-free region norm (cheb_region_norm_noalloc) against cheb_observables.
 
-cheb_region_norm_noalloc is for callers that may not allocate device memory (a stream
-captured in global mode, latency-critical loops, hosts whose own pool owns all device
-memory).  Its tile partials live in a static device array shared by every call, so the test
+cheb_region_norm_noalloc is for callers that may not allocate device memory (latency-critical
+loops that cannot take cudaMalloc's device-wide synchronisation, hosts whose own pool owns all
+device memory).  Its tile partials live in a static device array shared by every call, so the test
 calls it twice in a row on different inputs and checks both results against the plan-based
 entry point, which reduces the same quantity with plan-owned scratch.  This file is named to
 be collected last.

@@ -212,6 +212,14 @@ def ribbon_packet(W: int, L: int, sigma: float, k0: float, r0: int, c0: int) -> 
     return psi / np.linalg.norm(psi)
 
 
+def random_state(n_sites: int, seed: int, stream: int = 0) -> np.ndarray:
+    """psi_j = (u - 1/2) + i (u' - 1/2) from 2 n_sites consecutive draws (u of site j at 2j,
+    u' at 2j + 1), unit norm: every site occupied, every energy of the band present."""
+    u = uniform01(seed, stream, 2 * n_sites)
+    psi = (u[0::2] - 0.5) + 1j * (u[1::2] - 0.5)
+    return psi / np.linalg.norm(psi)
+
+
 ENSEMBLE_K0 = (math.pi / 6, math.pi / 4, math.pi / 3, math.pi / 2)
 ENSEMBLE_DISORDER = (0.5, 1.0, 2.0)
 
