@@ -85,9 +85,10 @@ def parse():
                     help="L:NPH -- Holstein chain size for --workload holstein (profiling runs; "
                          "default 12:10)")
     ap.add_argument("--blocking", default=None,
-                    help="S:SPT[:THREADS] -- force S orders per launch with SPT sites per thread "
-                         "(THREADS per CTA, default 256) and skip the autotuner (profiling "
-                         "runs); 0:0 forces single-order launches")
+                    help="S:SPT[:THREADS[:runs]] -- force S orders per launch with SPT sites per "
+                         "thread (THREADS per CTA, default 256; 'runs': the register-run kernel) "
+                         "and skip the autotuner (profiling runs); 0:0 forces single-order "
+                         "launches")
     return ap.parse_args()
 
 
@@ -308,7 +309,10 @@ def blocked_roofline(cb, plan, kms, kcount, steps, alg_per_unit, unit_definition
         achieved = smem_pl / sec / 1e9
         r = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
              "frac": achieved / smem_peak, "traffic": dram_pl,
-             "kernel": "k_rec_tb<%d,%d,%d> (all launches of the step)" % (plan.nvec, blk[1], blk[2]),
+             "kernel": ("k_rec_tbr<%s,%d,%d> (all launches of the step)"
+                        % ("float4" if plan.nvec >= 2 else "float2", blk[1], blk[2])
+                        if plan.blocking_kernel() == cb.CHEB_TB_RUNS else
+                        "k_rec_tb<%d,%d,%d> (all launches of the step)" % (plan.nvec, blk[1], blk[2])),
              "peak_kind": "shared-memory load bandwidth measured in this run by the library's "
                           "probe (cheb_measure_peak; MEASURED_PEAKS.json has no shared-memory "
                           "figure)",
@@ -346,10 +350,12 @@ def run_ours(args, world, rank, local):
     if args.blocking is None:
         plan.autotune()
     else:
-        parts = [int(x) for x in args.blocking.split(":")]
+        f = args.blocking.split(":")
+        kern = cb.CHEB_TB_RUNS if len(f) > 3 and f[3] == "runs" else cb.CHEB_TB_SITES
+        parts = [int(x) for x in f[:3]]
         bs, bspt = parts[0], parts[1]
         btpb = parts[2] if len(parts) > 2 else 256
-        plan.set_blocking(bs, bspt if bs else 4, btpb if bs else 256)
+        plan.set_blocking_kernel(bs, bspt if bs else 4, btpb if bs else 256, kern)
     Ms = [plan.block(q)["M"] for q in range(ens.n_ribbons)]
     sites = [w * l for w, l in ens.sizes]
     mv_per_step = ens.nvec * sum(Ms)
@@ -501,7 +507,9 @@ def run_ours(args, world, rank, local):
             "launch_shape": dict(zip(("threads", "sites_per_thread", "grid", "vecs_per_thread"),
                                      plan.launch_shape())),
             "temporal_blocking": dict(zip(("orders_per_launch", "sites_per_thread", "threads"),
-                                          plan.blocking_shape())),
+                                          plan.blocking_shape()),
+                                      kernel=("runs" if plan.blocking_kernel() == cb.CHEB_TB_RUNS
+                                              else "sites")),
             "parallelism": f"replicas x{world} (one ensemble per GPU)",
         },
         "site_vector_steps_per_s": site_steps,

@@ -298,6 +298,24 @@ int cheb_autotune(cheb_plan* plan);
    for a shape that is not compiled.  cheb_autotune also chooses these. */
 int cheb_plan_set_blocking(cheb_plan* plan, int orders_per_launch, int sites_per_thread,
                            int threads);
+/* The blocked kernel, chosen with the shape:
+     CHEB_TB_SITES  the kernel of cheb_plan_set_blocking: a thread's sites are `threads` apart
+                    in the region, all recurrence vectors of the region in shared memory;
+     CHEB_TB_RUNS   each thread owns a run of sites_per_thread consecutive sites (odd) whose
+                    T_{k-1} and T_{k-2} stay in its registers; an order reads only the vertical
+                    neighbours and the run-end neighbours from shared memory and stores T_k
+                    once.  Region rows are padded to a multiple of 4 (pairs of vectors) or 8
+                    (one vector) positions with at least one zero pad.  A CTA holds one pair of
+                    vectors (nvec 2 and 4: the two pairs of a tile go to two CTAs) or one vector
+                    (nvec 1).  Compiled (run x threads): pairs 3 x 1024, 3 x 768, 3 x 512,
+                    5 x 512, 5 x 640, 7 x 384; single vectors 5 x 1024, 5 x 512, 7 x 512.
+   cheb_plan_set_blocking_kernel(plan, s, spt, threads, CHEB_TB_SITES) equals
+   cheb_plan_set_blocking; errors as there.  cheb_plan_blocking_kernel reports the kernel of
+   the blocking in use (CHEB_TB_SITES when blocking is off). */
+typedef enum { CHEB_TB_SITES = 0, CHEB_TB_RUNS = 1 } cheb_tb_kernel;
+int cheb_plan_set_blocking_kernel(cheb_plan* plan, int orders_per_launch, int sites_per_thread,
+                                  int threads, int kernel);
+int cheb_plan_blocking_kernel(const cheb_plan* plan, int* kernel);
 
 /* Whole steps on a thread-block cluster (1D grid plans, CHEB_LAT1D with nvec 1, a shared
    potential and at most 32768 points): ctas = 8 or 16 runs all M orders of a step in one
@@ -334,6 +352,11 @@ int cheb_plan_blocking(const cheb_plan* plan, int* orders_per_launch, int* sites
    interior column would not fit. */
 int cheb_tb_tiles(int W, int L, int orders_per_launch, int region_sites, int32_t* out,
                   int64_t capacity, int64_t* ntiles);
+/* The same for the register-run kernel's padded regions: region_positions = threads x run,
+   and a tile must satisfy 1 + (R1 - R0) x S <= region_positions, S the row stride (the
+   smallest multiple of align >= C1 - C0 + 1; align = 4 for pairs of vectors, 8 for one). */
+int cheb_tb_tiles_padded(int W, int L, int orders_per_launch, int region_positions, int align,
+                         int32_t* out, int64_t capacity, int64_t* ntiles);
 /* Copies of the plan's device data to host memory, for checking the construction:
    the SELL matrix of a Holstein plan as CSR in original row order (rowptr [n+1] int64,
    col [nnz] int64, val [nnz] double with the unscaled H entries); nnz_out gets the count.

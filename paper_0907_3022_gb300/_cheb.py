@@ -111,6 +111,10 @@ _SIGS = {
                                         _i64p], _c.c_int),
     "cheb_tb_tiles": ([_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_int32),
                        _c.c_int64, _i64p], _c.c_int),
+    "cheb_tb_tiles_padded": ([_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int,
+                              _c.POINTER(_c.c_int32), _c.c_int64, _i64p], _c.c_int),
+    "cheb_plan_set_blocking_kernel": ([_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int], _c.c_int),
+    "cheb_plan_blocking_kernel": ([_vp, _ip], _c.c_int),
     "cheb_autotune": ([_vp], _c.c_int),
     "cheb_plan_launch": ([_vp, _ip, _ip, _ip, _ip], _c.c_int),
     "cheb_plan_set_blocking": ([_vp, _c.c_int, _c.c_int, _c.c_int], _c.c_int),
@@ -232,6 +236,24 @@ def cheb_tb_tiles(W: int, L: int, orders_per_launch: int, region_sites: int):
                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n.value,
                               ctypes.byref(n)), "cheb_tb_tiles")
     return out
+
+
+def cheb_tb_tiles_padded(W: int, L: int, orders_per_launch: int, region_positions: int, align: int):
+    """As cheb_tb_tiles for the register-run kernel's padded regions (row stride a multiple of
+    align with at least one pad, one leading zero position)."""
+    import numpy as np
+
+    n = ctypes.c_int64()
+    check(lib().cheb_tb_tiles_padded(W, L, orders_per_launch, region_positions, align, None, 0,
+                                     ctypes.byref(n)), "cheb_tb_tiles_padded")
+    out = np.zeros((n.value, 8), dtype=np.int32)
+    check(lib().cheb_tb_tiles_padded(W, L, orders_per_launch, region_positions, align,
+                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n.value,
+                                     ctypes.byref(n)), "cheb_tb_tiles_padded")
+    return out
+
+
+CHEB_TB_SITES, CHEB_TB_RUNS = 0, 1
 
 
 # ---- plans ---------------------------------------------------------------------------------
@@ -372,6 +394,18 @@ class Plan:
     def set_blocking(self, orders_per_launch: int, sites_per_thread: int = 4, threads: int = 256):
         check(lib().cheb_plan_set_blocking(self.handle, orders_per_launch, sites_per_thread,
                                            threads), "cheb_plan_set_blocking")
+
+    def set_blocking_kernel(self, orders_per_launch: int, sites_per_thread: int, threads: int,
+                            kernel: int):
+        check(lib().cheb_plan_set_blocking_kernel(self.handle, orders_per_launch, sites_per_thread,
+                                                  threads, kernel), "cheb_plan_set_blocking_kernel")
+
+    def blocking_kernel(self) -> int:
+        """CHEB_TB_SITES or CHEB_TB_RUNS (CHEB_TB_SITES when blocking is off)."""
+        v = ctypes.c_int()
+        check(lib().cheb_plan_blocking_kernel(self.handle, ctypes.byref(v)),
+              "cheb_plan_blocking_kernel")
+        return v.value
 
     def set_cluster(self, ctas: int = 8):
         """Whole steps on a cluster of `ctas` CTAs (8 or 16; 0 or False: off)."""

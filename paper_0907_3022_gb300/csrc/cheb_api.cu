@@ -280,7 +280,8 @@ static int tb_prepare(Plan* p)
         minM = std::min(minM, (int)B.M);
         maxM = std::max(maxM, (int)B.M);
     }
-    int rc0 = tb_configure(p->nvec, p->tb_spt, p->tb_tpb);
+    int rc0 = p->tb_kernel == CHEB_TB_RUNS ? tbr_configure(p->nvec, p->tb_spt, p->tb_tpb)
+                                           : tb_configure(p->nvec, p->tb_spt, p->tb_tpb);
     if (rc0) {
         p->tb_s = 0;
         return rc0;
@@ -421,6 +422,7 @@ static int enqueue_step_tb(Plan* p, void* psi, cudaStream_t st)
         a.kb = L.kb;
         a.prev_ka = L.prev_ka;
         a.blocks = p->d_blocks;
+        a.nvec = p->nvec;
         a.diag = p->d_diag;
         if (i == 0) {
             a.in_prev = nullptr;
@@ -452,7 +454,7 @@ static int enqueue_step_tb(Plan* p, void* psi, cudaStream_t st)
             }
             CHEB_CUDA(cudaEventRecord(p->ev_pool[p->ev_used], st));
         }
-        int rc = tb_launch(p, a, st);
+        int rc = p->tb_kernel == CHEB_TB_RUNS ? tbr_launch(p, a, st) : tb_launch(p, a, st);
         if (rc) return rc;
         if (p->timing) {
             CHEB_CUDA(cudaEventRecord(p->ev_pool[p->ev_used + 1], st));
@@ -1209,17 +1211,28 @@ extern "C" int cheb_autotune(cheb_plan* plan)
         p->shape_epoch++;
         float best_ms = 0.0f;
         rc = time_steps(&best_ms);
-        int best_s = 0, best_spt = p->tb_spt, best_tpb = p->tb_tpb;
-        const int shapes[][2] = {{4, 256}, {6, 256}, {8, 256}, {3, 512}, {4, 512}, {6, 512},
-                                 {2, 1024}, {3, 1024}, {6, 1024}, {8, 1024}};
+        int best_s = 0, best_spt = p->tb_spt, best_tpb = p->tb_tpb, best_kernel = p->tb_kernel;
+        // (kernel, sites per thread, threads)
+        const int shapes[][3] = {{CHEB_TB_SITES, 4, 256}, {CHEB_TB_SITES, 6, 256},
+                                 {CHEB_TB_SITES, 8, 256}, {CHEB_TB_SITES, 3, 512},
+                                 {CHEB_TB_SITES, 4, 512}, {CHEB_TB_SITES, 6, 512},
+                                 {CHEB_TB_SITES, 2, 1024}, {CHEB_TB_SITES, 3, 1024},
+                                 {CHEB_TB_SITES, 6, 1024}, {CHEB_TB_SITES, 8, 1024},
+                                 {CHEB_TB_RUNS, 3, 1024}, {CHEB_TB_RUNS, 3, 768},
+                                 {CHEB_TB_RUNS, 3, 512}, {CHEB_TB_RUNS, 5, 512},
+                                 {CHEB_TB_RUNS, 5, 640}, {CHEB_TB_RUNS, 7, 384},
+                                 {CHEB_TB_RUNS, 5, 1024}, {CHEB_TB_RUNS, 7, 512}};
         for (const auto& sh : shapes) {
             if (rc) break;
-            const int spt = sh[0], tpb = sh[1];
-            if (!tb_supported(p->nvec, spt, tpb)) continue;
+            const int kern = sh[0], spt = sh[1], tpb = sh[2];
+            if (kern == CHEB_TB_RUNS ? !tbr_supported(p->nvec, spt, tpb)
+                                     : !tb_supported(p->nvec, spt, tpb))
+                continue;
             for (int s_try : {2, 3, 4, 5, 6, 7, 8, 10, 12}) {
                 p->tb_s = s_try;
                 p->tb_spt = spt;
                 p->tb_tpb = tpb;
+                p->tb_kernel = kern;
                 for (TBSet& t : p->tb_sets) {  // tiles depend on the region budget (spt)
                     cudaFree(t.d_tiles);
                     cudaFree(t.d_begin);
@@ -1236,6 +1249,7 @@ extern "C" int cheb_autotune(cheb_plan* plan)
                     best_s = s_try;
                     best_spt = spt;
                     best_tpb = tpb;
+                    best_kernel = kern;
                 }
             }
         }
@@ -1247,6 +1261,7 @@ extern "C" int cheb_autotune(cheb_plan* plan)
         p->tb_s = best_s;
         p->tb_spt = best_spt;
         p->tb_tpb = best_tpb;
+        p->tb_kernel = best_kernel;
         int rc3 = tb_prepare(p);
         if (!rc) rc = rc3;
         CHEB_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream));
@@ -1315,7 +1330,8 @@ extern "C" int cheb_plan_step_model(const cheb_plan* plan, cheb_step_model* out)
             std::vector<int32_t> begin;
             if (!tb_build_tiles(p, p->tb_sets[L.set].s, tiles, begin))
                 return fail(CHEB_ERR_STATE, "cheb_plan_step_model: tiles");
-            tb_model_launch(p, tiles, L.ka, L.kb, L.prev_ka, m);
+            if (p->tb_kernel == CHEB_TB_RUNS) tbr_model_launch(p, tiles, L.ka, L.kb, L.prev_ka, m);
+            else tb_model_launch(p, tiles, L.ka, L.kb, L.prev_ka, m);
             dram += tb_launch_bytes(p, L);
         }
         out->computed_site_orders = m.computed;
@@ -1343,6 +1359,26 @@ extern "C" int cheb_tb_tiles(int W, int L, int orders_per_launch, int region_sit
     std::vector<TBTile> tiles;
     if (!tb_tiles_of_ribbon(W, L, orders_per_launch, region_sites, 0, tiles))
         return fail(CHEB_ERR_INVALID, "cheb_tb_tiles: the ribbon does not fit the region budget");
+    *ntiles = (int64_t)tiles.size();
+    for (size_t i = 0; i < tiles.size() && (int64_t)i < capacity; ++i) {
+        const TBTile& t = tiles[i];
+        const int32_t v[8] = {t.R0, t.R1, t.C0, t.C1, t.r0, t.r1, t.c0, t.c1};
+        std::memcpy(out + 8 * i, v, sizeof(v));
+    }
+    return CHEB_OK;
+}
+
+extern "C" int cheb_tb_tiles_padded(int W, int L, int orders_per_launch, int region_positions,
+                                    int align, int32_t* out, int64_t capacity, int64_t* ntiles)
+{
+    if (!ntiles) return fail(CHEB_ERR_INVALID, "cheb_tb_tiles_padded: NULL count");
+    if (W < 1 || L < 1 || orders_per_launch < 1 || region_positions < 2 || (align != 4 && align != 8))
+        return fail(CHEB_ERR_INVALID, "cheb_tb_tiles_padded: W, L, orders_per_launch >= 1, "
+                                      "region_positions >= 2, align 4 or 8");
+    if (capacity > 0 && !out) return fail(CHEB_ERR_INVALID, "cheb_tb_tiles_padded: NULL out");
+    std::vector<TBTile> tiles;
+    if (!tb_tiles_of_ribbon(W, L, orders_per_launch, region_positions, 0, tiles, align))
+        return fail(CHEB_ERR_INVALID, "cheb_tb_tiles_padded: the ribbon does not fit the region budget");
     *ntiles = (int64_t)tiles.size();
     for (size_t i = 0; i < tiles.size() && (int64_t)i < capacity; ++i) {
         const TBTile& t = tiles[i];
@@ -1427,14 +1463,32 @@ extern "C" int cheb_plan_kernel_stats(cheb_plan* plan, double* ms, int64_t* laun
 
 extern "C" int cheb_plan_set_blocking(cheb_plan* plan, int s, int spt, int threads)
 {
+    return cheb_plan_set_blocking_kernel(plan, s, spt, threads, CHEB_TB_SITES);
+}
+
+extern "C" int cheb_plan_blocking_kernel(const cheb_plan* plan, int* kernel)
+{
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    if (!p || !kernel) return fail(CHEB_ERR_INVALID, "cheb_plan_blocking_kernel: NULL argument");
+    *kernel = p->tb_sched.empty() ? CHEB_TB_SITES : p->tb_kernel;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_set_blocking_kernel(cheb_plan* plan, int s, int spt, int threads,
+                                             int kernel)
+{
     Plan* p = reinterpret_cast<Plan*>(plan);
     if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
     if (s < 0 || s > 16) return fail(CHEB_ERR_INVALID, "orders_per_launch must be in [0, 16]");
+    if (kernel != CHEB_TB_SITES && kernel != CHEB_TB_RUNS)
+        return fail(CHEB_ERR_INVALID, "blocked kernel must be CHEB_TB_SITES or CHEB_TB_RUNS");
     if (s > 0 && !tb_eligible(p))
         return fail(CHEB_ERR_UNSUPPORTED, "temporal blocking needs a complex64 lattice plan with "
                                           "nvec 1, 2 or 4 and a shared on-site array");
     if (threads == 0) threads = 256;
-    if (s > 0 && !tb_supported(p->nvec, spt, threads))
+    const bool ok = kernel == CHEB_TB_RUNS ? tbr_supported(p->nvec, spt, threads)
+                                           : tb_supported(p->nvec, spt, threads);
+    if (s > 0 && !ok)
         return fail(CHEB_ERR_INVALID, "temporal blocking: this (nvec, sites_per_thread, threads) "
                                       "shape is not compiled");
     for (TBSet& t : p->tb_sets) {
@@ -1446,6 +1500,7 @@ extern "C" int cheb_plan_set_blocking(cheb_plan* plan, int s, int spt, int threa
     if (s > 0) {
         p->tb_spt = spt;
         p->tb_tpb = threads;
+        p->tb_kernel = kernel;
     }
     p->tb_sched.clear();
     p->shape_epoch++;

@@ -126,6 +126,7 @@ struct TBArgs {
     int32_t ka, kb;          // orders formed by this launch
     int32_t prev_ka;         // first order of the previous launch of the step (0: none)
     const DevBlock* blocks;
+    int32_t nvec;            // vectors per site
     const void* diag;        // float d_i
     const void* in_prev;     // T_{ka-2} (unused when ka = 1)
     const void* in_cur;      // T_{ka-1} (psi when ka = 1)
@@ -161,13 +162,22 @@ int tb_configure(int nv, int spt, int tpb);
 bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vector<int32_t>& begin);
 // the tiles of one W x L ribbon for s orders per launch and rmax region sites per CTA
 // (appended to tiles); false if one interior column does not fit
-bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TBTile>& tiles);
+// align > 0: padded rows of the register-run kernel (stride a multiple of align, >= 1 pad)
+bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TBTile>& tiles,
+                        int align = 0);
 // host work model of one blocked launch over the given tiles (cheb_plan_step_model)
 struct TBModel {
     double useful = 0.0, computed = 0.0, smem = 0.0, l2 = 0.0;
 };
 void tb_model_launch(const Plan* p, const std::vector<TBTile>& tiles, int ka, int kb,
                      int prev_ka, TBModel& m);
+// temporal blocking with register-resident runs (cheb_tbr.cu)
+bool tbr_supported(int nv, int run, int tpb);
+size_t tbr_smem_bytes(int nv, int run, int tpb);
+int tbr_configure(int nv, int run, int tpb);
+int tbr_launch(Plan* p, const TBArgs& a, cudaStream_t s);
+void tbr_model_launch(const Plan* p, const std::vector<TBTile>& tiles, int ka, int kb,
+                      int prev_ka, TBModel& m);
 
 // kernel launchers (cheb_kernels.cu)
 int launch_recurrence(Plan* p, const RecArgs& a, int op, int prec, cudaStream_t s);
@@ -293,8 +303,9 @@ struct Plan {
     // temporal blocking (complex64 stencils): orders per launch (0: off), sites per thread
     int tb_s = 0;
     int cluster = 0;          // CTAs of the cluster running whole steps (small 1D grids); 0: off
-    int tb_spt = 4;
+    int tb_spt = 4;           // sites per thread (CHEB_TB_RUNS: the run length)
     int tb_tpb = 256;         // threads per CTA of the blocked kernel
+    int tb_kernel = CHEB_TB_SITES;  // blocked kernel: strided sites or register runs
     int tb_grid_cap = 0;
     void* d_C = nullptr;      // second recurrence pair and the main accumulator
     void* d_D = nullptr;

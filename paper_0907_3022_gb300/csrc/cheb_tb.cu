@@ -517,10 +517,20 @@ int tb_launch(Plan* p, const TBArgs& a, cudaStream_t s)
     return rc;
 }
 
+// Widest region row that fits rmax positions with rh rows: rmax / rh sites per row, or with
+// padded rows (align > 0; the register-run kernel) one leading zero position and a row stride
+// that is a multiple of align and leaves at least one zero pad after every row.
+static int tb_width_cap(int rmax, int rh, int align)
+{
+    if (align <= 0) return rmax / rh;
+    return (((rmax - 1) / rh) & ~(align - 1)) - 1;
+}
+
 // Tiles for a halo of s: row bands chosen for the least halo waste, then as many interior
-// columns as the region budget (threads * spt sites) allows.  Returns false if a ribbon cannot be
-// tiled (the region of one interior column would not fit).
-bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TBTile>& tiles)
+// columns as the region budget (rmax positions: threads * sites per thread) allows.  Returns
+// false if a ribbon cannot be tiled (the region of one interior column would not fit).
+bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TBTile>& tiles,
+                        int align)
 {
     // halo widths for s orders: s columns, but only ceil(s / 2) rows, since d rows away is at
     // least 2d - 1 bonds on the brick wall (the kernel's validity distance counts the same way)
@@ -531,7 +541,8 @@ bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TB
     for (int nbr = 1; nbr <= W; ++nbr) {
         const int tr = (W + nbr - 1) / nbr;
         const int rh = std::min(W, tr + (nbr > 1 ? 2 * hr : 0));  // worst band
-        const int tcmax = rmax / rh - (L > rmax / rh ? 2 * s : 0);
+        const int wcap = tb_width_cap(rmax, rh, align);
+        const int tcmax = wcap - (L > wcap ? 2 * s : 0);
         if (tcmax < 1) continue;
         const int tc = std::min(tcmax, L);
         const double eff = (double)tr * tc / ((double)rh * (tc + (L > tc ? 2 * s : 0)));
@@ -547,7 +558,7 @@ bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TB
         const int r1 = std::min(W, r0 + tr);
         const int R0 = std::max(0, r0 - hr), R1 = std::min(W, r1 + hr);
         const int rh = R1 - R0;
-        int tc = rmax / rh;
+        int tc = tb_width_cap(rmax, rh, align);
         if (tc < L) tc -= 2 * s;  // halo on both column sides
         if (tc < 1) return false;
         const int nbc = (L + tc - 1) / tc;
@@ -564,7 +575,9 @@ bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TB
             t.r1 = r1;
             t.c0 = c0;
             t.c1 = c1;
-            if ((int64_t)(t.R1 - t.R0) * (t.C1 - t.C0) > rmax) return false;
+            const int64_t RW = t.C1 - t.C0, RH = t.R1 - t.R0;
+            const int64_t used = align > 0 ? 1 + RH * ((RW + align) & ~(int64_t)(align - 1)) : RH * RW;
+            if (RW < 1 || used > rmax) return false;
             tiles.push_back(t);
         }
     }
@@ -574,12 +587,13 @@ bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TB
 bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vector<int32_t>& begin)
 {
     const int rmax = p->tb_tpb * p->tb_spt;
+    const int align = p->tb_kernel == CHEB_TB_RUNS ? (p->nvec >= 2 ? 4 : 8) : 0;
     tiles.clear();
     begin.assign(p->nblocks + 1, 0);
     for (int q = 0; q < p->nblocks; ++q) {
         begin[q] = (int32_t)tiles.size();
         const DevBlock& B = p->hblocks[q];
-        if (!tb_tiles_of_ribbon(B.W, B.L, s, rmax, q, tiles)) return false;
+        if (!tb_tiles_of_ribbon(B.W, B.L, s, rmax, q, tiles, align)) return false;
     }
     begin[p->nblocks] = (int32_t)tiles.size();
     return true;

@@ -1,0 +1,547 @@
+// Temporally blocked Chebyshev recurrence with register-resident runs (Sec. 2.2, Eqs. U_1 and
+// rec; brick-wall ribbons of Sec. 3.2, the 1D grid as W = 1), complex64.
+//
+// Same tiles, halos, validity rule and accumulator protocol as k_rec_tb (cheb_tb.cu): one
+// launch forms orders ka..kb for every ribbon, a CTA owns the region of one tile and keeps the
+// tile's interior valid for all orders.  What differs is how a CTA holds the region:
+//
+// * A CTA carries one plane element per site: a pair of vectors (float4, nvec 2 or 4; with 4
+//   the two pairs of a tile go to two CTAs) or a single vector (float2, nvec 1).
+// * Thread t owns the RUN consecutive positions t RUN .. t RUN + RUN - 1 of the region laid out
+//   row-major with a padded row stride.  T_{k-1} and T_{k-2} of its own sites stay in
+//   registers, so an order reads from shared memory only the vertical neighbour of each site
+//   and the two neighbours beyond the run's ends, and stores each site's T_k once (the
+//   neighbours of the next order read it).  Only T_{k-1} has a shared-memory plane (two planes,
+//   read one / write the other).
+// * Layout of a plane: position 0 is a zero element, site (rr, cc) of the RH x RW region is at
+//   1 + rr S + cc, S = the smallest multiple of A (4 for float4, 8 for float2) that is >= RW + 1,
+//   and the S - RW >= 1 positions after every row are zero pads; one more zero element follows
+//   the last position.  The pads make the neighbour left of column 0 and right of column RW - 1
+//   a zero read, which is the ribbon's open edge where the region ends at the ribbon border (where
+//   it ends at an open side the site is outside the validity limit and its value unused).  A
+//   vertical neighbour outside the region or the ribbon reads position 0.
+// * Bank conflicts: with RUN odd, the lanes of a quarter warp (float4) or half warp (float2)
+//   address distinct bank groups for the same j; with S a multiple of A, the up and down
+//   neighbours (+-S) of any two lanes still do.
+// * A run is formed at an order if any of its sites is still valid; pads are never formed and
+//   keep zero in registers and shared memory.
+//
+// Per formed site-order and plane element: one vertical load, 2 / RUN run-end loads, one store
+// (k_rec_tb: own, three neighbours, T_{k-2} and the store).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "cheb_internal.cuh"
+
+namespace cheb {
+
+template <typename PT> struct TBRPlane;
+template <> struct TBRPlane<float4> {
+    static constexpr int A = 4;    // row-stride alignment (elements)
+    static constexpr int PER = 2;  // vectors per element
+};
+template <> struct TBRPlane<float2> {
+    static constexpr int A = 8;
+    static constexpr int PER = 1;
+};
+
+__host__ __device__ constexpr size_t tbr_smem(int elem_bytes, int run, int tpb)
+{
+    return 2 * ((size_t)run * tpb + 1) * (size_t)elem_bytes;
+}
+
+// padded row stride for a region row of RW sites (align 4 or 8)
+__host__ __device__ __forceinline__ int tbr_stride(int RW, int align)
+{
+    return (RW + align) & ~(align - 1);
+}
+
+// same validity limit as k_rec_tb (cheb_tb.cu)
+__host__ __device__ __forceinline__ int tbr_limit(int rr, int cc, int RH, int RW, bool up,
+                                                  bool open_t, bool open_b, bool open_l,
+                                                  bool open_r)
+{
+    int dl = 1 << 20;
+    if (open_t) dl = min(dl, 2 * rr + (up ? 0 : 1));
+    if (open_b) dl = min(dl, 2 * (RH - 1 - rr) + (up ? 1 : 0));
+    if (open_l) dl = min(dl, cc);
+    if (open_r) dl = min(dl, RW - 1 - cc);
+    return dl;
+}
+
+__device__ __forceinline__ float4 tbr_zero(float4*) { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float2 tbr_zero(float2*) { return make_float2(0.f, 0.f); }
+
+// h = beta (l + r + v) - p + d x  (beta = bh + bl), halved for T_1 = H~ T_0
+__device__ __forceinline__ float2 tbr_h(float2 l, float2 r, float2 v, float2 p, float2 x, float d,
+                                        float bh, float bl, bool half)
+{
+    const float sx = (l.x + r.x) + v.x, sy = (l.y + r.y) + v.y;
+    float hx = fmaf(bl, sx, -p.x), hy = fmaf(bl, sy, -p.y);
+    hx = fmaf(bh, sx, hx);
+    hy = fmaf(bh, sy, hy);
+    hx = fmaf(d, x.x, hx);
+    hy = fmaf(d, x.y, hy);
+    if (half) {
+        hx *= 0.5f;
+        hy *= 0.5f;
+    }
+    return make_float2(hx, hy);
+}
+__device__ __forceinline__ float4 tbr_h(float4 l, float4 r, float4 v, float4 p, float4 x, float d,
+                                        float bh, float bl, bool half)
+{
+    const float2 a = tbr_h(make_float2(l.x, l.y), make_float2(r.x, r.y), make_float2(v.x, v.y),
+                           make_float2(p.x, p.y), make_float2(x.x, x.y), d, bh, bl, half);
+    const float2 b = tbr_h(make_float2(l.z, l.w), make_float2(r.z, r.w), make_float2(v.z, v.w),
+                           make_float2(p.z, p.w), make_float2(x.z, x.w), d, bh, bl, half);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+__device__ __forceinline__ float2 tbr_get(const float2& t, int) { return t; }
+__device__ __forceinline__ float2 tbr_get(const float4& t, int c)
+{
+    return c ? make_float2(t.z, t.w) : make_float2(t.x, t.y);
+}
+__device__ __forceinline__ void tbr_put(float2& t, int, float2 v) { t = v; }
+__device__ __forceinline__ void tbr_put(float4& t, int c, float2 v)
+{
+    if (c) {
+        t.z = v.x;
+        t.w = v.y;
+    } else {
+        t.x = v.x;
+        t.y = v.y;
+    }
+}
+
+// acc += (-i)^k q t with the sign of (-i)^k folded into q = (hi, lo)
+__device__ __forceinline__ void tbr_accum(float2& acc, const float2 q, const float2 t, const int k)
+{
+    if ((k & 1) == 0) {
+        acc.x = fmaf(q.y, t.x, acc.x);
+        acc.y = fmaf(q.y, t.y, acc.y);
+        acc.x = fmaf(q.x, t.x, acc.x);
+        acc.y = fmaf(q.x, t.y, acc.y);
+    } else {
+        acc.x = fmaf(q.y, t.y, acc.x);
+        acc.y = fmaf(-q.y, t.x, acc.y);
+        acc.x = fmaf(q.x, t.y, acc.x);
+        acc.y = fmaf(-q.x, t.x, acc.y);
+    }
+}
+
+__device__ __forceinline__ float2 tbr_phase(const float2 a, const float2 ph, const float2 pl)
+{
+    float rx = fmaf(pl.x, a.x, -pl.y * a.y);
+    float ry = fmaf(pl.x, a.y, pl.y * a.x);
+    rx = fmaf(ph.x, a.x, fmaf(-ph.y, a.y, rx));
+    ry = fmaf(ph.x, a.y, fmaf(ph.y, a.x, ry));
+    return make_float2(rx, ry);
+}
+
+// One order of the run: dst <- 2 H~ src - dst at every site (src = T_{k-1}, dst = T_{k-2} in,
+// T_k out), T_k stored to Pw, q_k T_k added to the interior accumulators.  Reads Qr (T_{k-1}).
+template <typename PT, int RUN, bool FIRST>
+__device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restrict__ Pw,
+                                          const PT (&src)[RUN], PT (&dst)[RUN],
+                                          const float (&d)[RUN], const int (&vidx)[RUN],
+                                          unsigned padm, unsigned interm, int e0, bool active,
+                                          float bh, float bl, float2 qk, int k,
+                                          float2 (&acc)[RUN][TBRPlane<PT>::PER],
+                                          float (&part)[FIRST ? 2 * TBRPlane<PT>::PER : 1])
+{
+    constexpr int PER = TBRPlane<PT>::PER;
+    if (active) {
+        PT V[RUN];
+#pragma unroll
+        for (int j = 0; j < RUN; ++j) V[j] = Qr[vidx[j]];
+        const PT Lf = Qr[e0 > 0 ? e0 - 1 : 0];
+        const PT Rt = Qr[e0 + RUN];
+        const bool half = FIRST && k == 1;
+#pragma unroll
+        for (int j = 0; j < RUN; ++j) {
+            if ((padm >> j) & 1u) continue;
+            const PT l = j > 0 ? src[j - 1] : Lf;
+            const PT r = j < RUN - 1 ? src[j + 1] : Rt;
+            const PT h = tbr_h(l, r, V[j], dst[j], src[j], d[j], bh, bl, half);
+            if ((interm >> j) & 1u) {
+#pragma unroll
+                for (int c = 0; c < PER; ++c) {
+                    const float2 hv = tbr_get(h, c);
+                    tbr_accum(acc[j][c], qk, hv, k);
+                    if constexpr (FIRST) {
+                        if (k == 1) {  // ||T_0||^2, <T_0|H~ T_0> (FP32: divergence check only)
+                            const float2 x = tbr_get(src[j], c);
+                            part[2 * c + 0] = fmaf(x.x, x.x, fmaf(x.y, x.y, part[2 * c + 0]));
+                            part[2 * c + 1] = fmaf(x.x, hv.x, fmaf(x.y, hv.y, part[2 * c + 1]));
+                        }
+                    }
+                }
+            }
+            dst[j] = h;
+            Pw[e0 + j] = h;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename PT, int RUN, int TPB, bool FIRST>
+__global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
+{
+    constexpr int PER = TBRPlane<PT>::PER;
+    constexpr int ALIGN = TBRPlane<PT>::A;
+    constexpr int NPOS = RUN * TPB;
+    constexpr int PS = NPOS + 1;  // plane size: positions and the trailing zero
+    extern __shared__ float4 tbr_smem_raw[];
+    PT* const plane0 = reinterpret_cast<PT*>(tbr_smem_raw);
+    PT* const plane1 = plane0 + PS;
+    __shared__ double s_red[(TPB / 32) * 2 * PER];
+    const PT zero = tbr_zero((PT*)nullptr);
+    const int tid = threadIdx.x;
+    const int e0 = tid * RUN;
+    const int npairs = a.nvec / PER;  // plane elements per site in global memory
+    const int nvec = a.nvec;
+
+    const PT* __restrict__ in_prev = static_cast<const PT*>(a.in_prev);
+    const PT* __restrict__ in_cur = static_cast<const PT*>(a.in_cur);
+    PT* __restrict__ out_prev = static_cast<PT*>(a.out_prev);
+    PT* __restrict__ out_cur = static_cast<PT*>(a.out_cur);
+    PT* __restrict__ accE = static_cast<PT*>(a.acc_main);
+    PT* __restrict__ tail = static_cast<PT*>(a.tail);
+    PT* __restrict__ psi = static_cast<PT*>(a.psi);
+    const float* __restrict__ diag = static_cast<const float*>(a.diag);
+    const float2* __restrict__ qc = static_cast<const float2*>(a.qcoef);
+    if (tid == 0) {
+        plane0[NPOS] = zero;
+        plane1[NPOS] = zero;
+    }
+
+    const int nwork = a.ntiles * npairs;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int ti = w / npairs, pr = w - ti * npairs;
+        const TBTile T = a.tiles[ti];
+        const DevBlock B = a.blocks[T.block];
+        float part[FIRST ? 2 * PER : 1];
+#pragma unroll
+        for (int q = 0; q < (FIRST ? 2 * PER : 1); ++q) part[q] = 0.f;
+        if (a.ka <= B.M) {
+            const int ke = min(a.kb, B.M);
+            const bool done = (ke == B.M);
+            const int RW = T.C1 - T.C0, RH = T.R1 - T.R0;
+            const int S = tbr_stride(RW, ALIGN);
+            // q / S as (q * ceil(2^32 / S)) >> 32: exact for q < NPOS <= 2^13
+            const unsigned long long invS = ((1ull << 32) + (unsigned)S - 1u) / (unsigned)S;
+            const bool open_t = T.R0 > 0, open_b = T.R1 < B.W, open_l = T.C0 > 0, open_r = T.C1 < B.L;
+            PT X[RUN], P[RUN];
+            float d[RUN];
+            int vidx[RUN];
+            unsigned padm = 0, interm = 0;
+            int rl = -1;  // last order index (1-based shrink) at which the run is formed
+#pragma unroll
+            for (int j = 0; j < RUN; ++j) {
+                const int e = e0 + j, q = e - 1;
+                const int rr = q >= 0 ? (int)(((unsigned long long)q * invS) >> 32) : -1;
+                const int cc = q - rr * S;
+                const bool site = q >= 0 && rr < RH && cc < RW;
+                X[j] = zero;
+                P[j] = zero;
+                d[j] = 0.f;
+                vidx[j] = 0;
+                if (site) {
+                    const int r = T.R0 + rr, c = T.C0 + cc;
+                    const bool up = (r + c) & 1;  // vertical neighbour r - 1 (else r + 1)
+                    rl = max(rl, tbr_limit(rr, cc, RH, RW, up, open_t, open_b, open_l, open_r));
+                    vidx[j] = up ? ((rr > 0 && r > 0) ? e - S : 0)
+                                 : ((rr + 1 < RH && r + 1 < B.W) ? e + S : 0);
+                    if (r >= T.r0 && r < T.r1 && c >= T.c0 && c < T.c1) interm |= 1u << j;
+                    const int64_t g = B.offset + (int64_t)r * B.L + c;
+                    X[j] = in_cur[g * npairs + pr];
+                    if (!FIRST) P[j] = in_prev[g * npairs + pr];
+                    d[j] = diag[g];
+                } else {
+                    padm |= 1u << j;
+                }
+            }
+            // the accumulator this launch continues: E (main), the tail, or E + tail at the
+            // ribbon's last order (same protocol as k_rec_tb)
+            const bool to_main = FIRST || (a.ka <= B.ksplit);
+            const bool tail_has = a.prev_ka > B.ksplit;
+            const bool read_e = !FIRST && (to_main || done);
+            const bool read_t = !FIRST && !to_main && tail_has;
+            float2 acc[RUN][PER];
+#pragma unroll
+            for (int j = 0; j < RUN; ++j) {
+                PT eP = zero, tP = zero;
+                if (((interm >> j) & 1u) && (read_e || read_t)) {
+                    const int q = e0 + j - 1;
+                    const int rr = (int)(((unsigned long long)q * invS) >> 32), cc = q - rr * S;
+                    const int64_t g = B.offset + (int64_t)(T.R0 + rr) * B.L + (T.C0 + cc);
+                    if (read_e) eP = accE[g * npairs + pr];
+                    if (read_t) tP = tail[g * npairs + pr];
+                }
+#pragma unroll
+                for (int c = 0; c < PER; ++c) {
+                    const float2 ev = tbr_get(eP, c), tv = tbr_get(tP, c);
+                    acc[j][c] = (read_e && read_t) ? make_float2(ev.x + tv.x, ev.y + tv.y)
+                                                   : (read_t ? tv : ev);
+                }
+            }
+            // T_{ka-1} of every position into plane 0; pads also zero plane 1
+#pragma unroll
+            for (int j = 0; j < RUN; ++j) {
+                plane0[e0 + j] = X[j];
+                if ((padm >> j) & 1u) plane1[e0 + j] = zero;
+            }
+            float bh, bl;
+            {
+                bh = (float)B.beta;
+                bl = (float)(B.beta - (double)bh);
+            }
+            if (FIRST) {  // q_0 T_0
+                const float2 q0 = qc[B.coef_off + 0];
+#pragma unroll
+                for (int j = 0; j < RUN; ++j)
+                    if ((interm >> j) & 1u)
+#pragma unroll
+                        for (int c = 0; c < PER; ++c) tbr_accum(acc[j][c], q0, tbr_get(X[j], c), 0);
+            }
+            __syncthreads();
+            // ---- the orders, two per iteration: P <- 2 H~ X - P, then X <- 2 H~ P - X ----
+            float2 qn = qc[B.coef_off + a.ka];
+            int k = a.ka;
+            for (;;) {
+                float2 qk = qn;
+                if (k < ke) qn = qc[B.coef_off + k + 1];
+                tbr_order<PT, RUN, FIRST>(plane0, plane1, X, P, d, vidx, padm, interm, e0,
+                                          rl >= k - a.ka + 1, bh, bl, qk, k, acc, part);
+                if (k == ke) break;
+                ++k;
+                qk = qn;
+                if (k < ke) qn = qc[B.coef_off + k + 1];
+                tbr_order<PT, RUN, FIRST>(plane1, plane0, P, X, d, vidx, padm, interm, e0,
+                                          rl >= k - a.ka + 1, bh, bl, qk, k, acc, part);
+                if (k == ke) break;
+                ++k;
+            }
+            // T_ke is in P when ke - ka is even (the last order ran the first half), else in X
+            const bool last_in_p = ((ke - a.ka) & 1) == 0;
+            float lim[PER];
+#pragma unroll
+            for (int c = 0; c < PER; ++c)
+                lim[c] = done ? (float)(4.0 * a.norm2[((size_t)T.block * nvec + pr * PER + c) * 2]) : 0.f;
+            float2 ph, pl;
+            ph.x = (float)B.ph_re;
+            pl.x = (float)(B.ph_re - (double)ph.x);
+            ph.y = (float)B.ph_im;
+            pl.y = (float)(B.ph_im - (double)ph.y);
+#pragma unroll
+            for (int j = 0; j < RUN; ++j) {
+                if (!((interm >> j) & 1u)) continue;
+                const int q = e0 + j - 1;
+                const int rr = (int)(((unsigned long long)q * invS) >> 32), cc = q - rr * S;
+                const int64_t g = (B.offset + (int64_t)(T.R0 + rr) * B.L + (T.C0 + cc)) * npairs + pr;
+                const PT tk = last_in_p ? P[j] : X[j];
+                const PT tk1 = last_in_p ? X[j] : P[j];
+                PT aP;
+#pragma unroll
+                for (int c = 0; c < PER; ++c) tbr_put(aP, c, acc[j][c]);
+                if (!done) {
+                    out_cur[g] = tk;
+                    out_prev[g] = tk1;
+                    if (to_main) accE[g] = aP;
+                    else tail[g] = aP;
+                } else {
+                    PT oP;
+#pragma unroll
+                    for (int c = 0; c < PER; ++c) {
+                        tbr_put(oP, c, tbr_phase(acc[j][c], ph, pl));  // E + tail + partial
+                        // growth check |T_M|^2 <= 4 ||psi||^2, in FP32 (a divergence test)
+                        const float2 t = tbr_get(tk, c);
+                        const float t2 = fmaf(t.x, t.x, t.y * t.y);
+                        if (!(t2 <= lim[c])) atomicOr(a.errflag, 1);
+                    }
+                    psi[g] = oP;
+                }
+            }
+        }
+        if constexpr (FIRST) {
+            // per (tile, vector) partials: FP32 warp tree, FP64 across the warps
+            const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+            for (int q = 0; q < 2 * PER; ++q) {
+                float xs = part[q];
+                for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
+                if (lane == 0) s_red[warp * 2 * PER + q] = (double)xs;
+            }
+            __syncthreads();
+            if (tid < 2 * PER) {
+                double t = 0.0;
+                for (int q = 0; q < TPB / 32; ++q) t += s_red[q * 2 * PER + tid];
+                // vector pr * PER + tid / 2, component tid % 2
+                a.partials[((size_t)ti * nvec + pr * PER) * 2 + tid] = t;
+            }
+            __syncthreads();
+        }
+    }
+    if constexpr (FIRST) {
+        __shared__ unsigned int s_last;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_last = (atomicAdd(a.done_counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            // one warp per (ribbon, vector) slot, lane-strided over the tiles, fixed xor tree
+            const int lane = tid & 31, warp = tid >> 5;
+            for (int slot = warp; slot < a.nblocks * nvec; slot += TPB / 32) {
+                const int q = slot / nvec, v = slot % nvec;
+                const int it1 = a.block_tile_begin[q + 1];
+                double n2 = 0.0, eh = 0.0;
+                for (int it = a.block_tile_begin[q] + lane; it < it1; it += 32) {
+                    n2 += __ldcg(a.partials + ((size_t)it * nvec + v) * 2 + 0);
+                    eh += __ldcg(a.partials + ((size_t)it * nvec + v) * 2 + 1);
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+                    eh += __shfl_xor_sync(0xffffffffu, eh, off);
+                }
+                if (lane == 0) {
+                    const DevBlock Bq = a.blocks[q];
+                    a.red_out[(size_t)slot * 2 + 0] = n2;
+                    a.red_out[(size_t)slot * 2 + 1] = Bq.a * eh + Bq.b * n2;
+                }
+            }
+            if (tid == 0) *a.done_counter = 0u;
+        }
+    }
+}
+
+// ---- dispatch ---------------------------------------------------------------------------
+// Compiled (vectors per plane element, run, threads): pairs of vectors (nvec 2 and 4) and single
+// vectors (nvec 1); one CTA per SM (up to 1024 threads) or two.
+#define CHEB_TBR_SHAPES(X)                                                             \
+    X(float4, 3, 1024) X(float4, 3, 768) X(float4, 5, 512) X(float4, 5, 640)            \
+    X(float4, 7, 384) X(float4, 3, 512) X(float2, 5, 1024) X(float2, 7, 512)           \
+    X(float2, 5, 512)
+
+static int tbr_elem_bytes(int nv) { return nv >= 2 ? 16 : 8; }
+
+bool tbr_supported(int nv, int run, int tpb)
+{
+    const int eb = tbr_elem_bytes(nv);
+#define CHEB_TBR_IS(PT, RUN, TPB) \
+    if ((int)sizeof(PT) == eb && run == RUN && tpb == TPB) return true;
+    CHEB_TBR_SHAPES(CHEB_TBR_IS)
+#undef CHEB_TBR_IS
+    return false;
+}
+
+size_t tbr_smem_bytes(int nv, int run, int tpb) { return tbr_smem(tbr_elem_bytes(nv), run, tpb); }
+
+template <typename PT, int RUN, int TPB>
+static int tbr_attr_t()
+{
+    const int smem = (int)tbr_smem(sizeof(PT), RUN, TPB);
+    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tbr<PT, RUN, TPB, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tbr<PT, RUN, TPB, false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return CHEB_OK;
+}
+
+int tbr_configure(int nv, int run, int tpb)
+{
+    const int eb = tbr_elem_bytes(nv);
+#define CHEB_TBR_ATTR(PT, RUN, TPB) \
+    if ((int)sizeof(PT) == eb && run == RUN && tpb == TPB) return tbr_attr_t<PT, RUN, TPB>();
+    CHEB_TBR_SHAPES(CHEB_TBR_ATTR)
+#undef CHEB_TBR_ATTR
+    return fail(CHEB_ERR_UNSUPPORTED, "run blocking: unsupported nvec / run / threads");
+}
+
+template <typename PT, int RUN, int TPB>
+static void tbr_launch_t(const TBArgs& a, int grid, cudaStream_t s)
+{
+    const size_t smem = tbr_smem(sizeof(PT), RUN, TPB);
+    if (a.ka == 1) k_rec_tbr<PT, RUN, TPB, true><<<grid, TPB, smem, s>>>(a);
+    else k_rec_tbr<PT, RUN, TPB, false><<<grid, TPB, smem, s>>>(a);
+}
+
+int tbr_launch(Plan* p, const TBArgs& a, cudaStream_t s)
+{
+    const int per = p->nvec >= 2 ? 2 : 1;
+    int grid = a.ntiles * (p->nvec / per);
+    if (p->tb_grid_cap > 0 && grid > p->tb_grid_cap) grid = p->tb_grid_cap;
+    if (grid < 1) return CHEB_OK;
+    const int eb = tbr_elem_bytes(p->nvec), run = p->tb_spt, tpb = p->tb_tpb;
+    bool ok = false;
+#define CHEB_TBR_GO(PT, RUN, TPB)                                     \
+    if (!ok && (int)sizeof(PT) == eb && run == RUN && tpb == TPB) {   \
+        tbr_launch_t<PT, RUN, TPB>(a, grid, s);                       \
+        ok = true;                                                    \
+    }
+    CHEB_TBR_SHAPES(CHEB_TBR_GO)
+#undef CHEB_TBR_GO
+    if (!ok) return fail(CHEB_ERR_UNSUPPORTED, "run blocking: unsupported nvec / run / threads");
+    CHEB_CUDA(cudaGetLastError());
+    p->launches++;
+    return CHEB_OK;
+}
+
+// Host work model of one launch of this kernel (cheb_plan_step_model)
+void tbr_model_launch(const Plan* p, const std::vector<TBTile>& tiles, int ka, int kb,
+                      int prev_ka, TBModel& m)
+{
+    const int nv = p->nvec;
+    const int per = nv >= 2 ? 2 : 1, align = nv >= 2 ? 4 : 8;
+    const double eb = tbr_elem_bytes(nv);
+    const double nel = nv / per;  // plane elements per site (CTAs per tile)
+    const int run = p->tb_spt, npos = p->tb_spt * p->tb_tpb;
+    const bool first = ka == 1;
+    for (const TBTile& T : tiles) {
+        const DevBlock& B = p->hblocks[T.block];
+        if (ka > B.M) continue;
+        const int ke = std::min(kb, (int)B.M), ns = ke - ka + 1;
+        const bool done = ke == B.M;
+        const int RW = T.C1 - T.C0, RH = T.R1 - T.R0, S = tbr_stride(RW, align);
+        const double inter = (double)(T.r1 - T.r0) * (T.c1 - T.c0);
+        const bool ot = T.R0 > 0, ob = T.R1 < B.W, ol = T.C0 > 0, orr = T.C1 < B.L;
+        // runs: positions t run .. t run + run - 1; a run is formed while any site is valid;
+        // every non-pad position of a formed run is formed
+        double formed = 0.0, run_orders = 0.0;
+        for (int t = 0; t * run < npos; ++t) {
+            int rl = -1, sites = 0;
+            for (int j = 0; j < run; ++j) {
+                const int q = t * run + j - 1;
+                if (q < 0) continue;
+                const int rr = q / S, cc = q - rr * S;
+                if (rr >= RH || cc >= RW) continue;
+                ++sites;
+                const bool up = ((T.R0 + rr) + (T.C0 + cc)) & 1;
+                rl = std::max(rl, tbr_limit(rr, cc, RH, RW, up, ot, ob, ol, orr));
+            }
+            const int n = std::max(0, std::min(ns, rl));
+            formed += (double)sites * n;
+            run_orders += n;
+        }
+        m.useful += inter * ns;
+        m.computed += formed;
+        // per formed run-order: RUN vertical loads and two run-end loads; per formed site-order
+        // one store; region copy into plane 0 (and pads of plane 1); all times the CTAs of the
+        // tile (one per plane element of a site)
+        const double positions = 1.0 + (double)RH * S;
+        m.smem += nel * eb * (run_orders * (run + 2.0) + formed + positions + (positions - RH * RW));
+        const double vin = first ? 1.0 : 2.0;
+        const bool to_main = first || ka <= B.ksplit;
+        const bool read_e = !first && (to_main || done);
+        const bool read_t = !first && !to_main && prev_ka > B.ksplit;
+        const double acc_in = (read_e ? 1.0 : 0.0) + (read_t ? 1.0 : 0.0);
+        const double outs = done ? 1.0 : 3.0;
+        m.l2 += (double)RH * RW * (vin * nel * eb + 4.0 * nel) + inter * nel * eb * (acc_in + outs);
+    }
+}
+
+}  // namespace cheb

@@ -171,3 +171,49 @@ def test_tiles_span_row_bands_and_column_tiles():
             t = cb.cheb_tb_tiles(W, L, s, spt * tpb)
             assert len(set(t[:, 4].tolist())) >= 2, (s, spt, tpb, W, L)
             assert len(set(t[:, 6].tolist())) >= 2, (s, spt, tpb, W, L)
+
+
+# ---- padded regions of the register-run kernel -----------------------------------------------
+def _check_tiles_padded(W, L, s, positions, align):
+    import numpy as np
+
+    import paper_0907_3022_gb300 as cb
+
+    tiles = cb.cheb_tb_tiles_padded(W, L, s, positions, align)
+    hr = (s + 1) // 2
+    cover = np.zeros((W, L), dtype=np.int32)
+    for R0, R1, C0, C1, r0, r1, c0, c1 in tiles.tolist():
+        assert 0 <= R0 <= r0 < r1 <= R1 <= W and 0 <= C0 <= c0 < c1 <= C1 <= L
+        stride = (C1 - C0 + align) // align * align
+        # at least one zero pad after every row, stride a multiple of align, and the leading
+        # zero position plus all rows fit the CTA's positions
+        assert stride >= C1 - C0 + 1 and stride % align == 0 and stride - (C1 - C0) <= align
+        assert 1 + (R1 - R0) * stride <= positions
+        assert r0 - R0 == min(hr, r0) and R1 - r1 == min(hr, W - r1)
+        assert c0 - C0 == min(s, c0) and C1 - c1 == min(s, L - c1)
+        cover[r0:r1, c0:c1] += 1
+        for r in range(r0, r1):
+            for c in range(c0, c1):
+                assert _limit(r, c, W, L, R0, R1, C0, C1) >= s
+    assert (cover == 1).all()
+    return len(tiles)
+
+
+def test_padded_tiles_partition_the_ribbon_with_valid_interiors():
+    for W, L in [(1, 1), (1, 300), (2, 3), (3, 5), (7, 230), (50, 60), (97, 41), (130, 30),
+                 (160, 400), (40, 500)]:
+        for s in (1, 3, 8, 10):
+            for positions, align in ((1536, 4), (2304, 4), (2560, 4), (3072, 4), (5120, 8)):
+                _check_tiles_padded(W, L, s, positions, align)
+
+
+def test_padded_tiles_rejected_when_one_column_does_not_fit():
+    import paper_0907_3022_gb300 as cb
+
+    with pytest.raises(cb.ChebError) as e:
+        # rows of one interior column and a 10-column halo need a stride of 24: 11 x 24 + 1 > 200
+        cb.cheb_tb_tiles_padded(300, 5000, 10, 200, 4)
+    assert e.value.status == cb.CHEB_ERR_INVALID
+    with pytest.raises(cb.ChebError):
+        cb.cheb_tb_tiles_padded(10, 10, 4, 1024, 2)
+

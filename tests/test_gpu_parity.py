@@ -453,7 +453,11 @@ def test_adjoint_full_configuration_fd_and_oracle():
 
 def test_adjoint_batch_of_realisations_c64():
     """16 disorder realisations (one potential per vector), complex64: two realisations
-    against the oracle's FP64 gradient."""
+    against the oracle's FP64 gradient.  Tolerances: P_R relative 1e-5 and the gradient
+    relative L2 5e-5 -- the complex64 forward and adjoint states carry relative errors of a
+    few 1e-6 after these 40 steps, and the gradient, a sum over steps and orders of products
+    of the two, amplifies them by the sum's condition number (sum of |terms| / |sum|, about 3
+    here), so its error is about 1e-5 at most (6e-6 measured)."""
     cb = _cb()
     import torch
 
@@ -473,8 +477,8 @@ def test_adjoint_batch_of_realisations_c64():
         a, b = oracle.rescale(-3.5, 3.5, 0.0)
         C, M = oracle.coeffs(a, b, 1.0)
         P_ref, grad_ref, _ = H.adjoint_region(a, b, C, T, psi0, mask)
-        assert abs(Pd[r].item() - P_ref) <= 1e-4 * max(P_ref, 1e-3)
-        assert rel(g[:, r].cpu().numpy(), grad_ref) <= 2e-3
+        assert abs(Pd[r].item() - P_ref) <= 1e-5 * P_ref
+        assert rel(g[:, r].cpu().numpy(), grad_ref) <= 5e-5
 
 
 def test_autograd_function_matches_adjoint():

@@ -1,5 +1,5 @@
-"""The temporally blocked recurrence at the launch shapes the ensemble benchmark runs (8 and 10
-orders per launch; 6 sites x 512 threads and 3 sites x 1024 threads per CTA), element by
+"""The temporally blocked recurrence at the launch shapes the ensemble benchmark runs (8 to 12
+orders per launch; both blocked kernels at their tuned CTA shapes), element by
 element against the FP64 oracle, on ribbons whose tiles need several row bands and several
 column tiles, so that the row halo (ceil(s/2) rows), the column halo (s columns), ragged last
 bands and columns and the merged last launch of a step are all exercised.
@@ -23,7 +23,12 @@ pytestmark = pytest.mark.gpu
 SIZES = [(158, 3177), (154, 3426), (131, 1999), (1, 300), (3, 5), (97, 41), (7, 230), (130, 30),
          (2, 3), (1, 1)]
 NSTEPS = 10
-SHAPES = [(8, 6, 512), (10, 6, 512), (8, 3, 1024), (10, 3, 1024)]
+SITES, RUNS = 0, 1
+# (orders per launch, sites per thread, threads, kernel): the strided-site kernel's tuned
+# shapes and the register-run kernel's
+SHAPES = [(8, 6, 512, SITES), (10, 6, 512, SITES), (8, 3, 1024, SITES), (10, 3, 1024, SITES),
+          (8, 3, 768, RUNS), (10, 3, 768, RUNS), (10, 5, 512, RUNS), (12, 3, 768, RUNS),
+          (10, 3, 512, RUNS)]
 
 _cache = {}
 
@@ -68,8 +73,8 @@ def _plan(cb, ens):
     return cb.Plan(desc, lo, hi, 0.0, cb.CHEB_C64, ens.nvec, keep=keep)
 
 
-@pytest.mark.parametrize("s,spt,tpb", SHAPES)
-def test_blocked_timed_shape_matches_oracle(s, spt, tpb):
+@pytest.mark.parametrize("s,spt,tpb,kernel", SHAPES)
+def test_blocked_timed_shape_matches_oracle(s, spt, tpb, kernel):
     import paper_0907_3022_gb300 as cb
 
     ens = _ensemble()
@@ -78,8 +83,8 @@ def test_blocked_timed_shape_matches_oracle(s, spt, tpb):
     plan = _plan(cb, ens)
     psi = dev_vec(x0, C64)
     plan.evolve(psi, ens.dt, 0)
-    plan.set_blocking(s, spt, tpb)
-    assert plan.blocking_shape() == (s, spt, tpb)
+    plan.set_blocking_kernel(s, spt, tpb, kernel)
+    assert plan.blocking_shape() == (s, spt, tpb) and plan.blocking_kernel() == kernel
     assert [plan.block(q)["M"] for q in range(ens.n_ribbons)] == Ms
     plan.evolve(psi, ens.dt, NSTEPS)
     out = host(psi)
