@@ -81,6 +81,9 @@ def parse():
     ap.add_argument("--matrix-free", action="store_true",
                     help="--workload holstein/polaron: matrix-free Holstein operator instead of "
                          "the stored SELL matrix")
+    ap.add_argument("--sell-sigma", type=int, default=0,
+                    help="--workload holstein/polaron with the stored matrix: SELL-C-sigma window "
+                         "(0: library default, 1: rows unsorted)")
     ap.add_argument("--hol-size", default=None,
                     help="L:NPH -- Holstein chain size for --workload holstein (profiling runs; "
                          "default 12:10)")
@@ -571,7 +574,8 @@ def _single_plan(cb, cfg, prec):
         desc, keep = cb.desc_ribbons([o.W], [o.L], o.hop, eps)
     elif cfg["kind"] == "holstein":
         desc = cb.desc_holstein(o.L, o.nph, o.periodic, o.hop, o.omega0, o.g,
-                                matrix_free=cfg.get("matrix_free", False))
+                                matrix_free=cfg.get("matrix_free", False),
+                                sell_sigma=cfg.get("sell_sigma", 0))
         keep = ()
     else:
         V = torch.from_numpy(o.potential()).to("cuda")
@@ -603,6 +607,7 @@ def run_single(args, world, rank, local):
     torch.cuda.set_device(local)
     cfg = _single_setup(args)
     cfg["matrix_free"] = bool(args.matrix_free)
+    cfg["sell_sigma"] = args.sell_sigma
     prec = cb.CHEB_C64 if args.prec == "c64" else cb.CHEB_C128
     plan, psi = _single_plan(cb, cfg, prec)
     stream = torch.cuda.current_stream()
@@ -755,6 +760,11 @@ def run_single(args, world, rank, local):
         out["e2e"] = {"value": mv_per_step * args.steps / e2e_s, "unit": UNIT,
                       "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
                       "api": "cheb_evolve_host (pinned host buffers)"}
+        if cfg["kind"] == "holstein" and not cfg["matrix_free"]:
+            st = plan.sell_stats()
+            out["sell"] = {"sigma": st["sigma"], "stored_entries": st["stored"],
+                           "offdiag_entries": st["offdiag"],
+                           "padding": st["stored"] / max(st["offdiag"], 1) - 1.0}
         line_cfg = {"workload": cfg["name"], "sites": cfg["sites"], "M": M, "l2": l2_note,
                     "operator": ("matrix-free" if cfg["matrix_free"] else "SELL-32")
                     if cfg["kind"] == "holstein" else "stencil",
@@ -996,7 +1006,7 @@ def run_polaron(args, world, rank, local):
     d = torch.from_numpy(pw.delta()).to("cuda")
     g = torch.from_numpy(pw.gsite()).to("cuda")
     desc = cb.desc_holstein(pw.L, pw.nph, pw.periodic, pw.hop, pw.omega0, 1.0, delta=d, gsite=g,
-                            matrix_free=args.matrix_free)
+                            matrix_free=args.matrix_free, sell_sigma=args.sell_sigma)
     lo, hi = pw.bounds()
     t0 = time.perf_counter()
     plan = cb.Plan(desc, [lo], [hi], pw.alpha, prec, 1, keep=(d, g))

@@ -100,7 +100,10 @@ typedef struct cheb_ham_desc {
     int32_t hol_periodic;    /* 1: bond (L-1, 0) present (needs L >= 3)                   */
     double omega0;           /* phonon frequency w0                                        */
     double g;                /* dimensionless coupling g                                   */
-    int32_t sell_sigma;      /* reserved (SELL row sorting is not applied; must be 0 or 1)  */
+    int32_t sell_sigma;      /* CHEB_HOLSTEIN stored matrix: SELL-C-sigma window (C = 32):
+                                rows sorted by decreasing length inside windows of sigma
+                                rows (a multiple of 32, <= 2^20), so chunks pad little;
+                                1 = no sorting; 0 = CHEB_SELL_SIGMA_DEFAULT               */
     /* CHEB_HOLSTEIN, optional: device [L] site couplings g_i (Eq. ghm,
        g_i = ((eps_p + eps_p,i)/w0)^{1/2}); NULL: g at every site.  With onsite = device [L]
        site potentials Delta_i (NULL: 0) this is the generalised model of Sec. 3.3. */
@@ -113,6 +116,9 @@ typedef struct cheb_ham_desc {
        as the stored matrix.  0 = SELL-C matrix.  The CSR export needs the stored matrix. */
     int32_t hol_matrix_free;
 } cheb_ham_desc;
+
+/* sell_sigma = 0 selects this window (1: rows in basis order, no sorting) */
+#define CHEB_SELL_SIGMA_DEFAULT 1
 
 typedef struct cheb_plan cheb_plan;
 
@@ -378,6 +384,11 @@ int64_t cheb_plan_launches(const cheb_plan* plan);
 int cheb_plan_set_timing(cheb_plan* plan, int enable);
 int cheb_plan_kernel_stats(cheb_plan* plan, double* ms, int64_t* launches, double* bytes,
                            int reset);
+
+/* SELL matrix of a Holstein plan: the sigma in use, the entries stored per chunk column
+   (with padding) and the off-diagonal entries of the matrix (without padding).
+   CHEB_ERR_UNSUPPORTED for plans without a stored matrix. */
+int cheb_plan_sell_stats(const cheb_plan* plan, int* sigma, int64_t* stored, int64_t* offdiag);
 
 /* ---- work model and peak probes (measurement; no counterpart in the paper) ----------- */
 /* What one step of the plan's current launch schedule does, counted on the host from the

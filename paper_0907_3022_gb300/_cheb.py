@@ -126,6 +126,7 @@ _SIGS = {
     "cheb_plan_set_timing": ([_vp, _c.c_int], _c.c_int),
     "cheb_plan_kernel_stats": ([_vp, _dp, _i64p, _dp, _c.c_int], _c.c_int),
     "cheb_plan_step_model": ([_vp, _c.POINTER(cheb_step_model)], _c.c_int),
+    "cheb_plan_sell_stats": ([_vp, _ip, _i64p, _i64p], _c.c_int),
     "cheb_measure_peak": ([_c.c_int, _vp, _dp], _c.c_int),
     "cheb_region_norm_noalloc": ([_vp, _c.c_int, _c.c_int64, _c.c_int32, _c.c_int, _c.c_int64, _vp,
                                   _vp], _c.c_int),
@@ -441,6 +442,13 @@ class Plan:
                                            ctypes.byref(by), int(reset)), "cheb_plan_kernel_stats")
         return ms.value, n.value, by.value
 
+    def sell_stats(self) -> dict:
+        """cheb_plan_sell_stats: sigma, stored entries (with padding), off-diagonal entries."""
+        sg, st, nz = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        check(lib().cheb_plan_sell_stats(self.handle, ctypes.byref(sg), ctypes.byref(st),
+                                         ctypes.byref(nz)), "cheb_plan_sell_stats")
+        return {"sigma": sg.value, "stored": st.value, "offdiag": nz.value}
+
     def step_model(self) -> dict:
         """cheb_plan_step_model as a dict (work of one step of the current schedule)."""
         m = cheb_step_model()
@@ -513,10 +521,12 @@ def desc_armchair(n_a, lengths, hop: float, onsite=None, onsite_per_vec: bool = 
 
 
 def desc_holstein(L: int, nph: int, periodic: bool, hop: float, omega0: float, g: float,
-                  delta=None, gsite=None, matrix_free: bool = False) -> cheb_ham_desc:
+                  delta=None, gsite=None, matrix_free: bool = False,
+                  sell_sigma: int = 0) -> cheb_ham_desc:
     """Holstein descriptor; delta / gsite: optional device float64 tensors [L] with the site
     potentials Delta_i and couplings g_i (keep them alive while the plan is built);
-    matrix_free: apply H without storing it (L <= 32, nph <= 15)."""
+    matrix_free: apply H without storing it (L <= 32, nph <= 15); sell_sigma: SELL-C-sigma
+    sorting window of the stored matrix (0: library default, 1: none)."""
     d = cheb_ham_desc()
     d.kind = CHEB_HOLSTEIN
     d.nblocks = 1
@@ -529,4 +539,5 @@ def desc_holstein(L: int, nph: int, periodic: bool, hop: float, omega0: float, g
     d.onsite = _ptr(delta)
     d.hol_g = _ptr(gsite)
     d.hol_matrix_free = int(matrix_free)
+    d.sell_sigma = int(sell_sigma)
     return d

@@ -164,6 +164,7 @@ static RecArgs base_args(Plan* p)
     a.sell_val = p->d_sell_val;
     a.sell_chunk_off = p->d_sell_chunk_off;
     a.sell_chunk_len = p->d_sell_chunk_len;
+    a.sell_perm = p->d_sell_perm;
     a.partials = p->d_partials;
     a.done_counter = p->d_counter;
     a.red_out = p->d_red;
@@ -198,7 +199,10 @@ static double launch_bytes(const Plan* p, int k)
         }
         total += sites * (vecs * cs + ds);
     }
-    if (p->op == OP_SELL) total += (double)p->sell_nnz_stored * (4.0 + (double)p->real_size());
+    if (p->op == OP_SELL) {
+        total += (double)p->sell_nnz_stored * (4.0 + (double)p->real_size());
+        if (p->d_sell_perm) total += 4.0 * (double)p->n_sites;  // row of each position
+    }
     return total;
 }
 
@@ -548,7 +552,7 @@ static void free_plan(Plan* p)
                     p->d_tail,
                     p->d_qcoef, p->d_partials, p->d_counter, p->d_red, p->d_err,
                     p->d_obs_scratch, p->d_rec_scratch, p->d_sell_col, p->d_sell_val, p->d_sell_chunk_off,
-                    p->d_sell_chunk_len, p->d_hol_diag_raw, p->d_sell_val_raw, p->d_binom,
+                    p->d_sell_chunk_len, p->d_sell_perm, p->d_hol_diag_raw, p->d_sell_val_raw, p->d_binom,
                     p->d_hol_rowlen, p->d_holmf_G, p->d_holmf_dtab, p->d_holmf_qtab,
                     p->d_holmf_partials};
     for (void* q : ptrs)
@@ -609,7 +613,9 @@ extern "C" int cheb_plan_create(cheb_plan** out, const cheb_ham_desc* h, const d
         return bail(fail(CHEB_ERR_ALIGN, "onsite must be 16-byte aligned"));
     if (h->kind == CHEB_HOLSTEIN && h->hol_g && !aligned16(h->hol_g))
         return bail(fail(CHEB_ERR_ALIGN, "hol_g must be 16-byte aligned"));
-    if (h->sell_sigma > 1) return bail(fail(CHEB_ERR_UNSUPPORTED, "SELL row sorting is not applied"));
+    if (h->sell_sigma < 0 || (h->sell_sigma > 1 && (h->sell_sigma % 32 != 0 || h->sell_sigma > (1 << 20))))
+        return bail(fail(CHEB_ERR_INVALID, "sell_sigma must be 0, 1 or a multiple of 32 up to 2^20"));
+    p->sell_sigma = h->sell_sigma == 0 ? CHEB_SELL_SIGMA_DEFAULT : h->sell_sigma;
     if (h->onsite_per_vec && h->kind == CHEB_HOLSTEIN)
         return bail(fail(CHEB_ERR_UNSUPPORTED, "per-vector on-site data needs a lattice kind"));
     switch (h->kind) {
@@ -1304,6 +1310,18 @@ extern "C" int cheb_autotune(cheb_plan* plan)
     return CHEB_OK;
 }
 
+extern "C" int cheb_plan_sell_stats(const cheb_plan* plan, int* sigma, int64_t* stored,
+                                    int64_t* offdiag)
+{
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "cheb_plan_sell_stats: NULL plan");
+    if (p->op != OP_SELL) return fail(CHEB_ERR_UNSUPPORTED, "cheb_plan_sell_stats: no SELL matrix");
+    if (sigma) *sigma = p->sell_sigma;
+    if (stored) *stored = p->sell_nnz_stored;
+    if (offdiag) *offdiag = p->sell_nnz_offdiag;
+    return CHEB_OK;
+}
+
 extern "C" int cheb_plan_step_model(const cheb_plan* plan, cheb_step_model* out)
 {
     const Plan* p = reinterpret_cast<const Plan*>(plan);
@@ -1414,13 +1432,23 @@ extern "C" int cheb_plan_export_csr(cheb_plan* plan, int64_t* rowptr, int64_t* c
     std::vector<double> sval(std::max<int64_t>(p->sell_nnz_stored, 1));
     CHEB_CUDA(cudaMemcpy(scol.data(), p->d_sell_col, p->sell_nnz_stored * sizeof(int32_t), cudaMemcpyDeviceToHost));
     CHEB_CUDA(cudaMemcpy(sval.data(), p->d_sell_val_raw, p->sell_nnz_stored * sizeof(double), cudaMemcpyDeviceToHost));
+    // storage position of every row (the identity without sigma sorting)
+    std::vector<int64_t> posof(n);
+    if (p->d_sell_perm) {
+        std::vector<int32_t> perm(n);
+        CHEB_CUDA(cudaMemcpy(perm.data(), p->d_sell_perm, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        for (int64_t q = 0; q < n; ++q) posof[perm[q]] = q;
+    } else {
+        for (int64_t q = 0; q < n; ++q) posof[q] = q;
+    }
     int64_t k = 0;
     for (int64_t i = 0; i < n; ++i) {
         rowptr[i] = k;
         col[k] = i;
         val[k] = diag[i];
         ++k;
-        const int64_t off = coff[i >> 5] + (i & 31);
+        const int64_t pos = posof[i];
+        const int64_t off = coff[pos >> 5] + (pos & 31);
         for (int e = 0; e < rl[i]; ++e) {
             col[k] = scol[off + (int64_t)e * 32];
             val[k] = sval[off + (int64_t)e * 32];

@@ -56,32 +56,103 @@ __device__ inline int hol_row(const HolParams& P, int64_t i, int64_t* col, doubl
     return cnt;
 }
 
-__global__ void k_hol_chunklen(HolParams P, int64_t nchunks, int32_t* chunk_len)
-{
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t i = gtid;  // one thread per row; warps are chunks
-    int len = 0;
-    if (i < P.n) {
-        int64_t col[4];
-        double val[4], d;
-        len = hol_row(P, i, col, val, &d);
-    }
-    for (int off = 16; off > 0; off >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, off));
-    if ((threadIdx.x & 31) == 0 && (gtid >> 5) < nchunks) chunk_len[gtid >> 5] = len;
-}
-
-template <typename R>
-__global__ void k_hol_fill(HolParams P, const int64_t* chunk_off, const int32_t* chunk_len,
-                           int32_t* scol, R* sval, double* sval_raw, uint8_t* rowlen,
-                           double* diag_raw, R* diag_scaled, double a, double b)
+// off-diagonal count of every row
+__global__ void k_hol_rowlen(HolParams P, uint8_t* rowlen)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     int64_t col[4];
     double val[4], d;
+    rowlen[i] = (uint8_t)hol_row(P, i, col, val, &d);
+}
+
+// sum of n bytes into *out (grid-stride, one atomic per warp)
+__global__ void k_sum_u8(const uint8_t* x, int64_t n, unsigned long long* out)
+{
+    unsigned long long t = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        t += x[i];
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, t);
+}
+
+// SELL-C-sigma row order: inside every window of sigma consecutive rows the rows are ordered by
+// decreasing off-diagonal count, rows of equal count keeping their order (stable), so that the
+// C = 32 rows of a chunk have nearly equal lengths and the chunk pads little.  One CTA per
+// window: counts per length, then positions from warp ballots in passes of blockDim rows.
+// perm[position] = row.
+__global__ void k_sell_sigma_perm(const uint8_t* rowlen, int64_t n, int sigma, int32_t* perm)
+{
+    __shared__ int cnt[5], base[5];
+    __shared__ int wtot[32][5];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int64_t w0 = (int64_t)blockIdx.x * sigma;
+    const int64_t w1 = min(n, w0 + (int64_t)sigma);
+    if (tid < 5) cnt[tid] = 0;
+    __syncthreads();
+    for (int64_t i = w0 + tid; i < w1; i += blockDim.x) atomicAdd(&cnt[4 - rowlen[i]], 1);
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int c = 0; c < 5; ++c) {
+            base[c] = acc;
+            acc += cnt[c];
+        }
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t b0 = w0; b0 < w1; b0 += blockDim.x) {
+        const int64_t i = b0 + tid;
+        const int c = i < w1 ? 4 - rowlen[i] : -1;  // class 0 = longest rows
+        int lanepre = 0;
+        for (int cc = 0; cc < 5; ++cc) {
+            const unsigned m = __ballot_sync(0xffffffffu, c == cc);
+            if (lane == 0) wtot[warp][cc] = __popc(m);
+            if (c == cc) lanepre = __popc(m & lt);
+        }
+        __syncthreads();
+        if (c >= 0) {
+            int pre = 0;
+            for (int w = 0; w < warp; ++w) pre += wtot[w][c];
+            perm[w0 + base[c] + pre + lanepre] = (int32_t)i;
+        }
+        __syncthreads();
+        if (tid < 5) {
+            int t = 0;
+            for (int w = 0; w < nw; ++w) t += wtot[w][tid];
+            base[tid] += t;
+        }
+        __syncthreads();
+    }
+}
+
+// chunk lengths: the longest row of each chunk of 32 positions (row of a position: perm, or the
+// identity without sorting)
+__global__ void k_hol_chunklen(HolParams P, const uint8_t* rowlen, const int32_t* perm,
+                               int64_t nchunks, int32_t* chunk_len)
+{
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t pos = gtid;  // one thread per position; warps are chunks
+    int len = 0;
+    if (pos < P.n) len = rowlen[perm ? (int64_t)perm[pos] : pos];
+    for (int off = 16; off > 0; off >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, off));
+    if ((threadIdx.x & 31) == 0 && (gtid >> 5) < nchunks) chunk_len[gtid >> 5] = len;
+}
+
+template <typename R>
+__global__ void k_hol_fill(HolParams P, const int32_t* perm, const int64_t* chunk_off,
+                           const int32_t* chunk_len, int32_t* scol, R* sval, double* sval_raw,
+                           uint8_t* rowlen, double* diag_raw, R* diag_scaled, double a, double b)
+{
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // storage position
+    if (pos >= P.n) return;
+    const int64_t i = perm ? (int64_t)perm[pos] : pos;                    // its row
+    int64_t col[4];
+    double val[4], d;
     const int cnt = hol_row(P, i, col, val, &d);
-    const int64_t ch = i >> 5;
-    const int lane = (int)(i & 31);
+    const int64_t ch = pos >> 5;
+    const int lane = (int)(pos & 31);
     const int len = chunk_len[ch];
     const int64_t off = chunk_off[ch] + lane;
     for (int e = 0; e < len; ++e) {
@@ -128,8 +199,24 @@ int holstein_build(Plan* p)
     CHEB_CUDA(cudaMalloc(&p->d_sell_chunk_len, nchunks * sizeof(int32_t)));
     CHEB_CUDA(cudaMalloc(&p->d_sell_chunk_off, (nchunks + 1) * sizeof(int64_t)));
     const int th = 256;
+    // row lengths (kept for the CSR export and the energy when the basis is small), then the
+    // sigma-window order of the rows
+    uint8_t* rowlen = nullptr;
+    CHEB_CUDA(cudaMalloc(&rowlen, (size_t)n));
+    k_hol_rowlen<<<(unsigned)((n + th - 1) / th), th, 0, p->stream>>>(P, rowlen);
+    p->launches++;
+    CHEB_CUDA(cudaGetLastError());
+    if (p->sell_sigma > 1) {
+        CHEB_CUDA(cudaMalloc(&p->d_sell_perm, (size_t)n * sizeof(int32_t)));
+        const int64_t nwin = (n + p->sell_sigma - 1) / p->sell_sigma;
+        k_sell_sigma_perm<<<(unsigned)nwin, std::min(p->sell_sigma, 1024), 0, p->stream>>>(
+            rowlen, n, p->sell_sigma, p->d_sell_perm);
+        p->launches++;
+        CHEB_CUDA(cudaGetLastError());
+    }
     const int64_t blocks = (nchunks * 32 + th - 1) / th;
-    k_hol_chunklen<<<(unsigned)blocks, th, 0, p->stream>>>(P, nchunks, p->d_sell_chunk_len);
+    k_hol_chunklen<<<(unsigned)blocks, th, 0, p->stream>>>(P, rowlen, p->d_sell_perm, nchunks,
+                                                          p->d_sell_chunk_len);
     p->launches++;
     CHEB_CUDA(cudaGetLastError());
     std::vector<int32_t> len(nchunks);
@@ -148,23 +235,37 @@ int holstein_build(Plan* p)
     if (keep_raw) {
         CHEB_CUDA(cudaMalloc(&p->d_sell_val_raw, ns * sizeof(double)));
         CHEB_CUDA(cudaMalloc(&p->d_hol_diag_raw, (size_t)n * sizeof(double)));
-        CHEB_CUDA(cudaMalloc(&p->d_hol_rowlen, (size_t)n));
+        p->d_hol_rowlen = rowlen;
+        rowlen = nullptr;
     }
     const DevBlock& B = p->hblocks[0];
     const unsigned gb = (unsigned)((n + th - 1) / th);
     if (p->prec == CHEB_C128)
         k_hol_fill<double><<<gb, th, 0, p->stream>>>(
-            P, p->d_sell_chunk_off, p->d_sell_chunk_len, p->d_sell_col,
-            static_cast<double*>(p->d_sell_val), p->d_sell_val_raw, p->d_hol_rowlen,
+            P, p->d_sell_perm, p->d_sell_chunk_off, p->d_sell_chunk_len, p->d_sell_col,
+            static_cast<double*>(p->d_sell_val), p->d_sell_val_raw, nullptr,
             p->d_hol_diag_raw, static_cast<double*>(p->d_diag), B.a, B.b);
     else
         k_hol_fill<float><<<gb, th, 0, p->stream>>>(
-            P, p->d_sell_chunk_off, p->d_sell_chunk_len, p->d_sell_col,
-            static_cast<float*>(p->d_sell_val), p->d_sell_val_raw, p->d_hol_rowlen,
+            P, p->d_sell_perm, p->d_sell_chunk_off, p->d_sell_chunk_len, p->d_sell_col,
+            static_cast<float*>(p->d_sell_val), p->d_sell_val_raw, nullptr,
             p->d_hol_diag_raw, static_cast<float*>(p->d_diag), B.a, B.b);
     p->launches++;
     CHEB_CUDA(cudaGetLastError());
     CHEB_CUDA(cudaStreamSynchronize(p->stream));
+    // off-diagonal entries of the matrix without padding (padding statistics)
+    unsigned long long* d_cnt = nullptr;
+    CHEB_CUDA(cudaMalloc(&d_cnt, sizeof(unsigned long long)));
+    CHEB_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), p->stream));
+    k_sum_u8<<<(unsigned)std::min<int64_t>((n + th - 1) / th, 4096), th, 0, p->stream>>>(
+        p->d_hol_rowlen ? p->d_hol_rowlen : rowlen, n, d_cnt);
+    p->launches++;
+    unsigned long long nz = 0;
+    CHEB_CUDA(cudaMemcpyAsync(&nz, d_cnt, sizeof(nz), cudaMemcpyDeviceToHost, p->stream));
+    CHEB_CUDA(cudaStreamSynchronize(p->stream));
+    cudaFree(d_cnt);
+    if (rowlen) cudaFree(rowlen);
+    p->sell_nnz_offdiag = (int64_t)nz;
     return CHEB_OK;
 }
 
@@ -177,9 +278,9 @@ int holstein_build(Plan* p)
 //   energy: [item][0][v] = <x|H x> part
 template <typename R>
 __global__ void k_hol_obs(HolParams P, const WorkItem* items, int nitems, const void* psi_,
-                          int nvec, int kind, const int64_t* chunk_off, const int32_t* chunk_len,
-                          const int32_t* scol, const R* sval, const R* dscaled, double a,
-                          double b, double* partials, int nslot)
+                          int nvec, int kind, const int32_t* perm, const int64_t* chunk_off,
+                          const int32_t* chunk_len, const int32_t* scol, const R* sval,
+                          const R* dscaled, double a, double b, double* partials, int nslot)
 {
     using C = typename CT<R>::type;
     const C* psi = static_cast<const C*>(psi_);
@@ -190,16 +291,19 @@ __global__ void k_hol_obs(HolParams P, const WorkItem* items, int nitems, const 
             for (int slot = 0; slot < nslot; ++slot) {
                 double acc = 0.0;
                 for (int64_t u = threadIdx.x; u < it.count; u += blockDim.x) {
-                    const int64_t i = it.first + u;
-                    const C x = psi[i * nvec + v];
-                    const double wgt = (double)x.x * x.x + (double)x.y * x.y;
+                    int64_t i = it.first + u;
                     if (kind == CHEB_OBS_ENERGY) {
                         // <x|H|x> = (a/2) <x|2H~ x> + b |x|^2 from the scaled matrix the
-                        // recurrence uses (padding entries are zero)
+                        // recurrence uses (padding entries are zero); the sum runs over the
+                        // matrix's storage positions, row = perm[position] when sorted
+                        const int64_t pos = i;
+                        if (perm) i = perm[pos];
+                        const C x = psi[i * nvec + v];
+                        const double wgt = (double)x.x * x.x + (double)x.y * x.y;
                         const double d = (double)dscaled[i];
                         double hx = d * x.x, hy = d * x.y;
-                        const int64_t ch = i >> 5;
-                        const int64_t off = chunk_off[ch] + (i & 31);
+                        const int64_t ch = pos >> 5;
+                        const int64_t off = chunk_off[ch] + (pos & 31);
                         for (int e = 0; e < chunk_len[ch]; ++e) {
                             const C y = psi[(int64_t)scol[off + (int64_t)e * 32] * nvec + v];
                             const double w = (double)sval[off + (int64_t)e * 32];
@@ -207,7 +311,11 @@ __global__ void k_hol_obs(HolParams P, const WorkItem* items, int nitems, const 
                             hy += w * y.y;
                         }
                         acc += 0.5 * a * ((double)x.x * hx + (double)x.y * hy) + b * wgt;
-                    } else if (kind == CHEB_OBS_HOL_DENSITY) {
+                        continue;
+                    }
+                    const C x = psi[i * nvec + v];
+                    const double wgt = (double)x.x * x.x + (double)x.y * x.y;
+                    if (kind == CHEB_OBS_HOL_DENSITY) {
                         acc += wgt;
                     } else {
                         const int e = (int)(i / P.dph);
@@ -293,13 +401,13 @@ static int hol_obs_common(Plan* p, const void* psi, int kind, double* out, cudaS
     const double ba = p->hblocks[0].a, bb = p->hblocks[0].b;
     if (p->prec == CHEB_C128)
         k_hol_obs<double><<<grid, 256, 0, s>>>(P, p->d_items, nitems, psi, p->nvec, kind,
-                                               p->d_sell_chunk_off, p->d_sell_chunk_len,
+                                               p->d_sell_perm, p->d_sell_chunk_off, p->d_sell_chunk_len,
                                                p->d_sell_col, static_cast<const double*>(p->d_sell_val),
                                                static_cast<const double*>(p->d_diag), ba, bb,
                                                p->d_obs_scratch, nslot);
     else
         k_hol_obs<float><<<grid, 256, 0, s>>>(P, p->d_items, nitems, psi, p->nvec, kind,
-                                              p->d_sell_chunk_off, p->d_sell_chunk_len,
+                                              p->d_sell_perm, p->d_sell_chunk_off, p->d_sell_chunk_len,
                                               p->d_sell_col, static_cast<const float*>(p->d_sell_val),
                                               static_cast<const float*>(p->d_diag), ba, bb,
                                               p->d_obs_scratch, nslot);

@@ -102,6 +102,7 @@ struct RecArgs {
     const void* sell_val;   // R, already multiplied by 2/a
     const int64_t* sell_chunk_off;
     const int32_t* sell_chunk_len;
+    const int32_t* sell_perm;  // SELL-C-sigma: row of each storage position (NULL: identity)
     // reductions (FIRST): per work item [nvec][2] partial (norm2, <x|2H~x>/2)
     double* partials;
     unsigned int* done_counter;
@@ -251,6 +252,9 @@ struct Plan {
     void* d_sell_val = nullptr;
     int64_t* d_sell_chunk_off = nullptr;
     int32_t* d_sell_chunk_len = nullptr;
+    int32_t* d_sell_perm = nullptr;   // row of each storage position (sigma sorting)
+    int sell_sigma = 1;               // rows sorted by length inside windows of sigma rows
+    int64_t sell_nnz_offdiag = 0;     // off-diagonal entries without padding
     double* d_hol_diag_raw = nullptr; // unscaled H_ii (double)
     double* d_sell_val_raw = nullptr; // unscaled off-diagonals (double), same layout
     int64_t hol_dph = 0;

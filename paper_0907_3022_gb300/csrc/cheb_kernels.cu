@@ -119,12 +119,13 @@ struct SellOp {
     using C = typename V2<R>::C;
     using IO = VecIO<R, VPT>;
     __device__ __forceinline__ void init(const RecArgs&, const DevBlock&) {}
-    __device__ __forceinline__ void offdiag(const RecArgs& a, const C* __restrict__ cur, int64_t,
-                                            int64_t row, int64_t, int g, int nv,
+    // pos: the row's storage position (the row itself without sigma sorting)
+    __device__ __forceinline__ void offdiag(const RecArgs& a, const C* __restrict__ cur, int64_t pos,
+                                            int64_t, int64_t, int g, int nv,
                                             C (&acc)[VPT]) const {
         const R* __restrict__ sval = static_cast<const R*>(a.sell_val);
-        const int64_t chunk = row >> 5;
-        const int64_t off = a.sell_chunk_off[chunk] + (row & 31);
+        const int64_t chunk = pos >> 5;
+        const int64_t off = a.sell_chunk_off[chunk] + (pos & 31);
         const int len = a.sell_chunk_len[chunk];
         for (int e = 0; e < len; ++e) {
             const int col = a.sell_col[off + (int64_t)e * 32];
@@ -186,9 +187,11 @@ __global__ void __launch_bounds__(512) k_rec(RecArgs a)
             split_const<R>(B.ph_im, ph.y, pl.y);
             C* __restrict__ accp = ag.to_tail ? tail : psi;
             for (int64_t u = threadIdx.x; u < units; u += blockDim.x) {
-                const int64_t sl = it.first + u / nvg;  // site (row) within the block
+                // site within the block; for a sigma-sorted SELL matrix the storage position,
+                // whose row is sell_perm[position]
+                const int64_t sl = it.first + u / nvg;
                 const int g = (int)(u % nvg);
-                const int64_t gs = B.offset + sl;
+                const int64_t gs = B.offset + (a.sell_perm ? (int64_t)__ldg(a.sell_perm + sl) : sl);
                 const int64_t base = gs * nv + (int64_t)g * VPT;
                 // every load of this site first, then arithmetic and stores
                 C x[VPT], p[VPT], acc[VPT], ps[VPT];
