@@ -1224,10 +1224,9 @@ extern "C" int cheb_autotune(cheb_plan* plan)
                                  {CHEB_TB_SITES, 4, 512}, {CHEB_TB_SITES, 6, 512},
                                  {CHEB_TB_SITES, 2, 1024}, {CHEB_TB_SITES, 3, 1024},
                                  {CHEB_TB_SITES, 6, 1024}, {CHEB_TB_SITES, 8, 1024},
-                                 {CHEB_TB_RUNS, 3, 1024}, {CHEB_TB_RUNS, 3, 768},
-                                 {CHEB_TB_RUNS, 3, 512}, {CHEB_TB_RUNS, 5, 512},
-                                 {CHEB_TB_RUNS, 5, 640}, {CHEB_TB_RUNS, 7, 384},
-                                 {CHEB_TB_RUNS, 5, 1024}, {CHEB_TB_RUNS, 7, 512}};
+                                 {CHEB_TB_RUNS, 3, 768}, {CHEB_TB_RUNS, 3, 512},
+                                 {CHEB_TB_RUNS, 5, 512}, {CHEB_TB_RUNS, 7, 384},
+                                 {CHEB_TB_RUNS, 3, 1024}, {CHEB_TB_RUNS, 7, 512}};
         for (const auto& sh : shapes) {
             if (rc) break;
             const int kern = sh[0], spt = sh[1], tpb = sh[2];

@@ -23,8 +23,14 @@
 // * Bank conflicts: with RUN odd, the lanes of a quarter warp (float4) or half warp (float2)
 //   address distinct bank groups for the same j; with S a multiple of A, the up and down
 //   neighbours (+-S) of any two lanes still do.
-// * A run is formed at an order if any of its sites is still valid; pads are never formed and
-//   keep zero in registers and shared memory.
+// * A run is formed at an order if any of its sites is still valid.  Its pads are formed too,
+//   with zero coupling, diagonal and values, so they stay exactly zero: no per-site branch in
+//   the order loop (both planes are zeroed at every tile start, so every value read is finite).
+//   The accumulation runs for every position and only interior sites are written out, and the
+//   parity of the order, which decides how (-i)^k enters, is a compile-time constant.
+// * Each thread copies the inputs of its positions of the next work item (T_{ka-1}, T_{ka-2},
+//   d and the accumulator) into staging buffers with cp.async while the current item runs its
+//   orders, so the global-memory latency of a tile start is hidden.
 //
 // Per formed site-order and plane element: one vertical load, 2 / RUN run-end loads, one store
 // (k_rec_tb: own, three neighbours, T_{k-2} and the store).
@@ -117,10 +123,12 @@ __device__ __forceinline__ void tbr_put(float4& t, int c, float2 v)
     }
 }
 
-// acc += (-i)^k q t with the sign of (-i)^k folded into q = (hi, lo)
-__device__ __forceinline__ void tbr_accum(float2& acc, const float2 q, const float2 t, const int k)
+// acc += (-i)^k q t with the sign of (-i)^k folded into q = (hi, lo); the parity of k is a
+// compile-time constant in the order loop
+template <bool ODD>
+__device__ __forceinline__ void tbr_accum(float2& acc, const float2 q, const float2 t)
 {
-    if ((k & 1) == 0) {
+    if (!ODD) {
         acc.x = fmaf(q.y, t.x, acc.x);
         acc.y = fmaf(q.y, t.y, acc.y);
         acc.x = fmaf(q.x, t.x, acc.x);
@@ -142,14 +150,105 @@ __device__ __forceinline__ float2 tbr_phase(const float2 a, const float2 ph, con
     return make_float2(rx, ry);
 }
 
-// One order of the run: dst <- 2 H~ src - dst at every site (src = T_{k-1}, dst = T_{k-2} in,
-// T_k out), T_k stored to Pw, q_k T_k added to the interior accumulators.  Reads Qr (T_{k-1}).
+// asynchronous global -> shared copies of the next tile's inputs (each thread copies, and later
+// reads back, only its own positions)
+__device__ __forceinline__ void tbr_cp16(void* sdst, const void* gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void tbr_cp8(void* sdst, const void* gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void tbr_cp4(void* sdst, const void* gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void tbr_cp(float4* sdst, const float4* gsrc) { tbr_cp16(sdst, gsrc); }
+__device__ __forceinline__ void tbr_cp(float2* sdst, const float2* gsrc) { tbr_cp8(sdst, gsrc); }
+__device__ __forceinline__ void tbr_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void tbr_cp_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Geometry of a work item (tile ti, plane element pr) as a thread sees it.
+struct TBRTile {
+    TBTile T;
+    DevBlock B;
+    int pr;
+    int S;
+    unsigned long long invS;  // q / S = (q * invS) >> 32, exact for q < 2^13
+    bool live;                // the ribbon still has orders in this launch
+};
+
+__device__ __forceinline__ TBRTile tbr_tile(const TBArgs& a, int w, int npairs, int align)
+{
+    TBRTile t;
+    const int ti = w / npairs;
+    t.pr = w - ti * npairs;
+    t.T = a.tiles[ti];
+    t.B = a.blocks[t.T.block];
+    t.live = a.ka <= t.B.M;
+    t.S = tbr_stride(t.T.C1 - t.T.C0, align);
+    t.invS = ((1ull << 32) + (unsigned)t.S - 1u) / (unsigned)t.S;
+    return t;
+}
+
+// row / column of region position e (q = e - 1); false for the zero position and the pads
+__device__ __forceinline__ bool tbr_site(const TBRTile& t, int e, int& rr, int& cc)
+{
+    const int q = e - 1;
+    rr = q >= 0 ? (int)(((unsigned long long)q * t.invS) >> 32) : -1;
+    cc = q - rr * t.S;
+    return q >= 0 && rr < t.T.R1 - t.T.R0 && cc < t.T.C1 - t.T.C0;
+}
+
+// Issue the copies of a work item's inputs for this thread's positions: T_{ka-1}, T_{ka-2}
+// (not in the first launch), d, and for interior sites the accumulator the launch continues
+// (E, or the tail when only the tail is read; when both are read the tail is loaded directly).
 template <typename PT, int RUN, bool FIRST>
+__device__ __forceinline__ void tbr_fetch(const TBArgs& a, const TBRTile& t, int e0, int npairs,
+                                          PT* stX, PT* stP, PT* stA, float* stD)
+{
+    if (!t.live) return;
+    const PT* in_prev = static_cast<const PT*>(a.in_prev);
+    const PT* in_cur = static_cast<const PT*>(a.in_cur);
+    const PT* accE = static_cast<const PT*>(a.acc_main);
+    const PT* tail = static_cast<const PT*>(a.tail);
+    const float* diag = static_cast<const float*>(a.diag);
+    const bool done = min(a.kb, t.B.M) == t.B.M;
+    const bool to_main = FIRST || (a.ka <= t.B.ksplit);
+    const bool read_e = !FIRST && (to_main || done);
+    const bool read_t = !FIRST && !to_main && a.prev_ka > t.B.ksplit;
+#pragma unroll
+    for (int j = 0; j < RUN; ++j) {
+        int rr, cc;
+        if (tbr_site(t, e0 + j, rr, cc)) {
+            const int r = t.T.R0 + rr, c = t.T.C0 + cc;
+            const int64_t g = t.B.offset + (int64_t)r * t.B.L + c;
+            const int64_t gi = g * npairs + t.pr;
+            tbr_cp(stX + e0 + j, in_cur + gi);
+            if (!FIRST) tbr_cp(stP + e0 + j, in_prev + gi);
+            tbr_cp4(stD + e0 + j, diag + g);
+            const bool inter = r >= t.T.r0 && r < t.T.r1 && c >= t.T.c0 && c < t.T.c1;
+            if (inter && (read_e || read_t)) tbr_cp(stA + e0 + j, read_e ? accE + gi : tail + gi);
+        }
+    }
+    tbr_cp_commit();
+}
+
+// One order k of parity ODD for the thread's run: dst <- 2 H~ src - dst at every position
+// (src = T_{k-1}, dst = T_{k-2} in, T_k out), T_k stored to Pw, q_k T_k added to every
+// position's accumulator (only interior ones are written out).  Pads carry zero coupling,
+// diagonal and values, so they stay exactly zero (every value read is finite: both planes are
+// zeroed at each tile start).  Reads Qr (T_{k-1}).
+template <typename PT, int RUN, bool FIRST, bool ODD>
 __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restrict__ Pw,
                                           const PT (&src)[RUN], PT (&dst)[RUN],
-                                          const float (&d)[RUN], const int (&vidx)[RUN],
-                                          unsigned padm, unsigned interm, int e0, bool active,
-                                          float bh, float bl, float2 qk, int k,
+                                          const float (&d)[RUN], const float (&bh)[RUN],
+                                          const float (&bl)[RUN], const int (&vidx)[RUN],
+                                          unsigned interm, int e0, bool active, float2 qk, int k,
                                           float2 (&acc)[RUN][TBRPlane<PT>::PER],
                                           float (&part)[FIRST ? 2 * TBRPlane<PT>::PER : 1])
 {
@@ -160,24 +259,21 @@ __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restr
         for (int j = 0; j < RUN; ++j) V[j] = Qr[vidx[j]];
         const PT Lf = Qr[e0 > 0 ? e0 - 1 : 0];
         const PT Rt = Qr[e0 + RUN];
-        const bool half = FIRST && k == 1;
 #pragma unroll
         for (int j = 0; j < RUN; ++j) {
-            if ((padm >> j) & 1u) continue;
             const PT l = j > 0 ? src[j - 1] : Lf;
             const PT r = j < RUN - 1 ? src[j + 1] : Rt;
-            const PT h = tbr_h(l, r, V[j], dst[j], src[j], d[j], bh, bl, half);
-            if ((interm >> j) & 1u) {
+            const PT h = tbr_h(l, r, V[j], dst[j], src[j], d[j], bh[j], bl[j], FIRST && ODD && k == 1);
 #pragma unroll
-                for (int c = 0; c < PER; ++c) {
-                    const float2 hv = tbr_get(h, c);
-                    tbr_accum(acc[j][c], qk, hv, k);
-                    if constexpr (FIRST) {
-                        if (k == 1) {  // ||T_0||^2, <T_0|H~ T_0> (FP32: divergence check only)
-                            const float2 x = tbr_get(src[j], c);
-                            part[2 * c + 0] = fmaf(x.x, x.x, fmaf(x.y, x.y, part[2 * c + 0]));
-                            part[2 * c + 1] = fmaf(x.x, hv.x, fmaf(x.y, hv.y, part[2 * c + 1]));
-                        }
+            for (int c = 0; c < PER; ++c) {
+                const float2 hv = tbr_get(h, c);
+                tbr_accum<ODD>(acc[j][c], qk, hv);
+                if constexpr (FIRST && ODD) {
+                    if (k == 1 && ((interm >> j) & 1u)) {
+                        // ||T_0||^2, <T_0|H~ T_0> (FP32: feeds only the divergence check)
+                        const float2 x = tbr_get(src[j], c);
+                        part[2 * c + 0] = fmaf(x.x, x.x, fmaf(x.y, x.y, part[2 * c + 0]));
+                        part[2 * c + 1] = fmaf(x.x, hv.x, fmaf(x.y, hv.y, part[2 * c + 1]));
                     }
                 }
             }
@@ -186,6 +282,42 @@ __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restr
         }
     }
     __syncthreads();
+}
+
+// orders ka..ke, two per iteration (P <- 2 H~ X - P, then X <- 2 H~ P - X); P0 = parity of ka
+template <typename PT, int RUN, bool FIRST, bool P0>
+__device__ __forceinline__ void tbr_orders(PT* plane0, PT* plane1, PT (&X)[RUN], PT (&P)[RUN],
+                                           const float (&d)[RUN], const float (&bh)[RUN],
+                                           const float (&bl)[RUN], const int (&vidx)[RUN],
+                                           unsigned interm, int e0, int rl, int ka, int ke,
+                                           const float2* __restrict__ qc,
+                                           float2 (&acc)[RUN][TBRPlane<PT>::PER],
+                                           float (&part)[FIRST ? 2 * TBRPlane<PT>::PER : 1])
+{
+    float2 qn = qc[ka];
+    int k = ka;
+    for (;;) {
+        float2 qk = qn;
+        if (k < ke) qn = qc[k + 1];
+        tbr_order<PT, RUN, FIRST, P0>(plane0, plane1, X, P, d, bh, bl, vidx, interm, e0,
+                                      rl >= k - ka + 1, qk, k, acc, part);
+        if (k == ke) break;
+        ++k;
+        qk = qn;
+        if (k < ke) qn = qc[k + 1];
+        tbr_order<PT, RUN, FIRST, !P0>(plane1, plane0, P, X, d, bh, bl, vidx, interm, e0,
+                                       rl >= k - ka + 1, qk, k, acc, part);
+        if (k == ke) break;
+        ++k;
+    }
+}
+
+template <typename PT, int RUN, int TPB>
+__host__ __device__ constexpr size_t tbr_smem_layout()
+{
+    // two planes of NPOS + 1, staging for T_{ka-1}, T_{ka-2}, the accumulator, and d
+    return (2 * ((size_t)RUN * TPB + 1) + 3 * (size_t)RUN * TPB) * sizeof(PT) +
+           (size_t)RUN * TPB * sizeof(float);
 }
 
 template <typename PT, int RUN, int TPB, bool FIRST>
@@ -198,6 +330,10 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
     extern __shared__ float4 tbr_smem_raw[];
     PT* const plane0 = reinterpret_cast<PT*>(tbr_smem_raw);
     PT* const plane1 = plane0 + PS;
+    PT* const stX = plane1 + PS;
+    PT* const stP = stX + NPOS;
+    PT* const stA = stP + NPOS;
+    float* const stD = reinterpret_cast<float*>(stA + NPOS);
     __shared__ double s_red[(TPB / 32) * 2 * PER];
     const PT zero = tbr_zero((PT*)nullptr);
     const int tid = threadIdx.x;
@@ -205,14 +341,11 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
     const int npairs = a.nvec / PER;  // plane elements per site in global memory
     const int nvec = a.nvec;
 
-    const PT* __restrict__ in_prev = static_cast<const PT*>(a.in_prev);
-    const PT* __restrict__ in_cur = static_cast<const PT*>(a.in_cur);
     PT* __restrict__ out_prev = static_cast<PT*>(a.out_prev);
     PT* __restrict__ out_cur = static_cast<PT*>(a.out_cur);
     PT* __restrict__ accE = static_cast<PT*>(a.acc_main);
     PT* __restrict__ tail = static_cast<PT*>(a.tail);
     PT* __restrict__ psi = static_cast<PT*>(a.psi);
-    const float* __restrict__ diag = static_cast<const float*>(a.diag);
     const float2* __restrict__ qc = static_cast<const float2*>(a.qcoef);
     if (tid == 0) {
         plane0[NPOS] = zero;
@@ -220,118 +353,107 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
     }
 
     const int nwork = a.ntiles * npairs;
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
-        const int ti = w / npairs, pr = w - ti * npairs;
-        const TBTile T = a.tiles[ti];
-        const DevBlock B = a.blocks[T.block];
+    int w = blockIdx.x;
+    TBRTile t = tbr_tile(a, w < nwork ? w : 0, npairs, ALIGN);
+    if (w < nwork) tbr_fetch<PT, RUN, FIRST>(a, t, e0, npairs, stX, stP, stA, stD);
+    for (; w < nwork; w += gridDim.x) {
         float part[FIRST ? 2 * PER : 1];
 #pragma unroll
         for (int q = 0; q < (FIRST ? 2 * PER : 1); ++q) part[q] = 0.f;
-        if (a.ka <= B.M) {
-            const int ke = min(a.kb, B.M);
-            const bool done = (ke == B.M);
+        const TBRTile cur = t;
+        const TBTile& T = cur.T;
+        const DevBlock& B = cur.B;
+        // this work item's inputs, copied during the previous item's orders
+        tbr_cp_wait();
+        PT X[RUN], P[RUN];
+        float d[RUN], bh[RUN], bl[RUN];
+        int vidx[RUN];
+        unsigned interm = 0;
+        int rl = -1;  // last order index (1-based shrink) at which the run is formed
+        float2 acc[RUN][PER];
+        const int ke = min(a.kb, B.M);
+        const bool done = (ke == B.M);
+        const bool to_main = FIRST || (a.ka <= B.ksplit);
+        const bool read_e = !FIRST && (to_main || done);
+        const bool read_t = !FIRST && !to_main && a.prev_ka > B.ksplit;
+        if (cur.live) {
             const int RW = T.C1 - T.C0, RH = T.R1 - T.R0;
-            const int S = tbr_stride(RW, ALIGN);
-            // q / S as (q * ceil(2^32 / S)) >> 32: exact for q < NPOS <= 2^13
-            const unsigned long long invS = ((1ull << 32) + (unsigned)S - 1u) / (unsigned)S;
             const bool open_t = T.R0 > 0, open_b = T.R1 < B.W, open_l = T.C0 > 0, open_r = T.C1 < B.L;
-            PT X[RUN], P[RUN];
-            float d[RUN];
-            int vidx[RUN];
-            unsigned padm = 0, interm = 0;
-            int rl = -1;  // last order index (1-based shrink) at which the run is formed
+            const float bhi = (float)B.beta, blo = (float)(B.beta - (double)bhi);
 #pragma unroll
             for (int j = 0; j < RUN; ++j) {
-                const int e = e0 + j, q = e - 1;
-                const int rr = q >= 0 ? (int)(((unsigned long long)q * invS) >> 32) : -1;
-                const int cc = q - rr * S;
-                const bool site = q >= 0 && rr < RH && cc < RW;
+                const int e = e0 + j;
+                int rr, cc;
                 X[j] = zero;
                 P[j] = zero;
                 d[j] = 0.f;
+                bh[j] = 0.f;
+                bl[j] = 0.f;
                 vidx[j] = 0;
-                if (site) {
+                PT ea = zero;
+                if (tbr_site(cur, e, rr, cc)) {
                     const int r = T.R0 + rr, c = T.C0 + cc;
                     const bool up = (r + c) & 1;  // vertical neighbour r - 1 (else r + 1)
                     rl = max(rl, tbr_limit(rr, cc, RH, RW, up, open_t, open_b, open_l, open_r));
-                    vidx[j] = up ? ((rr > 0 && r > 0) ? e - S : 0)
-                                 : ((rr + 1 < RH && r + 1 < B.W) ? e + S : 0);
-                    if (r >= T.r0 && r < T.r1 && c >= T.c0 && c < T.c1) interm |= 1u << j;
-                    const int64_t g = B.offset + (int64_t)r * B.L + c;
-                    X[j] = in_cur[g * npairs + pr];
-                    if (!FIRST) P[j] = in_prev[g * npairs + pr];
-                    d[j] = diag[g];
-                } else {
-                    padm |= 1u << j;
-                }
-            }
-            // the accumulator this launch continues: E (main), the tail, or E + tail at the
-            // ribbon's last order (same protocol as k_rec_tb)
-            const bool to_main = FIRST || (a.ka <= B.ksplit);
-            const bool tail_has = a.prev_ka > B.ksplit;
-            const bool read_e = !FIRST && (to_main || done);
-            const bool read_t = !FIRST && !to_main && tail_has;
-            float2 acc[RUN][PER];
+                    vidx[j] = up ? ((rr > 0 && r > 0) ? e - cur.S : 0)
+                                 : ((rr + 1 < RH && r + 1 < B.W) ? e + cur.S : 0);
+                    X[j] = stX[e];
+                    if (!FIRST) P[j] = stP[e];
+                    d[j] = stD[e];
+                    bh[j] = bhi;
+                    bl[j] = blo;
+                    if (r >= T.r0 && r < T.r1 && c >= T.c0 && c < T.c1) {
+                        interm |= 1u << j;
+                        if (read_e || read_t) ea = stA[e];
+                        if (read_e && read_t) {  // E + tail at the ribbon's last order
+                            const int64_t gi = (B.offset + (int64_t)r * B.L + c) * npairs + cur.pr;
+                            const PT tv = tail[gi];
 #pragma unroll
-            for (int j = 0; j < RUN; ++j) {
-                PT eP = zero, tP = zero;
-                if (((interm >> j) & 1u) && (read_e || read_t)) {
-                    const int q = e0 + j - 1;
-                    const int rr = (int)(((unsigned long long)q * invS) >> 32), cc = q - rr * S;
-                    const int64_t g = B.offset + (int64_t)(T.R0 + rr) * B.L + (T.C0 + cc);
-                    if (read_e) eP = accE[g * npairs + pr];
-                    if (read_t) tP = tail[g * npairs + pr];
+                            for (int q = 0; q < PER; ++q) {
+                                const float2 x = tbr_get(ea, q), y = tbr_get(tv, q);
+                                tbr_put(ea, q, make_float2(x.x + y.x, x.y + y.y));
+                            }
+                        }
+                    }
                 }
 #pragma unroll
-                for (int c = 0; c < PER; ++c) {
-                    const float2 ev = tbr_get(eP, c), tv = tbr_get(tP, c);
-                    acc[j][c] = (read_e && read_t) ? make_float2(ev.x + tv.x, ev.y + tv.y)
-                                                   : (read_t ? tv : ev);
-                }
+                for (int q = 0; q < PER; ++q) acc[j][q] = tbr_get(ea, q);
             }
-            // T_{ka-1} of every position into plane 0; pads also zero plane 1
+            // T_{ka-1} of every position into plane 0, plane 1 zeroed (pads and all)
 #pragma unroll
             for (int j = 0; j < RUN; ++j) {
                 plane0[e0 + j] = X[j];
-                if ((padm >> j) & 1u) plane1[e0 + j] = zero;
-            }
-            float bh, bl;
-            {
-                bh = (float)B.beta;
-                bl = (float)(B.beta - (double)bh);
+                plane1[e0 + j] = zero;
             }
             if (FIRST) {  // q_0 T_0
                 const float2 q0 = qc[B.coef_off + 0];
 #pragma unroll
                 for (int j = 0; j < RUN; ++j)
-                    if ((interm >> j) & 1u)
 #pragma unroll
-                        for (int c = 0; c < PER; ++c) tbr_accum(acc[j][c], q0, tbr_get(X[j], c), 0);
+                    for (int q = 0; q < PER; ++q) tbr_accum<false>(acc[j][q], q0, tbr_get(X[j], q));
             }
+            // plane 0 complete; the barrier also orders this tile's reads of the staging
+            // buffers before the copies of the next item below overwrite them
             __syncthreads();
-            // ---- the orders, two per iteration: P <- 2 H~ X - P, then X <- 2 H~ P - X ----
-            float2 qn = qc[B.coef_off + a.ka];
-            int k = a.ka;
-            for (;;) {
-                float2 qk = qn;
-                if (k < ke) qn = qc[B.coef_off + k + 1];
-                tbr_order<PT, RUN, FIRST>(plane0, plane1, X, P, d, vidx, padm, interm, e0,
-                                          rl >= k - a.ka + 1, bh, bl, qk, k, acc, part);
-                if (k == ke) break;
-                ++k;
-                qk = qn;
-                if (k < ke) qn = qc[B.coef_off + k + 1];
-                tbr_order<PT, RUN, FIRST>(plane1, plane0, P, X, d, vidx, padm, interm, e0,
-                                          rl >= k - a.ka + 1, bh, bl, qk, k, acc, part);
-                if (k == ke) break;
-                ++k;
-            }
+        }
+        // the next work item's inputs stream in while this one runs its orders
+        if (w + (int)gridDim.x < nwork) {
+            t = tbr_tile(a, w + gridDim.x, npairs, ALIGN);
+            tbr_fetch<PT, RUN, FIRST>(a, t, e0, npairs, stX, stP, stA, stD);
+        }
+        if (cur.live) {
+            if (a.ka & 1)
+                tbr_orders<PT, RUN, FIRST, true>(plane0, plane1, X, P, d, bh, bl, vidx, interm, e0,
+                                                 rl, a.ka, ke, qc + B.coef_off, acc, part);
+            else
+                tbr_orders<PT, RUN, FIRST, false>(plane0, plane1, X, P, d, bh, bl, vidx, interm,
+                                                  e0, rl, a.ka, ke, qc + B.coef_off, acc, part);
             // T_ke is in P when ke - ka is even (the last order ran the first half), else in X
             const bool last_in_p = ((ke - a.ka) & 1) == 0;
             float lim[PER];
 #pragma unroll
             for (int c = 0; c < PER; ++c)
-                lim[c] = done ? (float)(4.0 * a.norm2[((size_t)T.block * nvec + pr * PER + c) * 2]) : 0.f;
+                lim[c] = done ? (float)(4.0 * a.norm2[((size_t)T.block * nvec + cur.pr * PER + c) * 2]) : 0.f;
             float2 ph, pl;
             ph.x = (float)B.ph_re;
             pl.x = (float)(B.ph_re - (double)ph.x);
@@ -340,9 +462,9 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
 #pragma unroll
             for (int j = 0; j < RUN; ++j) {
                 if (!((interm >> j) & 1u)) continue;
-                const int q = e0 + j - 1;
-                const int rr = (int)(((unsigned long long)q * invS) >> 32), cc = q - rr * S;
-                const int64_t g = (B.offset + (int64_t)(T.R0 + rr) * B.L + (T.C0 + cc)) * npairs + pr;
+                int rr, cc;
+                tbr_site(cur, e0 + j, rr, cc);
+                const int64_t g = (B.offset + (int64_t)(T.R0 + rr) * B.L + (T.C0 + cc)) * npairs + cur.pr;
                 const PT tk = last_in_p ? P[j] : X[j];
                 const PT tk1 = last_in_p ? X[j] : P[j];
                 PT aP;
@@ -359,8 +481,8 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
                     for (int c = 0; c < PER; ++c) {
                         tbr_put(oP, c, tbr_phase(acc[j][c], ph, pl));  // E + tail + partial
                         // growth check |T_M|^2 <= 4 ||psi||^2, in FP32 (a divergence test)
-                        const float2 t = tbr_get(tk, c);
-                        const float t2 = fmaf(t.x, t.x, t.y * t.y);
+                        const float2 tv = tbr_get(tk, c);
+                        const float t2 = fmaf(tv.x, tv.x, tv.y * tv.y);
                         if (!(t2 <= lim[c])) atomicOr(a.errflag, 1);
                     }
                     psi[g] = oP;
@@ -378,14 +500,16 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
             }
             __syncthreads();
             if (tid < 2 * PER) {
-                double t = 0.0;
-                for (int q = 0; q < TPB / 32; ++q) t += s_red[q * 2 * PER + tid];
+                double tt = 0.0;
+                for (int q = 0; q < TPB / 32; ++q) tt += s_red[q * 2 * PER + tid];
                 // vector pr * PER + tid / 2, component tid % 2
-                a.partials[((size_t)ti * nvec + pr * PER) * 2 + tid] = t;
+                const int ti = w / npairs;
+                a.partials[((size_t)ti * nvec + cur.pr * PER) * 2 + tid] = tt;
             }
             __syncthreads();
         }
     }
+    tbr_cp_wait();  // no copy may be left in flight when the CTA exits
     if constexpr (FIRST) {
         __shared__ unsigned int s_last;
         __threadfence();
@@ -423,9 +547,8 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
 // Compiled (vectors per plane element, run, threads): pairs of vectors (nvec 2 and 4) and single
 // vectors (nvec 1); one CTA per SM (up to 1024 threads) or two.
 #define CHEB_TBR_SHAPES(X)                                                             \
-    X(float4, 3, 1024) X(float4, 3, 768) X(float4, 5, 512) X(float4, 5, 640)            \
-    X(float4, 7, 384) X(float4, 3, 512) X(float2, 5, 1024) X(float2, 7, 512)           \
-    X(float2, 5, 512)
+    X(float4, 3, 768) X(float4, 3, 512) X(float4, 5, 512) X(float4, 7, 384)             \
+    X(float2, 3, 1024) X(float2, 7, 512) X(float2, 5, 512)
 
 static int tbr_elem_bytes(int nv) { return nv >= 2 ? 16 : 8; }
 
@@ -439,12 +562,19 @@ bool tbr_supported(int nv, int run, int tpb)
     return false;
 }
 
-size_t tbr_smem_bytes(int nv, int run, int tpb) { return tbr_smem(tbr_elem_bytes(nv), run, tpb); }
+size_t tbr_smem_bytes(int nv, int run, int tpb)
+{
+#define CHEB_TBR_SM(PT, RUN, TPB) \
+    if ((int)sizeof(PT) == tbr_elem_bytes(nv) && run == RUN && tpb == TPB) return tbr_smem_layout<PT, RUN, TPB>();
+    CHEB_TBR_SHAPES(CHEB_TBR_SM)
+#undef CHEB_TBR_SM
+    return 0;
+}
 
 template <typename PT, int RUN, int TPB>
 static int tbr_attr_t()
 {
-    const int smem = (int)tbr_smem(sizeof(PT), RUN, TPB);
+    const int smem = (int)tbr_smem_layout<PT, RUN, TPB>();
     CHEB_CUDA(cudaFuncSetAttribute(k_rec_tbr<PT, RUN, TPB, true>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CHEB_CUDA(cudaFuncSetAttribute(k_rec_tbr<PT, RUN, TPB, false>,
@@ -465,7 +595,7 @@ int tbr_configure(int nv, int run, int tpb)
 template <typename PT, int RUN, int TPB>
 static void tbr_launch_t(const TBArgs& a, int grid, cudaStream_t s)
 {
-    const size_t smem = tbr_smem(sizeof(PT), RUN, TPB);
+    const size_t smem = tbr_smem_layout<PT, RUN, TPB>();
     if (a.ka == 1) k_rec_tbr<PT, RUN, TPB, true><<<grid, TPB, smem, s>>>(a);
     else k_rec_tbr<PT, RUN, TPB, false><<<grid, TPB, smem, s>>>(a);
 }
