@@ -1226,6 +1226,7 @@ extern "C" int cheb_autotune(cheb_plan* plan)
                                  {CHEB_TB_SITES, 6, 1024}, {CHEB_TB_SITES, 8, 1024},
                                  {CHEB_TB_RUNS, 3, 768}, {CHEB_TB_RUNS, 3, 512},
                                  {CHEB_TB_RUNS, 5, 512}, {CHEB_TB_RUNS, 7, 384},
+                                 {CHEB_TB_RUNS, 9, 256}, {CHEB_TB_RUNS, 11, 256},
                                  {CHEB_TB_RUNS, 3, 1024}, {CHEB_TB_RUNS, 7, 512}};
         for (const auto& sh : shapes) {
             if (rc) break;

@@ -182,14 +182,26 @@ struct TBRTile {
     bool live;                // the ribbon still has orders in this launch
 };
 
-__device__ __forceinline__ TBRTile tbr_tile(const TBArgs& a, int w, int npairs, int align)
+// Descriptors of a work item staged in shared memory one item ahead: the ribbon's DevBlock
+// (18 words, 8-byte aligned at word 0) and the tile (9 words); thread tid < 27 loads word tid.
+constexpr int TBR_META_WORDS = 28;
+static_assert(sizeof(DevBlock) == 18 * 4 && sizeof(TBTile) == 9 * 4, "descriptor words");
+
+__device__ __forceinline__ int tbr_meta_load(const TBArgs& a, int w, int npairs, int tid)
+{
+    const int ti = w / npairs;
+    if (tid < 18) return reinterpret_cast<const int*>(a.blocks + a.tiles[ti].block)[tid];
+    return reinterpret_cast<const int*>(a.tiles + ti)[tid - 18];
+}
+
+__device__ __forceinline__ TBRTile tbr_tile(const int* meta, int w, int ka, int npairs, int align)
 {
     TBRTile t;
     const int ti = w / npairs;
     t.pr = w - ti * npairs;
-    t.T = a.tiles[ti];
-    t.B = a.blocks[t.T.block];
-    t.live = a.ka <= t.B.M;
+    t.B = *reinterpret_cast<const DevBlock*>(meta);
+    t.T = *reinterpret_cast<const TBTile*>(meta + 18);
+    t.live = ka <= t.B.M;
     t.S = tbr_stride(t.T.C1 - t.T.C0, align);
     t.invS = ((1ull << 32) + (unsigned)t.S - 1u) / (unsigned)t.S;
     return t;
@@ -352,11 +364,22 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
         plane1[NPOS] = zero;
     }
 
+    __shared__ __align__(16) int s_meta[2][TBR_META_WORDS];  // descriptors of items it, it + 1
     const int nwork = a.ntiles * npairs;
     int w = blockIdx.x;
-    TBRTile t = tbr_tile(a, w < nwork ? w : 0, npairs, ALIGN);
-    if (w < nwork) tbr_fetch<PT, RUN, FIRST>(a, t, e0, npairs, stX, stP, stA, stD);
-    for (; w < nwork; w += gridDim.x) {
+    const bool any = w < nwork;  // a CTA without an item still counts in the finalize below
+    if (any && tid < 27) s_meta[0][tid] = tbr_meta_load(a, w, npairs, tid);
+    __syncthreads();
+    TBRTile t;
+    if (any) {
+        t = tbr_tile(s_meta[0], w, a.ka, npairs, ALIGN);
+        tbr_fetch<PT, RUN, FIRST>(a, t, e0, npairs, stX, stP, stA, stD);
+    }
+    for (int it = 0; w < nwork; w += gridDim.x, ++it) {
+        // the next item's descriptors: loads in flight during this item's start
+        const int wn = w + (int)gridDim.x;
+        int meta_word = 0;
+        if (tid < 27 && wn < nwork) meta_word = tbr_meta_load(a, wn, npairs, tid);
         float part[FIRST ? 2 * PER : 1];
 #pragma unroll
         for (int q = 0; q < (FIRST ? 2 * PER : 1); ++q) part[q] = 0.f;
@@ -432,13 +455,15 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
 #pragma unroll
                     for (int q = 0; q < PER; ++q) tbr_accum<false>(acc[j][q], q0, tbr_get(X[j], q));
             }
-            // plane 0 complete; the barrier also orders this tile's reads of the staging
-            // buffers before the copies of the next item below overwrite them
-            __syncthreads();
         }
+        // plane 0 complete; the barrier also orders this tile's reads of the staging buffers
+        // before the copies of the next item below overwrite them, and publishes the next
+        // item's descriptors (slot (it + 1) & 1 was last read two items ago)
+        if (tid < 27) s_meta[(it + 1) & 1][tid] = meta_word;
+        __syncthreads();
         // the next work item's inputs stream in while this one runs its orders
-        if (w + (int)gridDim.x < nwork) {
-            t = tbr_tile(a, w + gridDim.x, npairs, ALIGN);
+        if (wn < nwork) {
+            t = tbr_tile(s_meta[(it + 1) & 1], wn, a.ka, npairs, ALIGN);
             tbr_fetch<PT, RUN, FIRST>(a, t, e0, npairs, stX, stP, stA, stD);
         }
         if (cur.live) {
@@ -548,6 +573,7 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
 // vectors (nvec 1); one CTA per SM (up to 1024 threads) or two.
 #define CHEB_TBR_SHAPES(X)                                                             \
     X(float4, 3, 768) X(float4, 3, 512) X(float4, 5, 512) X(float4, 7, 384)             \
+    X(float4, 9, 256) X(float4, 11, 256)                                                \
     X(float2, 3, 1024) X(float2, 7, 512) X(float2, 5, 512)
 
 static int tbr_elem_bytes(int nv) { return nv >= 2 ? 16 : 8; }
