@@ -315,8 +315,7 @@ int cheb_plan_set_blocking(cheb_plan* plan, int orders_per_launch, int sites_per
                     vectors (nvec 2 and 4: the two pairs of a tile go to two CTAs) or one vector
                     (nvec 1).  Each thread prefetches its positions of the next tile while
                     the current one runs.  Compiled (run x threads): pairs 3 x 768, 3 x 512,
-                    5 x 512, 7 x 384, 9 x 256, 11 x 256; single vectors 3 x 1024, 5 x 512,
-                    7 x 512.
+                    5 x 512, 7 x 384, 9 x 256; single vectors 3 x 1024, 5 x 512, 7 x 512.
    cheb_plan_set_blocking_kernel(plan, s, spt, threads, CHEB_TB_SITES) equals
    cheb_plan_set_blocking; errors as there.  cheb_plan_blocking_kernel reports the kernel of
    the blocking in use (CHEB_TB_SITES when blocking is off). */

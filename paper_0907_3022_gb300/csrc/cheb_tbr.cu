@@ -207,14 +207,44 @@ __device__ __forceinline__ TBRTile tbr_tile(const int* meta, int w, int ka, int 
     return t;
 }
 
-// row / column of region position e (q = e - 1); false for the zero position and the pads
-__device__ __forceinline__ bool tbr_site(const TBRTile& t, int e, int& rr, int& cc)
-{
-    const int q = e - 1;
-    rr = q >= 0 ? (int)(((unsigned long long)q * t.invS) >> 32) : -1;
-    cc = q - rr * t.S;
-    return q >= 0 && rr < t.T.R1 - t.T.R0 && cc < t.T.C1 - t.T.C0;
-}
+// Walk over a thread's consecutive positions e0, e0 + 1, ...: region row rr and column cc of
+// position e (site (rr, cc) is at e = 1 + rr S + cc) and the ribbon-relative site index
+// rg = (R0 + rr) L + C0 + cc, advanced incrementally (one division per run, at its start).
+// Position 0 (the zero element) starts at column -1; columns RW .. S - 1 are pads.
+struct TBRWalk {
+    int rr, cc, rg;
+    __device__ __forceinline__ TBRWalk(const TBRTile& t, int e0)
+    {
+        const int q = e0 - 1;
+        if (q < 0) {
+            rr = 0;
+            cc = -1;
+        } else {
+            rr = (int)(((unsigned long long)q * t.invS) >> 32);
+            cc = q - rr * t.S;
+        }
+        rg = (t.T.R0 + rr) * t.B.L + t.T.C0 + cc;
+    }
+    __device__ __forceinline__ bool site(const TBRTile& t) const
+    {
+        return cc >= 0 && cc < t.T.C1 - t.T.C0 && rr < t.T.R1 - t.T.R0;
+    }
+    __device__ __forceinline__ bool interior(const TBRTile& t) const
+    {
+        const int r = t.T.R0 + rr, c = t.T.C0 + cc;
+        return r >= t.T.r0 && r < t.T.r1 && c >= t.T.c0 && c < t.T.c1;
+    }
+    __device__ __forceinline__ void next(const TBRTile& t)
+    {
+        ++cc;
+        ++rg;
+        if (cc == t.S) {
+            cc = 0;
+            ++rr;
+            rg += t.B.L - t.S;
+        }
+    }
+};
 
 // Issue the copies of a work item's inputs for this thread's positions: T_{ka-1}, T_{ka-2}
 // (not in the first launch), d, and for interior sites the accumulator the launch continues
@@ -233,19 +263,20 @@ __device__ __forceinline__ void tbr_fetch(const TBArgs& a, const TBRTile& t, int
     const bool to_main = FIRST || (a.ka <= t.B.ksplit);
     const bool read_e = !FIRST && (to_main || done);
     const bool read_t = !FIRST && !to_main && a.prev_ka > t.B.ksplit;
+    // the ribbon's first element of this plane index; sites at + rg * npairs
+    const int64_t base = t.B.offset * npairs + t.pr;
+    const PT* const accsrc = read_e ? accE : tail;
+    TBRWalk wk(t, e0);
 #pragma unroll
     for (int j = 0; j < RUN; ++j) {
-        int rr, cc;
-        if (tbr_site(t, e0 + j, rr, cc)) {
-            const int r = t.T.R0 + rr, c = t.T.C0 + cc;
-            const int64_t g = t.B.offset + (int64_t)r * t.B.L + c;
-            const int64_t gi = g * npairs + t.pr;
+        if (wk.site(t)) {
+            const int64_t gi = base + (int64_t)wk.rg * npairs;
             tbr_cp(stX + e0 + j, in_cur + gi);
             if (!FIRST) tbr_cp(stP + e0 + j, in_prev + gi);
-            tbr_cp4(stD + e0 + j, diag + g);
-            const bool inter = r >= t.T.r0 && r < t.T.r1 && c >= t.T.c0 && c < t.T.c1;
-            if (inter && (read_e || read_t)) tbr_cp(stA + e0 + j, read_e ? accE + gi : tail + gi);
+            tbr_cp4(stD + e0 + j, diag + t.B.offset + wk.rg);
+            if ((read_e || read_t) && wk.interior(t)) tbr_cp(stA + e0 + j, accsrc + gi);
         }
+        wk.next(t);
     }
     tbr_cp_commit();
 }
@@ -403,10 +434,11 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
             const int RW = T.C1 - T.C0, RH = T.R1 - T.R0;
             const bool open_t = T.R0 > 0, open_b = T.R1 < B.W, open_l = T.C0 > 0, open_r = T.C1 < B.L;
             const float bhi = (float)B.beta, blo = (float)(B.beta - (double)bhi);
+            TBRWalk wk(cur, e0);
 #pragma unroll
             for (int j = 0; j < RUN; ++j) {
                 const int e = e0 + j;
-                int rr, cc;
+                const int rr = wk.rr, cc = wk.cc;
                 X[j] = zero;
                 P[j] = zero;
                 d[j] = 0.f;
@@ -414,9 +446,9 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
                 bl[j] = 0.f;
                 vidx[j] = 0;
                 PT ea = zero;
-                if (tbr_site(cur, e, rr, cc)) {
-                    const int r = T.R0 + rr, c = T.C0 + cc;
-                    const bool up = (r + c) & 1;  // vertical neighbour r - 1 (else r + 1)
+                if (wk.site(cur)) {
+                    const int r = T.R0 + rr;
+                    const bool up = (r + T.C0 + cc) & 1;  // vertical neighbour r - 1 (else r + 1)
                     rl = max(rl, tbr_limit(rr, cc, RH, RW, up, open_t, open_b, open_l, open_r));
                     vidx[j] = up ? ((rr > 0 && r > 0) ? e - cur.S : 0)
                                  : ((rr + 1 < RH && r + 1 < B.W) ? e + cur.S : 0);
@@ -425,11 +457,11 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
                     d[j] = stD[e];
                     bh[j] = bhi;
                     bl[j] = blo;
-                    if (r >= T.r0 && r < T.r1 && c >= T.c0 && c < T.c1) {
+                    if (wk.interior(cur)) {
                         interm |= 1u << j;
                         if (read_e || read_t) ea = stA[e];
                         if (read_e && read_t) {  // E + tail at the ribbon's last order
-                            const int64_t gi = (B.offset + (int64_t)r * B.L + c) * npairs + cur.pr;
+                            const int64_t gi = (B.offset + wk.rg) * npairs + cur.pr;
                             const PT tv = tail[gi];
 #pragma unroll
                             for (int q = 0; q < PER; ++q) {
@@ -441,6 +473,7 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
                 }
 #pragma unroll
                 for (int q = 0; q < PER; ++q) acc[j][q] = tbr_get(ea, q);
+                wk.next(cur);
             }
             // T_{ka-1} of every position into plane 0, plane 1 zeroed (pads and all)
 #pragma unroll
@@ -484,12 +517,11 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
             pl.x = (float)(B.ph_re - (double)ph.x);
             ph.y = (float)B.ph_im;
             pl.y = (float)(B.ph_im - (double)ph.y);
+            TBRWalk wk(cur, e0);
 #pragma unroll
-            for (int j = 0; j < RUN; ++j) {
+            for (int j = 0; j < RUN; ++j, wk.next(cur)) {
                 if (!((interm >> j) & 1u)) continue;
-                int rr, cc;
-                tbr_site(cur, e0 + j, rr, cc);
-                const int64_t g = (B.offset + (int64_t)(T.R0 + rr) * B.L + (T.C0 + cc)) * npairs + cur.pr;
+                const int64_t g = (B.offset + wk.rg) * npairs + cur.pr;
                 const PT tk = last_in_p ? P[j] : X[j];
                 const PT tk1 = last_in_p ? X[j] : P[j];
                 PT aP;
@@ -573,7 +605,7 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
 // vectors (nvec 1); one CTA per SM (up to 1024 threads) or two.
 #define CHEB_TBR_SHAPES(X)                                                             \
     X(float4, 3, 768) X(float4, 3, 512) X(float4, 5, 512) X(float4, 7, 384)             \
-    X(float4, 9, 256) X(float4, 11, 256)                                                \
+    X(float4, 9, 256)                                                                    \
     X(float2, 3, 1024) X(float2, 7, 512) X(float2, 5, 512)
 
 static int tbr_elem_bytes(int nv) { return nv >= 2 ? 16 : 8; }

@@ -27,7 +27,7 @@ SITES, RUNS = 0, 1
 # (orders per launch, sites per thread, threads, kernel): the strided-site kernel's tuned
 # shapes and the register-run kernel's
 SHAPES = [(8, 6, 512, SITES), (10, 6, 512, SITES), (8, 3, 1024, SITES), (10, 3, 1024, SITES),
-          (8, 7, 384, RUNS), (10, 7, 384, RUNS), (10, 11, 256, RUNS), (12, 9, 256, RUNS),
+          (8, 7, 384, RUNS), (10, 7, 384, RUNS), (10, 9, 256, RUNS), (12, 9, 256, RUNS),
           (10, 3, 768, RUNS)]
 
 _cache = {}
