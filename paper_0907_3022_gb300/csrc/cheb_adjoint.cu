@@ -35,64 +35,63 @@ template <> struct AV2<float> {
     static __device__ __forceinline__ C make(float x, float y) { return make_float2(x, y); }
 };
 
-// 2 H~ x at site gs of vector v (stencil geometry of block B)
+// Geometry of the single ribbon (or 1D grid) of an adjoint plan.  The kernels run on a 2-D
+// grid: threads over the columns c, grid rows over the ribbon rows r (grid-stride), and loop
+// over the nvec vectors of a site, so no index needs a division.
+struct AdjGeo {
+    int32_t W, L, nvec;
+    int32_t diag_per_vec;
+    double beta;      // 2 h_offdiag / a
+    const void* diag; // d_i = 2 (H_ii - b) / a, [site] or [site][vec]
+};
+
+// 2 H~ x of vector v at site (r, c), element index idx = site * nvec + v
 template <typename R>
-__device__ __forceinline__ typename AV2<R>::C stencil_2h(const typename AV2<R>::C* x,
-                                                         const DevBlock& B, int64_t sl, int64_t gs,
-                                                         int nv, int v, R d)
+__device__ __forceinline__ typename AV2<R>::C adj_2h(const typename AV2<R>::C* __restrict__ x,
+                                                   const AdjGeo& g, int r, int c, int64_t idx,
+                                                   R d)
 {
-    const int r = (int)(sl / B.L);
-    const int c = (int)(sl - (int64_t)r * B.L);
     const int vr = ((r + c) & 1) ? r - 1 : r + 1;
+    const int64_t rowstep = (int64_t)g.L * g.nvec;
     R sx = 0, sy = 0;
-    if (c > 0) { auto y = x[(gs - 1) * nv + v]; sx += y.x; sy += y.y; }
-    if (c + 1 < B.L) { auto y = x[(gs + 1) * nv + v]; sx += y.x; sy += y.y; }
-    if (vr >= 0 && vr < B.W) {
-        auto y = x[(gs + (int64_t)(vr - r) * B.L) * nv + v];
+    if (c > 0) { const auto y = x[idx - g.nvec]; sx += y.x; sy += y.y; }
+    if (c + 1 < g.L) { const auto y = x[idx + g.nvec]; sx += y.x; sy += y.y; }
+    if (vr >= 0 && vr < g.W) {
+        const auto y = x[vr > r ? idx + rowstep : idx - rowstep];
         sx += y.x;
         sy += y.y;
     }
-    const auto o = x[gs * nv + v];
-    const R beta = (R)B.beta;
+    const auto o = x[idx];
+    const R beta = (R)g.beta;
     return AV2<R>::make(fma(d, o.x, beta * sx), fma(d, o.y, beta * sy));
 }
 
-struct AdjArgs {
-    const WorkItem* items;
-    int nitems;
-    int nvec;
-    const DevBlock* blocks;
-    const void* diag;
-    int diag_per_vec;
-};
-
 // forward recurrence without accumulation: out = H~ cur (first) or 2 H~ cur - prev
 template <typename R>
-__global__ void k_adj_forward(AdjArgs a, const void* cur_, const void* prev_, void* out_, int first)
+__global__ void k_adj_forward(AdjGeo g, const void* cur_, const void* prev_, void* out_, int first)
 {
     using C = typename AV2<R>::C;
     const C* cur = static_cast<const C*>(cur_);
     const C* prev = static_cast<const C*>(prev_);
     C* out = static_cast<C*>(out_);
-    const R* diag = static_cast<const R*>(a.diag);
-    for (int w = blockIdx.x; w < a.nitems; w += gridDim.x) {
-        const WorkItem it = a.items[w];
-        const DevBlock B = a.blocks[it.block];
-        for (int64_t u = threadIdx.x; u < it.count * a.nvec; u += blockDim.x) {
-            const int64_t sl = it.first + u / a.nvec;
-            const int v = (int)(u % a.nvec);
-            const int64_t gs = B.offset + sl;
-            const R d = a.diag_per_vec ? diag[gs * a.nvec + v] : diag[gs];
-            C h = stencil_2h<R>(cur, B, sl, gs, a.nvec, v, d);
+    const R* diag = static_cast<const R*>(g.diag);
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.L) return;
+    for (int r = blockIdx.y; r < g.W; r += gridDim.y) {
+        const int64_t site = (int64_t)r * g.L + c;
+        for (int v = 0; v < g.nvec; ++v) {
+            const int64_t idx = site * g.nvec + v;
+            const R d = g.diag_per_vec ? diag[idx] : diag[site];
+            C h = adj_2h<R>(cur, g, r, c, idx, d);
             if (first) {
                 h.x *= (R)0.5;
                 h.y *= (R)0.5;
             } else {
-                const C p = prev[gs * a.nvec + v];
-                h.x -= p.x;
-                h.y -= p.y;
+                const C pv = prev[idx];
+                h.x -= pv.x;
+                h.y -= pv.y;
             }
-            out[gs * a.nvec + v] = h;
+            out[idx] = h;
         }
     }
 }
@@ -100,80 +99,75 @@ __global__ void k_adj_forward(AdjArgs a, const void* cur_, const void* prev_, vo
 // reverse step k: wk_out = conj(C_k) lam + f H~ w1 - w2 (f = 2, or 1 at k = 0; no matvec at
 // k = M; no w2 for k >= M-1), grad += g Re(conj(w1) v_k) for k < M (g = 4/a, or 2/a at k = 0)
 template <typename R>
-__global__ void k_adj_reverse(AdjArgs a, int k, int M, const void* lam_, const void* w1_,
-                              void* w2out_, const void* vk_, const void* qcoef_, double* grad)
+__global__ void k_adj_reverse(AdjGeo g, int k, int M, const void* lam_, const void* w1_,
+                              void* w2out_, const void* vk_, const void* qcoef_, int coef_off,
+                              double ph_re, double ph_im, double a, double* grad)
 {
     using C = typename AV2<R>::C;
     const C* lam = static_cast<const C*>(lam_);
     const C* w1 = static_cast<const C*>(w1_);
     C* w2out = static_cast<C*>(w2out_);
     const C* vk = static_cast<const C*>(vk_);
-    using CC = typename AV2<R>::C;
-    const CC* qc = static_cast<const CC*>(qcoef_);  // (hi, lo) pairs
-    const R* diag = static_cast<const R*>(a.diag);
-    for (int w = blockIdx.x; w < a.nitems; w += gridDim.x) {
-        const WorkItem it = a.items[w];
-        const DevBlock B = a.blocks[it.block];
-        const CC qq = qc[B.coef_off + k];
-        // conj(C_k) = conj(ph) q_k (1 for even k, +i for odd k)
-        const R pr = (R)B.ph_re, pim = -(R)B.ph_im;
-        const double gfac = (k == 0 ? 2.0 : 4.0) / B.a;
-        for (int64_t sl = it.first + threadIdx.x; sl < it.first + it.count; sl += blockDim.x) {
-            const int64_t gs = B.offset + sl;
-            double gsum = 0.0;
-            for (int v = 0; v < a.nvec; ++v) {
-                const int64_t idx = gs * a.nvec + v;
-                const C l = lam[idx];
-                C lp = AV2<R>::make(pr * l.x - pim * l.y, pr * l.y + pim * l.x);
-                if (k & 1) lp = AV2<R>::make(-lp.y, lp.x);  // i * lp
-                C wk = AV2<R>::make(fma(qq.x, lp.x, qq.y * lp.x), fma(qq.x, lp.y, qq.y * lp.y));
-                if (k < M) {
-                    const R d = a.diag_per_vec ? diag[idx] : diag[gs];
-                    C h = stencil_2h<R>(w1, B, sl, gs, a.nvec, v, d);
-                    const R f = (k == 0) ? (R)0.5 : (R)1.0;
-                    wk.x += f * h.x;
-                    wk.y += f * h.y;
-                    if (k < M - 1) {
-                        const C w2 = w2out[idx];
-                        wk.x -= w2.x;
-                        wk.y -= w2.y;
-                    }
-                    const C wn = w1[idx];
-                    const C vv = vk[idx];
-                    const double gv = gfac * ((double)wn.x * vv.x + (double)wn.y * vv.y);
-                    if (a.diag_per_vec) grad[idx] += gv;
-                    else gsum += gv;
+    const C* qc = static_cast<const C*>(qcoef_);  // (hi, lo) pairs
+    const R* diag = static_cast<const R*>(g.diag);
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.L) return;
+    const C qq = qc[coef_off + k];
+    // conj(C_k) = conj(ph) q_k (1 for even k, +i for odd k)
+    const R pr = (R)ph_re, pim = -(R)ph_im;
+    const double gfac = (k == 0 ? 2.0 : 4.0) / a;
+    for (int r = blockIdx.y; r < g.W; r += gridDim.y) {
+        const int64_t site = (int64_t)r * g.L + c;
+        double gsum = 0.0;
+        for (int v = 0; v < g.nvec; ++v) {
+            const int64_t idx = site * g.nvec + v;
+            const C l = lam[idx];
+            C lp = AV2<R>::make(pr * l.x - pim * l.y, pr * l.y + pim * l.x);
+            if (k & 1) lp = AV2<R>::make(-lp.y, lp.x);  // i * lp
+            C wk = AV2<R>::make(fma(qq.x, lp.x, qq.y * lp.x), fma(qq.x, lp.y, qq.y * lp.y));
+            if (k < M) {
+                const R d = g.diag_per_vec ? diag[idx] : diag[site];
+                const C h = adj_2h<R>(w1, g, r, c, idx, d);
+                const R f = (k == 0) ? (R)0.5 : (R)1.0;
+                wk.x += f * h.x;
+                wk.y += f * h.y;
+                if (k < M - 1) {
+                    const C w2 = w2out[idx];
+                    wk.x -= w2.x;
+                    wk.y -= w2.y;
                 }
-                w2out[idx] = wk;
+                const C wn = w1[idx];
+                const C vv = vk[idx];
+                const double gv = gfac * ((double)wn.x * vv.x + (double)wn.y * vv.y);
+                if (g.diag_per_vec) grad[idx] += gv;
+                else gsum += gv;
             }
-            if (!a.diag_per_vec && k < M) grad[gs] += gsum;
+            w2out[idx] = wk;
         }
+        if (!g.diag_per_vec && k < M) grad[site] += gsum;
     }
 }
 
 // lambda_n = Pi psi_n for the region of columns > region_col
 template <typename R>
-__global__ void k_adj_region_seed(AdjArgs a, const void* psi_, void* lam_, int64_t region_col)
+__global__ void k_adj_region_seed(AdjGeo g, const void* psi_, void* lam_, int64_t region_col)
 {
     using C = typename AV2<R>::C;
     const C* psi = static_cast<const C*>(psi_);
     C* lam = static_cast<C*>(lam_);
-    for (int w = blockIdx.x; w < a.nitems; w += gridDim.x) {
-        const WorkItem it = a.items[w];
-        const DevBlock B = a.blocks[it.block];
-        for (int64_t u = threadIdx.x; u < it.count * a.nvec; u += blockDim.x) {
-            const int64_t sl = it.first + u / a.nvec;
-            const int v = (int)(u % a.nvec);
-            const int64_t gs = B.offset + sl;
-            const int r = (int)(sl / B.L);
-            const int64_t c = sl - (int64_t)r * B.L;
-            lam[gs * a.nvec + v] = (c > region_col) ? psi[gs * a.nvec + v] : AV2<R>::make(0, 0);
-        }
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.L) return;
+    for (int r = blockIdx.y; r < g.W; r += gridDim.y) {
+        const int64_t site = (int64_t)r * g.L + c;
+        for (int v = 0; v < g.nvec; ++v)
+            lam[site * g.nvec + v] = (c > region_col) ? psi[site * g.nvec + v] : AV2<R>::make(0, 0);
     }
 }
 
 // Enqueue the whole gradient computation on stream s (capturable: no allocation, no
-// synchronisation).  ws holds the trajectory, checkpoints, segment, adjoint pair and lambda.
+// synchronisation).  ws holds the trajectory psi_0 .. psi_n, the checkpoints, two rolling
+// vectors for the checkpoint pass, the segment, and three adjoint vectors (lambda of the step
+// and the two w_k being formed, rotated from step to step instead of copied).
 template <typename R>
 static int adjoint_enqueue(Plan* p, cudaStream_t s, char* ws, const void* psi0, int nsteps,
                            const void* lambda_n, int64_t region_col, double* g, void* lambda0,
@@ -184,13 +178,12 @@ static int adjoint_enqueue(Plan* p, cudaStream_t s, char* ws, const void* psi0, 
     const int M = B.M;
     const int S = (int)std::ceil(std::sqrt((double)(M + 1)));
     const int nseg = (M + 1 + S - 1) / S;
-    AdjArgs a{p->d_items, (int)p->hitems.size(), p->nvec, p->d_blocks, p->d_diag,
-              p->desc.onsite_per_vec};
-    const int grid = std::min<int>(a.nitems, 65535);
+    AdjGeo geo{B.W, B.L, p->nvec, p->desc.onsite_per_vec, B.beta, p->d_diag};
     const int th = 256;
+    const dim3 grid((unsigned)((B.L + th - 1) / th), (unsigned)std::min(B.W, 65535));
     auto V = [&](size_t i) { return static_cast<void*>(ws + i * vb); };
-    const size_t o_traj = 0, o_ck = nsteps + 1, o_seg = o_ck + 2 * nseg, o_w = o_seg + S,
-                 o_lam = o_w + 2;
+    const size_t o_traj = 0, o_ck = nsteps + 1, o_roll = o_ck + 2 * nseg, o_seg = o_roll + 2,
+                 o_lw = o_seg + S;
     int rc = CHEB_OK;
     // forward trajectory with the fused propagator
     CHEB_CUDA(cudaMemcpyAsync(V(o_traj), psi0, vb, cudaMemcpyDeviceToDevice, s));
@@ -199,12 +192,13 @@ static int adjoint_enqueue(Plan* p, cudaStream_t s, char* ws, const void* psi0, 
         rc = plan_enqueue_step(p, V(o_traj + st + 1), s);
         if (rc) return rc;
     }
-    // seed
-    void* lam = V(o_lam);
+    // seed lambda_n in adjoint buffer li
+    int li = 0;
+    void* lam = V(o_lw + li);
     if (lambda_n) {
         CHEB_CUDA(cudaMemcpyAsync(lam, lambda_n, vb, cudaMemcpyDeviceToDevice, s));
     } else {
-        k_adj_region_seed<R><<<grid, th, 0, s>>>(a, V(o_traj + nsteps), lam, region_col);
+        k_adj_region_seed<R><<<grid, th, 0, s>>>(geo, V(o_traj + nsteps), lam, region_col);
         p->launches++;
         if (P) {
             rc = launch_observable(p, V(o_traj + nsteps), CHEB_OBS_PROB_COLS, (double)region_col, P, s);
@@ -214,57 +208,51 @@ static int adjoint_enqueue(Plan* p, cudaStream_t s, char* ws, const void* psi0, 
     const size_t gbytes = (size_t)p->n_sites * (p->desc.onsite_per_vec ? p->nvec : 1) * sizeof(double);
     CHEB_CUDA(cudaMemsetAsync(g, 0, gbytes, s));
     auto fwd = [&](const void* cur, const void* prev, void* out, int first) {
-        k_adj_forward<R><<<grid, th, 0, s>>>(a, cur, prev, out, first);
+        k_adj_forward<R><<<grid, th, 0, s>>>(geo, cur, prev, out, first);
         p->launches++;
     };
+    // vectors v_k needed by the reverse sweep: k <= M - 1; the checkpoint pass forms v_1 ..
+    // v_kc, kc = the second vector of the last segment (or M - 1)
+    const int kc = std::min(M - 1, (nseg - 1) * S + 1);
     for (int st = nsteps - 1; st >= 0; --st) {
-        // checkpoints of this step: pairs (v_{jS}, v_{jS+1})
-        void* P0 = V(o_seg);
-        void* P1 = V(o_seg + 1);
-        CHEB_CUDA(cudaMemcpyAsync(P0, V(o_traj + st), vb, cudaMemcpyDeviceToDevice, s));  // v_0
-        fwd(P0, nullptr, P1, 1);                                                           // v_1
-        // P0 holds v_k, P1 holds v_{k+1}
-        for (int k = 0; k <= M; ++k) {
-            if (k % S == 0) {
-                const int j = k / S;
-                CHEB_CUDA(cudaMemcpyAsync(V(o_ck + 2 * j), P0, vb, cudaMemcpyDeviceToDevice, s));
-                if (k + 1 <= M)
-                    CHEB_CUDA(cudaMemcpyAsync(V(o_ck + 2 * j + 1), P1, vb, cudaMemcpyDeviceToDevice, s));
-            }
-            if (k + 2 <= M) {
-                fwd(P1, P0, P0, 0);  // v_{k+2} over v_k
-                std::swap(P0, P1);
-            } else if (k + 1 <= M) {
-                std::swap(P0, P1);   // P0 = v_M for a checkpoint that starts at k = M
-            } else {
-                break;
-            }
-        }
-        // reverse over segments
+        // where v_k lives during the checkpoint pass: v_0 is the trajectory's psi_st, the two
+        // vectors v_{jS}, v_{jS+1} of every segment have their own slots, the others roll
+        auto loc = [&](int k) -> void* {
+            if (k == 0) return V(o_traj + st);
+            const int j = k / S, m = k % S;
+            if (m == 0) return V(o_ck + 2 * j);
+            if (m == 1) return V(o_ck + 2 * j + 1);
+            return V(o_roll + (k & 1));
+        };
+        if (kc >= 1) fwd(loc(0), nullptr, loc(1), 1);
+        for (int k = 2; k <= kc; ++k) fwd(loc(k - 1), loc(k - 2), loc(k), 0);
+        // reverse over segments; segment vector k: the checkpoints for k0, k0 + 1, else the
+        // recomputed segment buffer
+        void* const wb0 = V(o_lw + (li + 1) % 3);  // w_k of even k
+        void* const wb1 = V(o_lw + (li + 2) % 3);  // w_k of odd k
         for (int j = nseg - 1; j >= 0; --j) {
             const int k0 = j * S, k1 = std::min(k0 + S - 1, M);
-            CHEB_CUDA(cudaMemcpyAsync(V(o_seg), V(o_ck + 2 * j), vb, cudaMemcpyDeviceToDevice, s));
-            if (k1 > k0)
-                CHEB_CUDA(cudaMemcpyAsync(V(o_seg + 1), V(o_ck + 2 * j + 1), vb, cudaMemcpyDeviceToDevice, s));
-            for (int k = k0 + 2; k <= k1; ++k)
-                fwd(V(o_seg + (k - 1 - k0)), V(o_seg + (k - 2 - k0)), V(o_seg + (k - k0)), 0);
+            auto seg = [&](int k) -> void* { return k - k0 < 2 ? loc(k) : V(o_seg + (k - k0)); };
+            for (int k = k0 + 2; k <= std::min(k1, M - 1); ++k) fwd(seg(k - 1), seg(k - 2), seg(k), 0);
             for (int k = k1; k >= k0; --k) {
-                void* wk = V(o_w + (k & 1));             // w_k overwrites w_{k+2}
-                const void* w1 = V(o_w + ((k + 1) & 1)); // w_{k+1}
-                k_adj_reverse<R><<<grid, th, 0, s>>>(a, k, M, lam, w1, wk, V(o_seg + (k - k0)),
-                                                     p->d_qcoef, g);
+                void* wk = (k & 1) ? wb1 : wb0;               // w_k overwrites w_{k+2}
+                const void* w1 = ((k + 1) & 1) ? wb1 : wb0;  // w_{k+1}
+                k_adj_reverse<R><<<grid, th, 0, s>>>(geo, k, M, lam, w1, wk,
+                                                     k < M ? seg(k) : nullptr, p->d_qcoef,
+                                                     B.coef_off, B.ph_re, B.ph_im, B.a, g);
                 p->launches++;
             }
         }
-        // lambda_s = w_0
-        CHEB_CUDA(cudaMemcpyAsync(lam, V(o_w + 0), vb, cudaMemcpyDeviceToDevice, s));
+        // lambda_st = w_0: its buffer becomes the next step's lambda
+        li = (li + 1) % 3;
+        lam = V(o_lw + li);
     }
     if (lambda0) CHEB_CUDA(cudaMemcpyAsync(lambda0, lam, vb, cudaMemcpyDeviceToDevice, s));
     CHEB_CUDA(cudaGetLastError());
     return CHEB_OK;
 }
 
-// The gradient call is recorded once as a CUDA graph (about 80 launches and 25 copies per
+// The gradient call is recorded once as a CUDA graph (about 3 M launches and one copy per
 // time step, each too short to hide its own launch overhead) and replayed while the
 // pointers, the number of steps and the plan's coefficients stay the same.
 template <typename R>
@@ -275,7 +263,7 @@ static int adjoint_impl(Plan* p, const void* psi0, int nsteps, const void* lambd
     const int M = p->hblocks[0].M;
     const int S = (int)std::ceil(std::sqrt((double)(M + 1)));
     const int nseg = (M + 1 + S - 1) / S;
-    const size_t nvecs = (size_t)(nsteps + 1) + 2 * (size_t)nseg + (size_t)S + 3;
+    const size_t nvecs = (size_t)(nsteps + 1) + 2 * (size_t)nseg + 2 + (size_t)S + 3;
     const size_t gbytes = (size_t)p->n_sites * (p->desc.onsite_per_vec ? p->nvec : 1) * sizeof(double);
     const size_t need = nvecs * vb + (grad ? 0 : gbytes);
     if (p->adj_ws_bytes < need) {
