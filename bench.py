@@ -81,6 +81,10 @@ def parse():
     ap.add_argument("--matrix-free", action="store_true",
                     help="--workload holstein/polaron: matrix-free Holstein operator instead of "
                          "the stored SELL matrix")
+    ap.add_argument("--sweep", action="store_true",
+                    help="ensemble only: time whole steps (graph replay, CUDA events) for the "
+                         "compiled blocked shapes of both blocked kernels and print one JSON line "
+                         "per shape with the work model (profiling runs; no contract line)")
     ap.add_argument("--sell-sigma", type=int, default=0,
                     help="--workload holstein/polaron with the stored matrix: SELL-C-sigma window "
                          "(0: library default, 1: rows unsorted)")
@@ -336,6 +340,45 @@ def blocked_roofline(cb, plan, kms, kcount, steps, alg_per_unit, unit_definition
              "traffic_source": "algorithmic: every operand read or written once per launch"}
     r.update(common)
     return r
+
+
+SWEEP_SHAPES = [("sites", 6, 512), ("sites", 3, 1024), ("runs", 3, 768), ("runs", 5, 512),
+                ("runs", 7, 384), ("runs", 9, 256)]
+
+
+def run_sweep(args, local):
+    """Whole-step times of the ensemble for blocked shapes: orders per launch 8, 10, 12 for each
+    (kernel, sites per thread, threads), graph-replayed steps between CUDA events."""
+    import torch
+
+    import paper_0907_3022_gb300 as cb
+
+    torch.cuda.set_device(local)
+    ens = wl.RibbonEnsemble()
+    plan, psi = make_plan(cb, ens, cb.CHEB_C64, ens.nvec, ens.packets())
+    plan.evolve(psi, ens.dt, 0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    nst = max(args.steps, 3)
+    for kname, spt, tpb in SWEEP_SHAPES:
+        kern = cb.CHEB_TB_RUNS if kname == "runs" else cb.CHEB_TB_SITES
+        for s in (8, 10, 12):
+            plan.set_blocking_kernel(s, spt, tpb, kern)
+            plan.evolve(psi, ens.dt, max(args.warmup, 3))
+            plan.sync()
+            e0.record()
+            plan.evolve(psi, ens.dt, nst)
+            e1.record()
+            torch.cuda.synchronize()
+            m = plan.step_model()
+            print(json.dumps({"kernel": kname, "sites_per_thread": spt, "threads": tpb,
+                              "orders_per_launch": s, "ms_per_step": e0.elapsed_time(e1) / nst,
+                              "computed_over_useful": m["computed_site_orders"] / m["useful_site_orders"],
+                              "smem_gb_per_step": m["smem_bytes"] / 1e9,
+                              "dram_gb_per_step": m["dram_bytes"] / 1e9,
+                              "launches_per_step": m["launches"]}), flush=True)
+    plan.close()
+    return 0
 
 
 def run_ours(args, world, rank, local):
@@ -612,7 +655,13 @@ def run_single(args, world, rank, local):
     plan, psi = _single_plan(cb, cfg, prec)
     stream = torch.cuda.current_stream()
     plan.evolve(psi, cfg["dt"], 0)
-    plan.autotune()
+    if args.blocking is None:
+        plan.autotune()
+    else:  # fixed launch shape (profiling runs): blocking as given, else the plan's default
+        f = args.blocking.split(":")
+        if int(f[0]) > 0:
+            kern = cb.CHEB_TB_RUNS if len(f) > 3 and f[3] == "runs" else cb.CHEB_TB_SITES
+            plan.set_blocking_kernel(int(f[0]), int(f[1]), int(f[2]) if len(f) > 2 else 256, kern)
     M = plan.block(0)["M"]
     a, b = oracle.rescale(*cfg["bounds"], cfg["alpha"])
     out = {}
@@ -640,8 +689,8 @@ def run_single(args, world, rank, local):
         clk = clocks.stop()
         ms = e0.elapsed_time(e1)
         gpu_launches = plan.launches() - launches0
-        roofline = None
         value = mv_per_step * args.steps / (ms / 1e3)
+        roofline = adjoint_roofline(cb, M, T, cfg["sites"], ms / args.steps, prec == cb.CHEB_C128)
         if not args.no_cpu_baseline:
             H = _oracle_operator(cfg)
             C, _ = oracle.coeffs(a, b, cfg["dt"])
@@ -783,6 +832,38 @@ def run_single(args, world, rank, local):
         print(json.dumps(line), flush=True)
     plan.close()
     return 0
+
+
+def adjoint_roofline(cb, M, T, sites, ms_per_gradient, fp64):
+    """FP64 roofline of one gradient (complex128): FP64 pipe instructions per site, counted
+    from the kernels' arithmetic -- the fused forward step 10 per order (4 DADD neighbour sums,
+    4 DFMA for 2 H~ x - p, 2 for the accumulation on average), the checkpoint and segment
+    recompute kernel 12 (the stencil 10, the subtraction 2), the reverse kernel 27 (the
+    conjugated coefficient 8, the stencil 10, the update 4, the gradient term 5) and 8 at the
+    last order (no matvec) -- times the launches of the sqrt(M) schedule, over the whole
+    gradient's time (launch gaps included), against the DFMA rate measured in this run."""
+    S = math.ceil(math.sqrt(M + 1))
+    nseg = (M + 1 + S - 1) // S
+    kc = min(M - 1, (nseg - 1) * S + 1)
+    rec = sum(max(0, min(min(j * S + S - 1, M), M - 1) - j * S - 1) for j in range(nseg))
+    per_step = M * 10 + kc * 12 + rec * 12 + M * 27 + 8
+    inst = per_step * T * sites
+    achieved = inst / (ms_per_gradient / 1e3) / 1e9
+    out = {"kernel": "k_adj_forward/k_adj_reverse + fused forward steps (whole gradient)",
+           "unit": "G FP64 pipe instructions/s", "traffic": None,
+           "launches_per_gradient": T * (M + kc + rec + M + 1) + 1,
+           "fp64_instructions_per_gradient": inst,
+           "per_unit": "per site and time step: 10 M (forward) + 12 (kc + recomputed) + 27 M + 8 "
+                       "(reverse) FP64 instructions"}
+    if not fp64:
+        out.update({"bound": "launch", "achieved": None, "peak": None, "frac": None,
+                    "note": "complex64: FP32 arithmetic; the gradient is bound by the launch "
+                            "latency of its ~3 M kernels per time step"})
+        return out
+    peak = cb.cheb_measure_peak(cb.CHEB_PEAK_FP64_GFLOPS) / 2.0
+    out.update({"bound": "fp64", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "peak_kind": "DFMA rate measured in this run by the library's probe"})
+    return out
 
 
 def run_reference_single(args, world, rank):
@@ -1117,6 +1198,8 @@ def main():
             return run_driven(args, world, rank, local)
         if args.workload != "ensemble":
             return run_single(args, world, rank, local)
+        if args.sweep:
+            return run_sweep(args, local)
         return run_ours(args, world, rank, local)
     finally:
         if world > 1:

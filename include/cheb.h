@@ -103,7 +103,7 @@ typedef struct cheb_ham_desc {
     int32_t sell_sigma;      /* CHEB_HOLSTEIN stored matrix: SELL-C-sigma window (C = 32):
                                 rows sorted by decreasing length inside windows of sigma
                                 rows (a multiple of 32, <= 2^20), so chunks pad little;
-                                1 = no sorting; 0 = CHEB_SELL_SIGMA_DEFAULT               */
+                                1 = no sorting; 0 = CHEB_SELL_SIGMA_DEFAULT_C128 / _C64   */
     /* CHEB_HOLSTEIN, optional: device [L] site couplings g_i (Eq. ghm,
        g_i = ((eps_p + eps_p,i)/w0)^{1/2}); NULL: g at every site.  With onsite = device [L]
        site potentials Delta_i (NULL: 0) this is the generalised model of Sec. 3.3. */
@@ -117,8 +117,13 @@ typedef struct cheb_ham_desc {
     int32_t hol_matrix_free;
 } cheb_ham_desc;
 
-/* sell_sigma = 0 selects this window (1: rows in basis order, no sorting) */
-#define CHEB_SELL_SIGMA_DEFAULT 1
+/* sell_sigma = 0 selects these windows: complex128 plans are bound by the FP64 rate and gain
+   from storing fewer padded entries (6.66 -> 6.41 ms per step at L = 12, nph <= 10, padding
+   25.4 % -> 0.12 %); complex64 plans are bound by gather latency, and the row indirection
+   sorting adds costs more than the padding it saves (3.86 -> 4.25 ms), so they keep the rows
+   in basis order (1) */
+#define CHEB_SELL_SIGMA_DEFAULT_C128 8192
+#define CHEB_SELL_SIGMA_DEFAULT_C64 1
 
 typedef struct cheb_plan cheb_plan;
 

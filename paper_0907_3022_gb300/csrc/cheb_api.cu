@@ -619,7 +619,8 @@ extern "C" int cheb_plan_create(cheb_plan** out, const cheb_ham_desc* h, const d
         return bail(fail(CHEB_ERR_ALIGN, "hol_g must be 16-byte aligned"));
     if (h->sell_sigma < 0 || (h->sell_sigma > 1 && (h->sell_sigma % 32 != 0 || h->sell_sigma > (1 << 20))))
         return bail(fail(CHEB_ERR_INVALID, "sell_sigma must be 0, 1 or a multiple of 32 up to 2^20"));
-    p->sell_sigma = h->sell_sigma == 0 ? CHEB_SELL_SIGMA_DEFAULT : h->sell_sigma;
+    p->sell_sigma = h->sell_sigma != 0 ? h->sell_sigma
+                    : (prec == CHEB_C128 ? CHEB_SELL_SIGMA_DEFAULT_C128 : CHEB_SELL_SIGMA_DEFAULT_C64);
     if (h->onsite_per_vec && h->kind == CHEB_HOLSTEIN)
         return bail(fail(CHEB_ERR_UNSUPPORTED, "per-vector on-site data needs a lattice kind"));
     switch (h->kind) {

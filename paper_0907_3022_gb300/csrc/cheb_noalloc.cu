@@ -59,13 +59,16 @@ __global__ void k_region_norm_partials(const void* psi_, int64_t n_sites, int32_
     }
 }
 
-// out[v] = sum over tiles, in tile order
+// out[v] = sum over the tiles: one warp per vector, lane l sums tiles l, l + 32, ... in order,
+// then a fixed xor tree (the summation order depends on the tile count only)
 __global__ void k_region_norm_finalize(const double* partials, int ntiles, int nvec, double* out)
 {
-    for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int v = warp; v < nvec; v += blockDim.x >> 5) {
         double t = 0.0;
-        for (int b = 0; b < ntiles; ++b) t += partials[(int64_t)b * nvec + v];
-        out[v] = t;
+        for (int b = lane; b < ntiles; b += 32) t += partials[(int64_t)b * nvec + v];
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) out[v] = t;
     }
 }
 
@@ -114,7 +117,7 @@ extern "C" int cheb_region_norm_noalloc(const void* psi, int prec, int64_t n_sit
         k_region_norm_partials<float><<<(unsigned)ntiles, 256, 0, s>>>(psi, n_sites, L, nvec,
                                                                          col_min, scratch);
     CHEB_CUDA(cudaGetLastError());
-    k_region_norm_finalize<<<1, 32, 0, s>>>(scratch, (int)ntiles, nvec, out);
+    k_region_norm_finalize<<<1, 256, 0, s>>>(scratch, (int)ntiles, nvec, out);
     CHEB_CUDA(cudaGetLastError());
     return CHEB_OK;
 }

@@ -717,18 +717,20 @@ void tbr_model_launch(const Plan* p, const std::vector<TBTile>& tiles, int ka, i
         }
         m.useful += inter * ns;
         m.computed += formed;
-        // per formed run-order: RUN vertical loads and two run-end loads; per formed site-order
-        // one store; region copy into plane 0 (and pads of plane 1); all times the CTAs of the
-        // tile (one per plane element of a site)
-        const double positions = 1.0 + (double)RH * S;
-        m.smem += nel * eb * (run_orders * (run + 2.0) + formed + positions + (positions - RH * RW));
+        // per formed run-order: RUN vertical loads, two run-end loads and RUN stores (pads
+        // included); per tile: both planes written over all positions, and the staging copies of
+        // the sites' inputs (T_{ka-1}, T_{ka-2}, d, the interior's accumulator), written by
+        // cp.async and read back once; all times the CTAs of the tile (one per plane element)
         const double vin = first ? 1.0 : 2.0;
         const bool to_main = first || ka <= B.ksplit;
         const bool read_e = !first && (to_main || done);
         const bool read_t = !first && !to_main && prev_ka > B.ksplit;
         const double acc_in = (read_e ? 1.0 : 0.0) + (read_t ? 1.0 : 0.0);
+        const double sites = (double)RH * RW;
+        m.smem += nel * (eb * run_orders * (2.0 * run + 2.0) + 2.0 * eb * npos +
+                         2.0 * (sites * (vin * eb + 4.0) + inter * eb * (acc_in > 0 ? 1.0 : 0.0)));
         const double outs = done ? 1.0 : 3.0;
-        m.l2 += (double)RH * RW * (vin * nel * eb + 4.0 * nel) + inter * nel * eb * (acc_in + outs);
+        m.l2 += sites * (vin * nel * eb + 4.0 * nel) + inter * nel * eb * (acc_in + outs);
     }
 }
 
