@@ -811,8 +811,6 @@ extern "C" int cheb_sync(cheb_plan* plan)
     if (flag) {
         CHEB_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream));
         CHEB_CUDA(cudaStreamSynchronize(p->stream));
-        if (flag & 2)  // a bounded barrier wait in a blocked kernel gave up (never expected)
-            return fail(CHEB_ERR_CUDA, "a blocked kernel's barrier wait gave up; results invalid");
         return fail(CHEB_ERR_DIVERGED, "a recurrence vector exceeded ||psi||: spectral bounds too tight");
     }
     return CHEB_OK;

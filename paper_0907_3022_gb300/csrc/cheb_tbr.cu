@@ -281,40 +281,6 @@ __device__ __forceinline__ void tbr_fetch(const TBArgs& a, const TBRTile& t, int
     tbr_cp_commit();
 }
 
-// Split-phase barrier of the order loop: an mbarrier in shared memory expecting every thread
-// of the CTA once per order.  A thread arrives (release) after storing its T_k, adds q_k T_k to
-// its accumulators while the others finish, and waits (acquire) for the phase before reading
-// T_k at the next order.  Every thread arrives exactly once per order, outside any branch; the
-// wait gives up after a bounded number of tries and raises bit 2 of the error flag (never
-// expected: every thread arrives).
-static constexpr int TBR_WAIT_TRIES = 1 << 22;
-
-__device__ __forceinline__ void tbr_mbar_init(uint64_t* bar, unsigned count)
-{
-    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void tbr_mbar_arrive(uint64_t* bar)
-{
-    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(a)
-                 : "memory");
-}
-__device__ __forceinline__ void tbr_mbar_wait(uint64_t* bar, unsigned parity, int* errflag)
-{
-    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
-    for (int it = 0; it < TBR_WAIT_TRIES; ++it) {
-        unsigned done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}\n"
-                     : "=r"(done)
-                     : "r"(a), "r"(parity)
-                     : "memory");
-        if (done) return;
-    }
-    atomicOr(errflag, 2);
-}
-
 // One order k of parity ODD for the thread's run: dst <- 2 H~ src - dst at every position
 // (src = T_{k-1}, dst = T_{k-2} in, T_k out), T_k stored to Pw, q_k T_k added to every
 // position's accumulator (only interior ones are written out).  Pads carry zero coupling,
@@ -327,8 +293,7 @@ __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restr
                                           const float (&bl)[RUN], const int (&vidx)[RUN],
                                           unsigned interm, int e0, bool active, float2 qk, int k,
                                           float2 (&acc)[RUN][TBRPlane<PT>::PER],
-                                          float (&part)[FIRST ? 2 * TBRPlane<PT>::PER : 1],
-                                          uint64_t* bar, unsigned& parity, int* errflag)
+                                          float (&part)[FIRST ? 2 * TBRPlane<PT>::PER : 1])
 {
     constexpr int PER = TBRPlane<PT>::PER;
     if (active) {
@@ -342,18 +307,9 @@ __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restr
             const PT l = j > 0 ? src[j - 1] : Lf;
             const PT r = j < RUN - 1 ? src[j + 1] : Rt;
             const PT h = tbr_h(l, r, V[j], dst[j], src[j], d[j], bh[j], bl[j], FIRST && ODD && k == 1);
-            dst[j] = h;
-            Pw[e0 + j] = h;
-        }
-    }
-    tbr_mbar_arrive(bar);
-    // work that reads only this thread's registers, while the others store their T_k
-    if (active) {
-#pragma unroll
-        for (int j = 0; j < RUN; ++j) {
 #pragma unroll
             for (int c = 0; c < PER; ++c) {
-                const float2 hv = tbr_get(dst[j], c);
+                const float2 hv = tbr_get(h, c);
                 tbr_accum<ODD>(acc[j][c], qk, hv);
                 if constexpr (FIRST && ODD) {
                     if (k == 1 && ((interm >> j) & 1u)) {
@@ -364,10 +320,11 @@ __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restr
                     }
                 }
             }
+            dst[j] = h;
+            Pw[e0 + j] = h;
         }
     }
-    tbr_mbar_wait(bar, parity, errflag);
-    parity ^= 1u;
+    __syncthreads();
 }
 
 // orders ka..ke, two per iteration (P <- 2 H~ X - P, then X <- 2 H~ P - X); P0 = parity of ka
@@ -378,8 +335,7 @@ __device__ __forceinline__ void tbr_orders(PT* plane0, PT* plane1, PT (&X)[RUN],
                                            unsigned interm, int e0, int rl, int ka, int ke,
                                            const float2* __restrict__ qc,
                                            float2 (&acc)[RUN][TBRPlane<PT>::PER],
-                                           float (&part)[FIRST ? 2 * TBRPlane<PT>::PER : 1],
-                                           uint64_t* bar, unsigned& parity, int* errflag)
+                                           float (&part)[FIRST ? 2 * TBRPlane<PT>::PER : 1])
 {
     float2 qn = qc[ka];
     int k = ka;
@@ -387,13 +343,13 @@ __device__ __forceinline__ void tbr_orders(PT* plane0, PT* plane1, PT (&X)[RUN],
         float2 qk = qn;
         if (k < ke) qn = qc[k + 1];
         tbr_order<PT, RUN, FIRST, P0>(plane0, plane1, X, P, d, bh, bl, vidx, interm, e0,
-                                      rl >= k - ka + 1, qk, k, acc, part, bar, parity, errflag);
+                                      rl >= k - ka + 1, qk, k, acc, part);
         if (k == ke) break;
         ++k;
         qk = qn;
         if (k < ke) qn = qc[k + 1];
         tbr_order<PT, RUN, FIRST, !P0>(plane1, plane0, P, X, d, bh, bl, vidx, interm, e0,
-                                       rl >= k - ka + 1, qk, k, acc, part, bar, parity, errflag);
+                                       rl >= k - ka + 1, qk, k, acc, part);
         if (k == ke) break;
         ++k;
     }
@@ -440,9 +396,6 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
     }
 
     __shared__ __align__(16) int s_meta[2][TBR_META_WORDS];  // descriptors of items it, it + 1
-    __shared__ uint64_t s_bar;  // the order loop's split-phase barrier
-    unsigned parity = 0;        // parity of the barrier phase this thread waits for next
-    if (tid == 0) tbr_mbar_init(&s_bar, TPB);
     const int nwork = a.ntiles * npairs;
     int w = blockIdx.x;
     const bool any = w < nwork;  // a CTA without an item still counts in the finalize below
@@ -549,12 +502,10 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
         if (cur.live) {
             if (a.ka & 1)
                 tbr_orders<PT, RUN, FIRST, true>(plane0, plane1, X, P, d, bh, bl, vidx, interm, e0,
-                                                 rl, a.ka, ke, qc + B.coef_off, acc, part, &s_bar,
-                                                 parity, a.errflag);
+                                                 rl, a.ka, ke, qc + B.coef_off, acc, part);
             else
                 tbr_orders<PT, RUN, FIRST, false>(plane0, plane1, X, P, d, bh, bl, vidx, interm,
-                                                  e0, rl, a.ka, ke, qc + B.coef_off, acc, part,
-                                                  &s_bar, parity, a.errflag);
+                                                  e0, rl, a.ka, ke, qc + B.coef_off, acc, part);
             // T_ke is in P when ke - ka is even (the last order ran the first half), else in X
             const bool last_in_p = ((ke - a.ka) & 1) == 0;
             float lim[PER];
