@@ -161,7 +161,9 @@ int cheb_plan_set_tol(cheb_plan* plan, double tol, int max_order);
 /* Replace the on-site energies (device pointer, same layout as in the descriptor). */
 int cheb_plan_set_onsite(cheb_plan* plan, const double* onsite);
 /* Scalars of the plan: sites per vector (total over ribbons), number of vectors, blocks,
-   and the a, b, M of block q (M for the last dt used, 0 before the first step). */
+   and the a, b, M of block q (M for the last dt used, 0 before the first step).  Complex64
+   lattice plans (CHEB_LAT1D, CHEB_HONEYCOMB_ZZ) enlarge the a of cheb_rescale by less than
+   one part in 2^23 so that the scaled hopping 2 h / a is a float32 number. */
 int cheb_plan_info(const cheb_plan* plan, int64_t* sites, int* nvec, int* nblocks);
 int cheb_plan_block(const cheb_plan* plan, int q, double* a, double* b, int* M,
                     int64_t* offset, int* W, int* L);

@@ -697,6 +697,18 @@ extern "C" int cheb_plan_create(cheb_plan** out, const cheb_ham_desc* h, const d
         // scaled off-diagonal: 1D grid -1/(2 dx^2); ribbons -t
         const double off = (h->kind == CHEB_LAT1D) ? -0.5 / (h->dx * h->dx) : -h->hop;
         B.beta = 2.0 * off / a;
+        if (prec == CHEB_C64 && off != 0.0 && std::isfinite(B.beta)) {
+            // complex64 lattice plans: a grows by less than one part in 2^23 so that the
+            // scaled hopping is a float32 number (|beta| rounded toward zero), which the
+            // kernels then apply with one multiply-add and no rounding bias; any a at least
+            // the half width of the spectrum is valid (Sec. 2.2)
+            float bf = (float)B.beta;
+            if (std::fabs((double)bf) > std::fabs(B.beta)) bf = std::nextafterf(bf, 0.0f);
+            if (bf != 0.0f) {
+                B.a = 2.0 * off / (double)bf;
+                B.beta = (double)bf;
+            }
+        }
         p->emin.push_back(emin[q]);
         p->emax.push_back(emax[q]);
     }

@@ -276,8 +276,7 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                     }
                 }
             }
-            float bh, bl;
-            tb_split(B.beta, bh, bl);
+            const float bh = (float)B.beta;  // exact: complex64 lattice plans choose a so
             cp_async_wait_all();
             __syncthreads();
             float dreg[SPT];  // the on-site values of this thread's sites, read once per tile
@@ -328,9 +327,8 @@ __global__ void __launch_bounds__(TPB, tb_min_blocks(NV, SPT, TPB)) k_rec_tb(TBA
                             const float2 pv = tb_get(pP, cv);
                             const float sx = (yl.x + yr.x) + yv.x;
                             const float sy = (yl.y + yr.y) + yv.y;
-                            float hx = fmaf(bl, sx, -pv.x), hy = fmaf(bl, sy, -pv.y);
-                            hx = fmaf(bh, sx, hx);
-                            hy = fmaf(bh, sy, hy);
+                            // beta is a float32 number in complex64 lattice plans
+                            float hx = fmaf(bh, sx, -pv.x), hy = fmaf(bh, sy, -pv.y);
                             hx = fmaf(d, x.x, hx);
                             hy = fmaf(d, x.y, hy);
                             if (k == 1) {  // T_1 = H~ T_0 (p = 0)

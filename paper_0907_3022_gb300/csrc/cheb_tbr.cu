@@ -80,14 +80,13 @@ __host__ __device__ __forceinline__ int tbr_limit(int rr, int cc, int RH, int RW
 __device__ __forceinline__ float4 tbr_zero(float4*) { return make_float4(0.f, 0.f, 0.f, 0.f); }
 __device__ __forceinline__ float2 tbr_zero(float2*) { return make_float2(0.f, 0.f); }
 
-// h = beta (l + r + v) - p + d x  (beta = bh + bl), halved for T_1 = H~ T_0
+// h = beta (l + r + v) - p + d x, halved for T_1 = H~ T_0; beta is a float32 number in
+// complex64 lattice plans (the plan chooses a so), zero at pads
 __device__ __forceinline__ float2 tbr_h(float2 l, float2 r, float2 v, float2 p, float2 x, float d,
-                                        float bh, float bl, bool half)
+                                        float bh, bool half)
 {
     const float sx = (l.x + r.x) + v.x, sy = (l.y + r.y) + v.y;
-    float hx = fmaf(bl, sx, -p.x), hy = fmaf(bl, sy, -p.y);
-    hx = fmaf(bh, sx, hx);
-    hy = fmaf(bh, sy, hy);
+    float hx = fmaf(bh, sx, -p.x), hy = fmaf(bh, sy, -p.y);
     hx = fmaf(d, x.x, hx);
     hy = fmaf(d, x.y, hy);
     if (half) {
@@ -97,12 +96,12 @@ __device__ __forceinline__ float2 tbr_h(float2 l, float2 r, float2 v, float2 p, 
     return make_float2(hx, hy);
 }
 __device__ __forceinline__ float4 tbr_h(float4 l, float4 r, float4 v, float4 p, float4 x, float d,
-                                        float bh, float bl, bool half)
+                                        float bh, bool half)
 {
     const float2 a = tbr_h(make_float2(l.x, l.y), make_float2(r.x, r.y), make_float2(v.x, v.y),
-                           make_float2(p.x, p.y), make_float2(x.x, x.y), d, bh, bl, half);
+                           make_float2(p.x, p.y), make_float2(x.x, x.y), d, bh, half);
     const float2 b = tbr_h(make_float2(l.z, l.w), make_float2(r.z, r.w), make_float2(v.z, v.w),
-                           make_float2(p.z, p.w), make_float2(x.z, x.w), d, bh, bl, half);
+                           make_float2(p.z, p.w), make_float2(x.z, x.w), d, bh, half);
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
@@ -290,7 +289,7 @@ template <typename PT, int RUN, bool FIRST, bool ODD>
 __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restrict__ Pw,
                                           const PT (&src)[RUN], PT (&dst)[RUN],
                                           const float (&d)[RUN], const float (&bh)[RUN],
-                                          const float (&bl)[RUN], const int (&vidx)[RUN],
+                                          const int (&vidx)[RUN],
                                           unsigned interm, int e0, bool active, float2 qk, int k,
                                           float2 (&acc)[RUN][TBRPlane<PT>::PER],
                                           float (&part)[FIRST ? 2 * TBRPlane<PT>::PER : 1])
@@ -306,7 +305,7 @@ __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restr
         for (int j = 0; j < RUN; ++j) {
             const PT l = j > 0 ? src[j - 1] : Lf;
             const PT r = j < RUN - 1 ? src[j + 1] : Rt;
-            const PT h = tbr_h(l, r, V[j], dst[j], src[j], d[j], bh[j], bl[j], FIRST && ODD && k == 1);
+            const PT h = tbr_h(l, r, V[j], dst[j], src[j], d[j], bh[j], FIRST && ODD && k == 1);
 #pragma unroll
             for (int c = 0; c < PER; ++c) {
                 const float2 hv = tbr_get(h, c);
@@ -331,7 +330,7 @@ __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restr
 template <typename PT, int RUN, bool FIRST, bool P0>
 __device__ __forceinline__ void tbr_orders(PT* plane0, PT* plane1, PT (&X)[RUN], PT (&P)[RUN],
                                            const float (&d)[RUN], const float (&bh)[RUN],
-                                           const float (&bl)[RUN], const int (&vidx)[RUN],
+                                           const int (&vidx)[RUN],
                                            unsigned interm, int e0, int rl, int ka, int ke,
                                            const float2* __restrict__ qc,
                                            float2 (&acc)[RUN][TBRPlane<PT>::PER],
@@ -342,13 +341,13 @@ __device__ __forceinline__ void tbr_orders(PT* plane0, PT* plane1, PT (&X)[RUN],
     for (;;) {
         float2 qk = qn;
         if (k < ke) qn = qc[k + 1];
-        tbr_order<PT, RUN, FIRST, P0>(plane0, plane1, X, P, d, bh, bl, vidx, interm, e0,
+        tbr_order<PT, RUN, FIRST, P0>(plane0, plane1, X, P, d, bh, vidx, interm, e0,
                                       rl >= k - ka + 1, qk, k, acc, part);
         if (k == ke) break;
         ++k;
         qk = qn;
         if (k < ke) qn = qc[k + 1];
-        tbr_order<PT, RUN, FIRST, !P0>(plane1, plane0, P, X, d, bh, bl, vidx, interm, e0,
+        tbr_order<PT, RUN, FIRST, !P0>(plane1, plane0, P, X, d, bh, vidx, interm, e0,
                                        rl >= k - ka + 1, qk, k, acc, part);
         if (k == ke) break;
         ++k;
@@ -420,7 +419,7 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
         // this work item's inputs, copied during the previous item's orders
         tbr_cp_wait();
         PT X[RUN], P[RUN];
-        float d[RUN], bh[RUN], bl[RUN];
+        float d[RUN], bh[RUN];
         int vidx[RUN];
         unsigned interm = 0;
         int rl = -1;  // last order index (1-based shrink) at which the run is formed
@@ -433,7 +432,7 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
         if (cur.live) {
             const int RW = T.C1 - T.C0, RH = T.R1 - T.R0;
             const bool open_t = T.R0 > 0, open_b = T.R1 < B.W, open_l = T.C0 > 0, open_r = T.C1 < B.L;
-            const float bhi = (float)B.beta, blo = (float)(B.beta - (double)bhi);
+            const float bhi = (float)B.beta;  // exact: the plan chooses a so
             TBRWalk wk(cur, e0);
 #pragma unroll
             for (int j = 0; j < RUN; ++j) {
@@ -443,7 +442,6 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
                 P[j] = zero;
                 d[j] = 0.f;
                 bh[j] = 0.f;
-                bl[j] = 0.f;
                 vidx[j] = 0;
                 PT ea = zero;
                 if (wk.site(cur)) {
@@ -456,7 +454,6 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
                     if (!FIRST) P[j] = stP[e];
                     d[j] = stD[e];
                     bh[j] = bhi;
-                    bl[j] = blo;
                     if (wk.interior(cur)) {
                         interm |= 1u << j;
                         if (read_e || read_t) ea = stA[e];
@@ -501,10 +498,10 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
         }
         if (cur.live) {
             if (a.ka & 1)
-                tbr_orders<PT, RUN, FIRST, true>(plane0, plane1, X, P, d, bh, bl, vidx, interm, e0,
+                tbr_orders<PT, RUN, FIRST, true>(plane0, plane1, X, P, d, bh, vidx, interm, e0,
                                                  rl, a.ka, ke, qc + B.coef_off, acc, part);
             else
-                tbr_orders<PT, RUN, FIRST, false>(plane0, plane1, X, P, d, bh, bl, vidx, interm,
+                tbr_orders<PT, RUN, FIRST, false>(plane0, plane1, X, P, d, bh, vidx, interm,
                                                   e0, rl, a.ka, ke, qc + B.coef_off, acc, part);
             // T_ke is in P when ke - ka is even (the last order ran the first half), else in X
             const bool last_in_p = ((ke - a.ka) & 1) == 0;
