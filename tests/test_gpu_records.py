@@ -7,9 +7,10 @@ FP64 reduction of the same complex64 values on the host:
   - ||psi||^2: the products of float32 values are exact in FP64, so the two sums differ only
     by FP64 summation order: relative difference <= 1e-12;
   - <psi|H|psi>: the plan applies H through its scaled diagonal d_i = 2 (eps_i - b)/a rounded
-    to float32 (and the hopping in FP64); the host reference is the oracle's operator with
-    the on-site energies eps'_i = d_i a/2 + b that this rounded diagonal represents, so the two
-    again differ by summation order only: |difference| <= 1e-12 (a ||psi||^2).
+    to float32 (and the hopping in FP64), with the plan's own a; the host reference is the
+    oracle's operator with the on-site energies eps'_i = d_i a/2 + b that this rounded diagonal
+    represents, so the two again differ by summation order only: |difference| <= 1e-12
+    (a ||psi||^2).
 """
 import numpy as np
 import pytest
@@ -61,7 +62,13 @@ def test_complex64_records_equal_fp64_host_reductions(blocking):
     off = ens.offsets()
     for q in range(ens.n_ribbons):
         rb = ens.ribbon(q)
-        a, b = oracle.rescale(*rb.bounds(), 0.0)
+        # the plan's own rescaling (complex64 lattice plans enlarge a by under one float32 ulp
+        # so that the scaled hopping is a float32 number)
+        a, b = plan.block(q)["a"], plan.block(q)["b"]
+        a0, b0 = oracle.rescale(*rb.bounds(), 0.0)
+        assert b == b0 and a0 <= a <= a0 * (1 + 2.0 ** -22)
+        # 2 h / a (h = -1) is a float32 number, up to the double rounding of a itself
+        assert abs(float(np.float32(-2.0 / a)) + 2.0 / a) <= 1e-15
         d32 = (2.0 * (rb.onsite() - b) / a).astype(np.float32)
         H = oracle.honeycomb(rb.W, rb.L, rb.hop, d32.astype(np.float64) * (a / 2.0) + b)
         for v in range(ens.nvec):
