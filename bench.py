@@ -92,8 +92,9 @@ def parse():
                     help="L:NPH -- Holstein chain size for --workload holstein (profiling runs; "
                          "default 12:10)")
     ap.add_argument("--blocking", default=None,
-                    help="S:SPT[:THREADS[:runs]] -- force S orders per launch with SPT sites per "
-                         "thread (THREADS per CTA, default 256; 'runs': the register-run kernel) "
+                    help="S:SPT[:THREADS[:KERNEL]] -- force S orders per launch with SPT sites per "
+                         "thread (THREADS per CTA, default 256; KERNEL 'runs': the register-run "
+                         "kernel, 'runs_tma': the same with boxes staged by TMA) "
                          "and skip the autotuner (profiling runs); 0:0 forces single-order "
                          "launches")
     return ap.parse_args()
@@ -318,7 +319,7 @@ def blocked_roofline(cb, plan, kms, kcount, steps, alg_per_unit, unit_definition
              "frac": achieved / smem_peak, "traffic": dram_pl,
              "kernel": ("k_rec_tbr<%s,%d,%d> (all launches of the step)"
                         % ("float4" if plan.nvec >= 2 else "float2", blk[1], blk[2])
-                        if plan.blocking_kernel() == cb.CHEB_TB_RUNS else
+                        if plan.blocking_kernel() in (cb.CHEB_TB_RUNS, cb.CHEB_TB_RUNS_TMA) else
                         "k_rec_tb<%d,%d,%d> (all launches of the step)" % (plan.nvec, blk[1], blk[2])),
              "peak_kind": "shared-memory load bandwidth measured in this run by the library's "
                           "probe (cheb_measure_peak; MEASURED_PEAKS.json has no shared-memory "
@@ -343,7 +344,17 @@ def blocked_roofline(cb, plan, kms, kcount, steps, alg_per_unit, unit_definition
 
 
 SWEEP_SHAPES = [("sites", 6, 512), ("sites", 3, 1024), ("runs", 3, 768), ("runs", 5, 512),
-                ("runs", 7, 384), ("runs", 9, 256)]
+                ("runs", 7, 384), ("runs", 9, 256), ("runs_tma", 5, 512), ("runs_tma", 7, 384),
+                ("runs_tma", 9, 256)]
+KERNEL_NAMES = {"sites": 0, "runs": 1, "runs_tma": 2}  # cheb_tb_kernel values
+
+
+def kernel_of(name):
+    return KERNEL_NAMES.get(name, 0)
+
+
+def kernel_name(k):
+    return {v: n for n, v in KERNEL_NAMES.items()}.get(k, "sites")
 
 
 def run_sweep(args, local):
@@ -361,7 +372,7 @@ def run_sweep(args, local):
     e1 = torch.cuda.Event(enable_timing=True)
     nst = max(args.steps, 3)
     for kname, spt, tpb in SWEEP_SHAPES:
-        kern = cb.CHEB_TB_RUNS if kname == "runs" else cb.CHEB_TB_SITES
+        kern = kernel_of(kname)
         for s in (8, 10, 12):
             plan.set_blocking_kernel(s, spt, tpb, kern)
             plan.evolve(psi, ens.dt, max(args.warmup, 3))
@@ -397,7 +408,7 @@ def run_ours(args, world, rank, local):
         plan.autotune()
     else:
         f = args.blocking.split(":")
-        kern = cb.CHEB_TB_RUNS if len(f) > 3 and f[3] == "runs" else cb.CHEB_TB_SITES
+        kern = kernel_of(f[3]) if len(f) > 3 else cb.CHEB_TB_SITES
         parts = [int(x) for x in f[:3]]
         bs, bspt = parts[0], parts[1]
         btpb = parts[2] if len(parts) > 2 else 256
@@ -554,8 +565,7 @@ def run_ours(args, world, rank, local):
                                      plan.launch_shape())),
             "temporal_blocking": dict(zip(("orders_per_launch", "sites_per_thread", "threads"),
                                           plan.blocking_shape()),
-                                      kernel=("runs" if plan.blocking_kernel() == cb.CHEB_TB_RUNS
-                                              else "sites")),
+                                      kernel=kernel_name(plan.blocking_kernel())),
             "parallelism": f"replicas x{world} (one ensemble per GPU)",
         },
         "site_vector_steps_per_s": site_steps,
@@ -660,7 +670,7 @@ def run_single(args, world, rank, local):
     else:  # fixed launch shape (profiling runs): blocking as given, else the plan's default
         f = args.blocking.split(":")
         if int(f[0]) > 0:
-            kern = cb.CHEB_TB_RUNS if len(f) > 3 and f[3] == "runs" else cb.CHEB_TB_SITES
+            kern = kernel_of(f[3]) if len(f) > 3 else cb.CHEB_TB_SITES
             plan.set_blocking_kernel(int(f[0]), int(f[1]), int(f[2]) if len(f) > 2 else 256, kern)
     M = plan.block(0)["M"]
     a, b = oracle.rescale(*cfg["bounds"], cfg["alpha"])

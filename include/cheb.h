@@ -322,11 +322,19 @@ int cheb_plan_set_blocking(cheb_plan* plan, int orders_per_launch, int sites_per
                     vectors (nvec 2 and 4: the two pairs of a tile go to two CTAs) or one vector
                     (nvec 1).  Each thread prefetches its positions of the next tile while
                     the current one runs.  Compiled (run x threads): pairs 3 x 768, 3 x 512,
-                    5 x 512, 7 x 384, 9 x 256; single vectors 3 x 1024, 5 x 512, 7 x 512.
+                    5 x 512, 7 x 384, 9 x 256; single vectors 3 x 1024, 5 x 512, 7 x 512;
+     CHEB_TB_RUNS_TMA  CHEB_TB_RUNS with the next tile's T_{k-1} and T_{k-2} staged by
+                    tensor-memory-access boxes (one box per vector pair and buffer, completion
+                    on an mbarrier) in place of per-thread copies; pairs of vectors only (nvec
+                    2 and 4, CHEB_ERR_UNSUPPORTED otherwise).  All tiles of a ribbon share one
+                    padded row stride S (its widest tile's) so that the box of S x (its
+                    tallest region) lands as the plane layout; ribbons whose box exceeds
+                    256 x 256, or a driver without the tensor-map encoder, fall back to the
+                    per-thread copies.  Same compiled shapes as the pairs above.
    cheb_plan_set_blocking_kernel(plan, s, spt, threads, CHEB_TB_SITES) equals
    cheb_plan_set_blocking; errors as there.  cheb_plan_blocking_kernel reports the kernel of
    the blocking in use (CHEB_TB_SITES when blocking is off). */
-typedef enum { CHEB_TB_SITES = 0, CHEB_TB_RUNS = 1 } cheb_tb_kernel;
+typedef enum { CHEB_TB_SITES = 0, CHEB_TB_RUNS = 1, CHEB_TB_RUNS_TMA = 2 } cheb_tb_kernel;
 int cheb_plan_set_blocking_kernel(cheb_plan* plan, int orders_per_launch, int sites_per_thread,
                                   int threads, int kernel);
 int cheb_plan_blocking_kernel(const cheb_plan* plan, int* kernel);
@@ -366,11 +374,14 @@ int cheb_plan_blocking(const cheb_plan* plan, int* orders_per_launch, int* sites
    interior column would not fit. */
 int cheb_tb_tiles(int W, int L, int orders_per_launch, int region_sites, int32_t* out,
                   int64_t capacity, int64_t* ntiles);
-/* The same for the register-run kernel's padded regions: region_positions = threads x run,
-   and a tile must satisfy 1 + (R1 - R0) x S <= region_positions, S the row stride (the
-   smallest multiple of align >= C1 - C0 + 1; align = 4 for pairs of vectors, 8 for one). */
+/* The same for the register-run kernel's padded regions: region_positions = threads x run;
+   10 int32 per tile: the 8 above, then the row stride S (the smallest multiple of align >=
+   C1 - C0 + 1; align = 4 for pairs of vectors, 8 for one) and the box height BH.  With
+   boxes = 0 (CHEB_TB_RUNS) S is the tile's own and BH = R1 - R0; with boxes = 1
+   (CHEB_TB_RUNS_TMA) every tile of the ribbon takes the stride of its widest tile and BH =
+   the most region rows of its tiles.  In both, 1 + BH x S <= region_positions. */
 int cheb_tb_tiles_padded(int W, int L, int orders_per_launch, int region_positions, int align,
-                         int32_t* out, int64_t capacity, int64_t* ntiles);
+                         int boxes, int32_t* out, int64_t capacity, int64_t* ntiles);
 /* Copies of the plan's device data to host memory, for checking the construction:
    the SELL matrix of a Holstein plan as CSR in original row order (rowptr [n+1] int64,
    col [nnz] int64, val [nnz] double with the unscaled H entries); nnz_out gets the count.

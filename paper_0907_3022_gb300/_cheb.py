@@ -111,7 +111,7 @@ _SIGS = {
                                         _i64p], _c.c_int),
     "cheb_tb_tiles": ([_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_int32),
                        _c.c_int64, _i64p], _c.c_int),
-    "cheb_tb_tiles_padded": ([_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int,
+    "cheb_tb_tiles_padded": ([_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int,
                               _c.POINTER(_c.c_int32), _c.c_int64, _i64p], _c.c_int),
     "cheb_plan_set_blocking_kernel": ([_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int], _c.c_int),
     "cheb_plan_blocking_kernel": ([_vp, _ip], _c.c_int),
@@ -239,22 +239,24 @@ def cheb_tb_tiles(W: int, L: int, orders_per_launch: int, region_sites: int):
     return out
 
 
-def cheb_tb_tiles_padded(W: int, L: int, orders_per_launch: int, region_positions: int, align: int):
-    """As cheb_tb_tiles for the register-run kernel's padded regions (row stride a multiple of
-    align with at least one pad, one leading zero position)."""
+def cheb_tb_tiles_padded(W: int, L: int, orders_per_launch: int, region_positions: int, align: int,
+                         boxes: bool = False):
+    """As cheb_tb_tiles for the register-run kernel's padded regions: int32 [ntiles, 10], the 8
+    columns of cheb_tb_tiles, then the row stride S and box height BH (per tile, or with
+    boxes=True the ribbon's common ones)."""
     import numpy as np
 
     n = ctypes.c_int64()
-    check(lib().cheb_tb_tiles_padded(W, L, orders_per_launch, region_positions, align, None, 0,
-                                     ctypes.byref(n)), "cheb_tb_tiles_padded")
-    out = np.zeros((n.value, 8), dtype=np.int32)
-    check(lib().cheb_tb_tiles_padded(W, L, orders_per_launch, region_positions, align,
+    check(lib().cheb_tb_tiles_padded(W, L, orders_per_launch, region_positions, align, int(boxes),
+                                     None, 0, ctypes.byref(n)), "cheb_tb_tiles_padded")
+    out = np.zeros((n.value, 10), dtype=np.int32)
+    check(lib().cheb_tb_tiles_padded(W, L, orders_per_launch, region_positions, align, int(boxes),
                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n.value,
                                      ctypes.byref(n)), "cheb_tb_tiles_padded")
     return out
 
 
-CHEB_TB_SITES, CHEB_TB_RUNS = 0, 1
+CHEB_TB_SITES, CHEB_TB_RUNS, CHEB_TB_RUNS_TMA = 0, 1, 2
 
 
 # ---- plans ---------------------------------------------------------------------------------
@@ -402,7 +404,7 @@ class Plan:
                                                   threads, kernel), "cheb_plan_set_blocking_kernel")
 
     def blocking_kernel(self) -> int:
-        """CHEB_TB_SITES or CHEB_TB_RUNS (CHEB_TB_SITES when blocking is off)."""
+        """CHEB_TB_SITES, CHEB_TB_RUNS or CHEB_TB_RUNS_TMA (CHEB_TB_SITES when blocking is off)."""
         v = ctypes.c_int()
         check(lib().cheb_plan_blocking_kernel(self.handle, ctypes.byref(v)),
               "cheb_plan_blocking_kernel")

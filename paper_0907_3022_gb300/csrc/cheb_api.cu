@@ -263,6 +263,7 @@ static int tb_set_for(Plan* p, int s)
     TBSet set;
     set.s = s;
     set.ntiles = (int)tiles.size();
+    for (int q = 0; q < p->nblocks; ++q) set.first.push_back(tiles[(size_t)begin[q]]);
     if (cudaMalloc(&set.d_tiles, tiles.size() * sizeof(TBTile)) != cudaSuccess) return -2;
     if (cudaMalloc(&set.d_begin, begin.size() * sizeof(int32_t)) != cudaSuccess) {
         cudaFree(set.d_tiles);
@@ -288,8 +289,8 @@ static int tb_prepare(Plan* p)
         minM = std::min(minM, (int)B.M);
         maxM = std::max(maxM, (int)B.M);
     }
-    int rc0 = p->tb_kernel == CHEB_TB_RUNS ? tbr_configure(p->nvec, p->tb_spt, p->tb_tpb)
-                                           : tb_configure(p->nvec, p->tb_spt, p->tb_tpb);
+    int rc0 = tb_runs(p->tb_kernel) ? tbr_configure(p->nvec, p->tb_spt, p->tb_tpb)
+                                    : tb_configure(p->nvec, p->tb_spt, p->tb_tpb);
     if (rc0) {
         p->tb_s = 0;
         return rc0;
@@ -334,7 +335,7 @@ static int tb_prepare(Plan* p)
     }
     p->tb_sched = sched;
     p->shape_epoch++;
-    return CHEB_OK;
+    return tbr_maps_prepare(p);
 }
 
 // algorithmic bytes of one blocked launch: region inputs counted once per interior site
@@ -419,6 +420,20 @@ static int enqueue_step(Plan* p, void* psi, cudaStream_t s)
 static int enqueue_step_tb(Plan* p, void* psi, cudaStream_t st)
 {
     void* pairs[2][2] = {{p->d_A, p->d_B}, {p->d_C, p->d_D}};
+    // tensor maps of psi for the first launch (register-run kernel): the plan's own step-graph
+    // capture uses the slot its graph prepared; launches enqueued directly use the last slot,
+    // refreshed here; any other capture uses none (per-thread copies: a later call may rewrite
+    // the last slot for another psi)
+    int slot = p->tm_psi_slot;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CHEB_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+        slot = Plan::kGraphSlots;
+        int rc = tbr_maps_psi(p, psi, slot, st);
+        if (rc) return rc;
+    } else if (slot == Plan::kGraphSlots) {
+        slot = -1;
+    }
     for (size_t i = 0; i < p->tb_sched.size(); ++i) {
         const Plan::TBLaunch& L = p->tb_sched[i];
         const TBSet& set = p->tb_sets[L.set];
@@ -452,6 +467,8 @@ static int enqueue_step_tb(Plan* p, void* psi, cudaStream_t st)
         a.block_tile_begin = set.d_begin;
         a.norm2 = p->d_red;
         a.errflag = p->d_err;
+        a.tm_cur = tbr_maps_for(p, (int)i, 0, psi, slot);
+        a.tm_prev = tbr_maps_for(p, (int)i, 1, psi, slot);
         if (p->timing) {
             if (p->ev_used + 2 > p->ev_pool.size()) {
                 for (int e = 0; e < 64; ++e) {
@@ -462,7 +479,7 @@ static int enqueue_step_tb(Plan* p, void* psi, cudaStream_t st)
             }
             CHEB_CUDA(cudaEventRecord(p->ev_pool[p->ev_used], st));
         }
-        int rc = p->tb_kernel == CHEB_TB_RUNS ? tbr_launch(p, a, st) : tb_launch(p, a, st);
+        int rc = tb_runs(p->tb_kernel) ? tbr_launch(p, a, st) : tb_launch(p, a, st);
         if (rc) return rc;
         if (p->timing) {
             CHEB_CUDA(cudaEventRecord(p->ev_pool[p->ev_used + 1], st));
@@ -510,10 +527,16 @@ static int ensure_graph(Plan* p, void* psi, Plan::StepGraph** out)
         slot->exec = nullptr;
     }
     cudaGraph_t g = nullptr;
+    // psi's tensor maps for this graph slot, ordered on the plan's stream before any replay
+    const int gslot = (int)(slot - p->graphs);
+    int rc0 = tbr_maps_psi(p, psi, gslot, p->stream);
+    if (rc0) return rc0;
+    p->tm_psi_slot = gslot;
     CHEB_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
     const int64_t before = p->launches;
     int rc = enqueue_step(p, psi, p->cap_stream);
     cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+    p->tm_psi_slot = Plan::kGraphSlots;
     const int64_t captured = p->launches - before;
     p->launches = before;  // captured launches are counted when the graph is replayed
     if (rc) {
@@ -549,7 +572,7 @@ static void free_plan(Plan* p)
         if (t.d_tiles) cudaFree(t.d_tiles);
         if (t.d_begin) cudaFree(t.d_begin);
     }
-    for (void* q : {p->d_C, p->d_D, p->d_E, (void*)p->d_tb_partials, p->adj_ws})
+    for (void* q : {p->d_C, p->d_D, p->d_E, (void*)p->d_tb_partials, p->adj_ws, p->d_tmaps})
         if (q) cudaFree(q);
     if (p->adj_graph) cudaGraphExecDestroy(p->adj_graph);
     void* ptrs[] = {p->d_blocks, p->d_items, p->d_block_item_begin, p->d_diag, p->d_A, p->d_B,
@@ -1244,13 +1267,15 @@ extern "C" int cheb_autotune(cheb_plan* plan)
                                  {CHEB_TB_RUNS, 3, 768}, {CHEB_TB_RUNS, 3, 512},
                                  {CHEB_TB_RUNS, 5, 512}, {CHEB_TB_RUNS, 7, 384},
                                  {CHEB_TB_RUNS, 9, 256},
-                                 {CHEB_TB_RUNS, 3, 1024}, {CHEB_TB_RUNS, 7, 512}};
+                                 {CHEB_TB_RUNS, 3, 1024}, {CHEB_TB_RUNS, 7, 512},
+                                 {CHEB_TB_RUNS_TMA, 5, 512}, {CHEB_TB_RUNS_TMA, 7, 384},
+                                 {CHEB_TB_RUNS_TMA, 9, 256}};
         for (const auto& sh : shapes) {
             if (rc) break;
             const int kern = sh[0], spt = sh[1], tpb = sh[2];
-            if (kern == CHEB_TB_RUNS ? !tbr_supported(p->nvec, spt, tpb)
-                                     : !tb_supported(p->nvec, spt, tpb))
+            if (tb_runs(kern) ? !tbr_supported(p->nvec, spt, tpb) : !tb_supported(p->nvec, spt, tpb))
                 continue;
+            if (kern == CHEB_TB_RUNS_TMA && (p->nvec < 2 || !tbr_tma_available())) continue;
             for (int s_try : {2, 3, 4, 5, 6, 7, 8, 10, 12}) {
                 p->tb_s = s_try;
                 p->tb_spt = spt;
@@ -1365,7 +1390,7 @@ extern "C" int cheb_plan_step_model(const cheb_plan* plan, cheb_step_model* out)
             std::vector<int32_t> begin;
             if (!tb_build_tiles(p, p->tb_sets[L.set].s, tiles, begin))
                 return fail(CHEB_ERR_STATE, "cheb_plan_step_model: tiles");
-            if (p->tb_kernel == CHEB_TB_RUNS) tbr_model_launch(p, tiles, L.ka, L.kb, L.prev_ka, m);
+            if (tb_runs(p->tb_kernel)) tbr_model_launch(p, tiles, L.ka, L.kb, L.prev_ka, m);
             else tb_model_launch(p, tiles, L.ka, L.kb, L.prev_ka, m);
             dram += tb_launch_bytes(p, L);
         }
@@ -1404,7 +1429,8 @@ extern "C" int cheb_tb_tiles(int W, int L, int orders_per_launch, int region_sit
 }
 
 extern "C" int cheb_tb_tiles_padded(int W, int L, int orders_per_launch, int region_positions,
-                                    int align, int32_t* out, int64_t capacity, int64_t* ntiles)
+                                    int align, int boxes, int32_t* out, int64_t capacity,
+                                    int64_t* ntiles)
 {
     if (!ntiles) return fail(CHEB_ERR_INVALID, "cheb_tb_tiles_padded: NULL count");
     if (W < 1 || L < 1 || orders_per_launch < 1 || region_positions < 2 || (align != 4 && align != 8))
@@ -1412,13 +1438,13 @@ extern "C" int cheb_tb_tiles_padded(int W, int L, int orders_per_launch, int reg
                                       "region_positions >= 2, align 4 or 8");
     if (capacity > 0 && !out) return fail(CHEB_ERR_INVALID, "cheb_tb_tiles_padded: NULL out");
     std::vector<TBTile> tiles;
-    if (!tb_tiles_of_ribbon(W, L, orders_per_launch, region_positions, 0, tiles, align))
+    if (!tb_tiles_of_ribbon(W, L, orders_per_launch, region_positions, 0, tiles, align, boxes != 0))
         return fail(CHEB_ERR_INVALID, "cheb_tb_tiles_padded: the ribbon does not fit the region budget");
     *ntiles = (int64_t)tiles.size();
     for (size_t i = 0; i < tiles.size() && (int64_t)i < capacity; ++i) {
         const TBTile& t = tiles[i];
-        const int32_t v[8] = {t.R0, t.R1, t.C0, t.C1, t.r0, t.r1, t.c0, t.c1};
-        std::memcpy(out + 8 * i, v, sizeof(v));
+        const int32_t v[10] = {t.R0, t.R1, t.C0, t.C1, t.r0, t.r1, t.c0, t.c1, t.S, t.BH};
+        std::memcpy(out + 10 * i, v, sizeof(v));
     }
     return CHEB_OK;
 }
@@ -1525,14 +1551,17 @@ extern "C" int cheb_plan_set_blocking_kernel(cheb_plan* plan, int s, int spt, in
     Plan* p = reinterpret_cast<Plan*>(plan);
     if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
     if (s < 0 || s > 16) return fail(CHEB_ERR_INVALID, "orders_per_launch must be in [0, 16]");
-    if (kernel != CHEB_TB_SITES && kernel != CHEB_TB_RUNS)
-        return fail(CHEB_ERR_INVALID, "blocked kernel must be CHEB_TB_SITES or CHEB_TB_RUNS");
+    if (kernel != CHEB_TB_SITES && kernel != CHEB_TB_RUNS && kernel != CHEB_TB_RUNS_TMA)
+        return fail(CHEB_ERR_INVALID,
+                    "blocked kernel must be CHEB_TB_SITES, CHEB_TB_RUNS or CHEB_TB_RUNS_TMA");
     if (s > 0 && !tb_eligible(p))
         return fail(CHEB_ERR_UNSUPPORTED, "temporal blocking needs a complex64 lattice plan with "
                                           "nvec 1, 2 or 4 and a shared on-site array");
+    if (s > 0 && kernel == CHEB_TB_RUNS_TMA && p->nvec < 2)
+        return fail(CHEB_ERR_UNSUPPORTED, "CHEB_TB_RUNS_TMA needs pairs of vectors (nvec 2 or 4)");
     if (threads == 0) threads = 256;
-    const bool ok = kernel == CHEB_TB_RUNS ? tbr_supported(p->nvec, spt, threads)
-                                           : tb_supported(p->nvec, spt, threads);
+    const bool ok = tb_runs(kernel) ? tbr_supported(p->nvec, spt, threads)
+                                    : tb_supported(p->nvec, spt, threads);
     if (s > 0 && !ok)
         return fail(CHEB_ERR_INVALID, "temporal blocking: this (nvec, sites_per_thread, threads) "
                                       "shape is not compiled");

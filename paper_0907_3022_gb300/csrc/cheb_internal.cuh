@@ -119,6 +119,10 @@ struct TBTile {
     int32_t block;
     int32_t R0, R1, C0, C1;  // region (ribbon rows/columns, half-open)
     int32_t r0, r1, c0, c1;  // interior
+    // register-run kernel: the row stride of the ribbon's regions in shared memory (the same
+    // for every tile of the ribbon), the most region rows of its tiles, and whether the
+    // ribbon's inputs are copied by tensor-memory-access boxes of S x BH (1) or per thread (0)
+    int32_t S, BH, tma;
 };
 
 struct TBArgs {
@@ -144,6 +148,10 @@ struct TBArgs {
     const int32_t* block_tile_begin;
     const double* norm2;
     int* errflag;
+    // register-run kernel: tensor maps [block * pairs + pair] of T_{ka-1} and T_{ka-2} for
+    // the ribbons whose tiles are copied by boxes (NULL: per-thread copies)
+    const void* tm_cur;
+    const void* tm_prev;
 };
 
 struct TBSet {
@@ -151,6 +159,7 @@ struct TBSet {
     TBTile* d_tiles = nullptr;
     int32_t* d_begin = nullptr;
     int ntiles = 0;
+    std::vector<TBTile> first;  // host: the first tile of every ribbon (stride, box, tma flag)
 };
 
 struct Plan;
@@ -163,16 +172,22 @@ int tb_configure(int nv, int spt, int tpb);
 bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vector<int32_t>& begin);
 // the tiles of one W x L ribbon for s orders per launch and rmax region sites per CTA
 // (appended to tiles); false if one interior column does not fit
-// align > 0: padded rows of the register-run kernel (stride a multiple of align, >= 1 pad)
+// align > 0: padded rows of the register-run kernel (stride a multiple of align, >= 1 pad);
+// uniform: one stride and box height for all tiles of the ribbon (tensor-memory-access boxes)
 bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TBTile>& tiles,
-                        int align = 0);
+                        int align = 0, bool uniform = false);
 // host work model of one blocked launch over the given tiles (cheb_plan_step_model)
 struct TBModel {
     double useful = 0.0, computed = 0.0, smem = 0.0, l2 = 0.0;
 };
 void tb_model_launch(const Plan* p, const std::vector<TBTile>& tiles, int ka, int kb,
                      int prev_ka, TBModel& m);
-// temporal blocking with register-resident runs (cheb_tbr.cu)
+// temporal blocking with register-resident runs (cheb_tbr.cu), with or without boxes
+inline bool tb_runs(int kernel) { return kernel == CHEB_TB_RUNS || kernel == CHEB_TB_RUNS_TMA; }
+bool tbr_tma_available();
+int tbr_maps_prepare(Plan* p);                               // maps of the internal buffers
+int tbr_maps_psi(Plan* p, const void* psi, int slot, cudaStream_t s);  // psi maps into a slot
+const void* tbr_maps_for(const Plan* p, int launch, int which, const void* psi, int slot);
 bool tbr_supported(int nv, int run, int tpb);
 size_t tbr_smem_bytes(int nv, int run, int tpb);
 int tbr_configure(int nv, int run, int tpb);
@@ -309,7 +324,7 @@ struct Plan {
     int cluster = 0;          // CTAs of the cluster running whole steps (small 1D grids); 0: off
     int tb_spt = 4;           // sites per thread (CHEB_TB_RUNS: the run length)
     int tb_tpb = 256;         // threads per CTA of the blocked kernel
-    int tb_kernel = CHEB_TB_SITES;  // blocked kernel: strided sites or register runs
+    int tb_kernel = CHEB_TB_SITES;  // blocked kernel: strided sites or register runs (+ boxes)
     int tb_grid_cap = 0;
     void* d_C = nullptr;      // second recurrence pair and the main accumulator
     void* d_D = nullptr;
@@ -319,6 +334,18 @@ struct Plan {
         int ka, kb, prev_ka, set;
     };
     std::vector<TBLaunch> tb_sched;   // launches of one step (rebuilt with dt / tb_s)
+    // tensor maps of the register-run kernel (cheb_tbr.cu): per launch of the schedule the maps
+    // of its T_{ka-1} and T_{ka-2} buffers, then kGraphSlots + 1 slots for psi (the graph slots,
+    // then the slot of launches enqueued outside a capture); each map array holds
+    // nblocks * pairs maps.  tm_psi_slot: the psi slot a capture in progress uses.
+    void* d_tmaps = nullptr;
+    size_t tmaps_cap = 0;
+    size_t tmap_array = 0;            // bytes of one map array
+    struct TMPsi {
+        const void* psi = nullptr;
+        int64_t epoch = -1;
+    } tm_psi[kGraphSlots + 1];
+    int tm_psi_slot = kGraphSlots;
     double* d_tb_partials = nullptr;
     size_t tb_partials_cap = 0;
 

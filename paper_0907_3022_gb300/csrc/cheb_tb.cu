@@ -516,8 +516,8 @@ int tb_launch(Plan* p, const TBArgs& a, cudaStream_t s)
 }
 
 // Widest region row that fits rmax positions with rh rows: rmax / rh sites per row, or with
-// padded rows (align > 0; the register-run kernel) one leading zero position and a row stride
-// that is a multiple of align and leaves at least one zero pad after every row.
+// padded rows (align > 0; the register-run kernel) a row stride that is a multiple of align
+// and leaves at least one zero pad after every row, with one position to spare.
 static int tb_width_cap(int rmax, int rh, int align)
 {
     if (align <= 0) return rmax / rh;
@@ -528,7 +528,7 @@ static int tb_width_cap(int rmax, int rh, int align)
 // columns as the region budget (rmax positions: threads * sites per thread) allows.  Returns
 // false if a ribbon cannot be tiled (the region of one interior column would not fit).
 bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TBTile>& tiles,
-                        int align)
+                        int align, bool uniform)
 {
     // halo widths for s orders: s columns, but only ceil(s / 2) rows, since d rows away is at
     // least 2d - 1 bonds on the brick wall (the kernel's validity distance counts the same way)
@@ -552,11 +552,15 @@ bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TB
     }
     if (best_nbr < 0) return false;
     const int tr = (W + best_nbr - 1) / best_nbr;
+    // padded regions for boxes: every band takes its width from the tallest band's height, so
+    // that one row stride and one box of (stride x tallest rows) fit every tile of the ribbon
+    const int rh_max = std::min(W, tr + (best_nbr > 1 ? 2 * hr : 0));
+    const size_t first_tile = tiles.size();
     for (int r0 = 0; r0 < W; r0 += tr) {
         const int r1 = std::min(W, r0 + tr);
         const int R0 = std::max(0, r0 - hr), R1 = std::min(W, r1 + hr);
         const int rh = R1 - R0;
-        int tc = tb_width_cap(rmax, rh, align);
+        int tc = tb_width_cap(rmax, uniform ? rh_max : rh, align);
         if (tc < L) tc -= 2 * s;  // halo on both column sides
         if (tc < 1) return false;
         const int nbc = (L + tc - 1) / tc;
@@ -574,9 +578,24 @@ bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TB
             t.c0 = c0;
             t.c1 = c1;
             const int64_t RW = t.C1 - t.C0, RH = t.R1 - t.R0;
-            const int64_t used = align > 0 ? 1 + RH * ((RW + align) & ~(int64_t)(align - 1)) : RH * RW;
+            const int64_t S = align > 0 ? (RW + align) & ~(int64_t)(align - 1) : RW;
+            const int64_t used = align > 0 ? 1 + RH * S : RH * RW;
             if (RW < 1 || used > rmax) return false;
+            t.S = (int32_t)S;
+            t.BH = (int32_t)RH;
             tiles.push_back(t);
+        }
+    }
+    if (align > 0 && uniform) {  // the ribbon's common stride and box height
+        int S = 0, BH = 0;
+        for (size_t i = first_tile; i < tiles.size(); ++i) {
+            S = std::max(S, (tiles[i].C1 - tiles[i].C0 + align) & ~(align - 1));
+            BH = std::max(BH, tiles[i].R1 - tiles[i].R0);
+        }
+        if (1 + (int64_t)BH * S > rmax) return false;
+        for (size_t i = first_tile; i < tiles.size(); ++i) {
+            tiles[i].S = S;
+            tiles[i].BH = BH;
         }
     }
     return true;
@@ -585,13 +604,21 @@ bool tb_tiles_of_ribbon(int W, int L, int s, int rmax, int block, std::vector<TB
 bool tb_build_tiles(const Plan* p, int s, std::vector<TBTile>& tiles, std::vector<int32_t>& begin)
 {
     const int rmax = p->tb_tpb * p->tb_spt;
-    const int align = p->tb_kernel == CHEB_TB_RUNS ? (p->nvec >= 2 ? 4 : 8) : 0;
+    const bool runs = p->tb_kernel == CHEB_TB_RUNS || p->tb_kernel == CHEB_TB_RUNS_TMA;
+    const bool boxes_wanted = p->tb_kernel == CHEB_TB_RUNS_TMA && p->nvec >= 2;
+    const int align = runs ? (p->nvec >= 2 ? 4 : 8) : 0;
     tiles.clear();
     begin.assign(p->nblocks + 1, 0);
     for (int q = 0; q < p->nblocks; ++q) {
         begin[q] = (int32_t)tiles.size();
         const DevBlock& B = p->hblocks[q];
-        if (!tb_tiles_of_ribbon(B.W, B.L, s, rmax, q, tiles, align)) return false;
+        const size_t t0 = tiles.size();
+        if (!tb_tiles_of_ribbon(B.W, B.L, s, rmax, q, tiles, align, boxes_wanted)) return false;
+        // register-run kernel with boxes, pairs of vectors: boxes of (stride x rows) up to
+        // 256 x 256
+        const bool boxes = boxes_wanted && tiles[t0].S <= 256 && tiles[t0].BH <= 256 &&
+                           tbr_tma_available();
+        for (size_t i = t0; i < tiles.size(); ++i) tiles[i].tma = boxes ? 1 : 0;
     }
     begin[p->nblocks] = (int32_t)tiles.size();
     return true;

@@ -13,13 +13,15 @@
 //   and the two neighbours beyond the run's ends, and stores each site's T_k once (the
 //   neighbours of the next order read it).  Only T_{k-1} has a shared-memory plane (two planes,
 //   read one / write the other).
-// * Layout of a plane: position 0 is a zero element, site (rr, cc) of the RH x RW region is at
-//   1 + rr S + cc, S = the smallest multiple of A (4 for float4, 8 for float2) that is >= RW + 1,
-//   and the S - RW >= 1 positions after every row are zero pads; one more zero element follows
-//   the last position.  The pads make the neighbour left of column 0 and right of column RW - 1
-//   a zero read, which is the ribbon's open edge where the region ends at the ribbon border (where
+// * Layout of a plane: site (rr, cc) of the RH x RW region is at position rr S + cc, where the
+//   row stride S is the same for every tile of a ribbon (the tile builder takes the widest
+//   region row + 1 rounded up to A = 4 for float4, 8 for float2), so that the S - RW >= 1
+//   positions after every row are zero pads; one zero element follows the last position (index
+//   NPOS = RUN TPB).  The pads make the neighbour left of column 0 and right of column RW - 1 a
+//   zero read, which is the ribbon's open edge where the region ends at the ribbon border (where
 //   it ends at an open side the site is outside the validity limit and its value unused).  A
-//   vertical neighbour outside the region or the ribbon reads position 0.
+//   vertical neighbour outside the region or the ribbon, and the left neighbour of position 0,
+//   read the element at NPOS.
 // * Bank conflicts: with RUN odd, the lanes of a quarter warp (float4) or half warp (float2)
 //   address distinct bank groups for the same j; with S a multiple of A, the up and down
 //   neighbours (+-S) of any two lanes still do.
@@ -28,15 +30,22 @@
 //   the order loop (both planes are zeroed at every tile start, so every value read is finite).
 //   The accumulation runs for every position and only interior sites are written out, and the
 //   parity of the order, which decides how (-i)^k enters, is a compile-time constant.
-// * Each thread copies the inputs of its positions of the next work item (T_{ka-1}, T_{ka-2},
-//   d and the accumulator) into staging buffers with cp.async while the current item runs its
-//   orders, so the global-memory latency of a tile start is hidden.
+// * The inputs of the next work item (T_{ka-1}, T_{ka-2}, d and the accumulator) stream into
+//   staging buffers while the current item runs its orders, so the global-memory latency of a
+//   tile start is hidden.  With pairs of vectors, T_{ka-1} and T_{ka-2} come as two tensor-memory-
+//   access boxes of S x BH elements (BH = the ribbon's tallest region) whose shared-memory image
+//   is exactly the plane layout above (box row rr, column cc at rr S + cc; columns and rows beyond
+//   the ribbon read as zero); d, the accumulator and single-vector planes are copied per thread
+//   with cp.async, each thread its own positions.
 //
 // Per formed site-order and plane element: one vertical load, 2 / RUN run-end loads, one store
 // (k_rec_tb: own, three neighbours, T_{k-2} and the store).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "cheb_internal.cuh"
@@ -52,17 +61,6 @@ template <> struct TBRPlane<float2> {
     static constexpr int A = 8;
     static constexpr int PER = 1;
 };
-
-__host__ __device__ constexpr size_t tbr_smem(int elem_bytes, int run, int tpb)
-{
-    return 2 * ((size_t)run * tpb + 1) * (size_t)elem_bytes;
-}
-
-// padded row stride for a region row of RW sites (align 4 or 8)
-__host__ __device__ __forceinline__ int tbr_stride(int RW, int align)
-{
-    return (RW + align) & ~(align - 1);
-}
 
 // same validity limit as k_rec_tb (cheb_tb.cu)
 __host__ __device__ __forceinline__ int tbr_limit(int rr, int cc, int RH, int RW, bool up,
@@ -171,6 +169,54 @@ __device__ __forceinline__ void tbr_cp(float2* sdst, const float2* gsrc) { tbr_c
 __device__ __forceinline__ void tbr_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void tbr_cp_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Tensor-memory-access copies of a tile's T_{ka-1} / T_{ka-2}: one 3-D box (16-byte element,
+// S columns, BH rows) per buffer from the ribbon's tensor map, issued by one thread against
+// an mbarrier that expects the boxes' bytes; every thread waits on the barrier's phase before
+// reading the staging buffers.  Waits are bounded: a wait that gives up raises bit 2 of the
+// error flag (never expected: the copies always complete).
+static constexpr int TBR_WAIT_TRIES = 1 << 22;
+
+__device__ __forceinline__ unsigned tbr_smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void tbr_mbar_init(uint64_t* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tbr_smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void tbr_mbar_expect(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tbr_smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool tbr_mbar_wait(uint64_t* bar, unsigned parity)
+{
+    for (int i = 0; i < TBR_WAIT_TRIES; ++i) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done)
+                     : "r"(tbr_smem_u32(bar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tbr_tma_box(void* sdst, const void* tmap, int c0, int c1, int c2,
+                                            uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(tbr_smem_u32(sdst)),
+                 "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2),
+                 "r"(tbr_smem_u32(bar))
+                 : "memory");
+}
+// generic-proxy accesses of the staging buffers (the previous tile's reads, ordered by a CTA
+// barrier) before the async-proxy writes of the next boxes
+__device__ __forceinline__ void tbr_fence_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
 // Geometry of a work item (tile ti, plane element pr) as a thread sees it.
 struct TBRTile {
     TBTile T;
@@ -182,9 +228,11 @@ struct TBRTile {
 };
 
 // Descriptors of a work item staged in shared memory one item ahead: the ribbon's DevBlock
-// (18 words, 8-byte aligned at word 0) and the tile (9 words); thread tid < 27 loads word tid.
-constexpr int TBR_META_WORDS = 28;
-static_assert(sizeof(DevBlock) == 18 * 4 && sizeof(TBTile) == 9 * 4, "descriptor words");
+// (18 words, 8-byte aligned at word 0) and the tile (12 words); thread tid < 30 loads word
+// tid.
+constexpr int TBR_META_WORDS = 32;
+constexpr int TBR_META_USED = 30;  // DevBlock (18 words) then TBTile (12 words)
+static_assert(sizeof(DevBlock) == 18 * 4 && sizeof(TBTile) == 12 * 4, "descriptor words");
 
 __device__ __forceinline__ int tbr_meta_load(const TBArgs& a, int w, int npairs, int tid)
 {
@@ -193,7 +241,7 @@ __device__ __forceinline__ int tbr_meta_load(const TBArgs& a, int w, int npairs,
     return reinterpret_cast<const int*>(a.tiles + ti)[tid - 18];
 }
 
-__device__ __forceinline__ TBRTile tbr_tile(const int* meta, int w, int ka, int npairs, int align)
+__device__ __forceinline__ TBRTile tbr_tile(const int* meta, int w, int ka, int npairs)
 {
     TBRTile t;
     const int ti = w / npairs;
@@ -201,32 +249,26 @@ __device__ __forceinline__ TBRTile tbr_tile(const int* meta, int w, int ka, int 
     t.B = *reinterpret_cast<const DevBlock*>(meta);
     t.T = *reinterpret_cast<const TBTile*>(meta + 18);
     t.live = ka <= t.B.M;
-    t.S = tbr_stride(t.T.C1 - t.T.C0, align);
+    t.S = t.T.S;  // the ribbon's common stride (tile builder)
     t.invS = ((1ull << 32) + (unsigned)t.S - 1u) / (unsigned)t.S;
     return t;
 }
 
 // Walk over a thread's consecutive positions e0, e0 + 1, ...: region row rr and column cc of
-// position e (site (rr, cc) is at e = 1 + rr S + cc) and the ribbon-relative site index
+// position e (site (rr, cc) is at e = rr S + cc) and the ribbon-relative site index
 // rg = (R0 + rr) L + C0 + cc, advanced incrementally (one division per run, at its start).
-// Position 0 (the zero element) starts at column -1; columns RW .. S - 1 are pads.
+// Columns RW .. S - 1 are pads.
 struct TBRWalk {
     int rr, cc, rg;
     __device__ __forceinline__ TBRWalk(const TBRTile& t, int e0)
     {
-        const int q = e0 - 1;
-        if (q < 0) {
-            rr = 0;
-            cc = -1;
-        } else {
-            rr = (int)(((unsigned long long)q * t.invS) >> 32);
-            cc = q - rr * t.S;
-        }
+        rr = (int)(((unsigned long long)e0 * t.invS) >> 32);
+        cc = e0 - rr * t.S;
         rg = (t.T.R0 + rr) * t.B.L + t.T.C0 + cc;
     }
     __device__ __forceinline__ bool site(const TBRTile& t) const
     {
-        return cc >= 0 && cc < t.T.C1 - t.T.C0 && rr < t.T.R1 - t.T.R0;
+        return cc < t.T.C1 - t.T.C0 && rr < t.T.R1 - t.T.R0;
     }
     __device__ __forceinline__ bool interior(const TBRTile& t) const
     {
@@ -248,11 +290,31 @@ struct TBRWalk {
 // Issue the copies of a work item's inputs for this thread's positions: T_{ka-1}, T_{ka-2}
 // (not in the first launch), d, and for interior sites the accumulator the launch continues
 // (E, or the tail when only the tail is read; when both are read the tail is loaded directly).
-template <typename PT, int RUN, bool FIRST>
-__device__ __forceinline__ void tbr_fetch(const TBArgs& a, const TBRTile& t, int e0, int npairs,
-                                          PT* stX, PT* stP, PT* stA, float* stD)
+template <typename PT, int RUN, bool FIRST, bool BOX>
+__device__ __forceinline__ bool tbr_fetch(const TBArgs& a, const TBRTile& t, int e0, int npairs,
+                                          PT* stX, PT* stP, PT* stA, float* stD, uint64_t* bar,
+                                          bool box_ok)
 {
-    if (!t.live) return;
+    if (!t.live) return false;
+    // boxes (kernel variant BOX, pairs of vectors) where the ribbon has tensor maps for this
+    // launch's buffers and the staging buffers sit on 128-byte boundaries
+    bool boxX = false, boxP = false;
+    if constexpr (BOX) {
+        const int mi = t.T.block * npairs + t.pr;
+        boxX = box_ok && t.T.tma && a.tm_cur;
+        boxP = box_ok && !FIRST && t.T.tma && a.tm_prev;
+        if ((boxX || boxP) && threadIdx.x == 0) {
+            tbr_fence_async();
+            const unsigned box = (unsigned)t.S * (unsigned)t.T.BH * 16u;
+            tbr_mbar_expect(bar, box * ((boxX ? 1u : 0u) + (boxP ? 1u : 0u)));
+            if (boxX)
+                tbr_tma_box(stX, static_cast<const CUtensorMap*>(a.tm_cur) + mi, 0, t.T.C0, t.T.R0,
+                            bar);
+            if (boxP)
+                tbr_tma_box(stP, static_cast<const CUtensorMap*>(a.tm_prev) + mi, 0, t.T.C0,
+                            t.T.R0, bar);
+        }
+    }
     const PT* in_prev = static_cast<const PT*>(a.in_prev);
     const PT* in_cur = static_cast<const PT*>(a.in_cur);
     const PT* accE = static_cast<const PT*>(a.acc_main);
@@ -270,14 +332,15 @@ __device__ __forceinline__ void tbr_fetch(const TBArgs& a, const TBRTile& t, int
     for (int j = 0; j < RUN; ++j) {
         if (wk.site(t)) {
             const int64_t gi = base + (int64_t)wk.rg * npairs;
-            tbr_cp(stX + e0 + j, in_cur + gi);
-            if (!FIRST) tbr_cp(stP + e0 + j, in_prev + gi);
+            if (!boxX) tbr_cp(stX + e0 + j, in_cur + gi);
+            if (!FIRST && !boxP) tbr_cp(stP + e0 + j, in_prev + gi);
             tbr_cp4(stD + e0 + j, diag + t.B.offset + wk.rg);
             if ((read_e || read_t) && wk.interior(t)) tbr_cp(stA + e0 + j, accsrc + gi);
         }
         wk.next(t);
     }
     tbr_cp_commit();
+    return boxX || boxP;
 }
 
 // One order k of parity ODD for the thread's run: dst <- 2 H~ src - dst at every position
@@ -289,7 +352,7 @@ template <typename PT, int RUN, bool FIRST, bool ODD>
 __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restrict__ Pw,
                                           const PT (&src)[RUN], PT (&dst)[RUN],
                                           const float (&d)[RUN], const float (&bh)[RUN],
-                                          const int (&vidx)[RUN],
+                                          const int (&vidx)[RUN], int zpos,
                                           unsigned interm, int e0, bool active, float2 qk, int k,
                                           float2 (&acc)[RUN][TBRPlane<PT>::PER],
                                           float (&part)[FIRST ? 2 * TBRPlane<PT>::PER : 1])
@@ -299,7 +362,7 @@ __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restr
         PT V[RUN];
 #pragma unroll
         for (int j = 0; j < RUN; ++j) V[j] = Qr[vidx[j]];
-        const PT Lf = Qr[e0 > 0 ? e0 - 1 : 0];
+        const PT Lf = Qr[e0 > 0 ? e0 - 1 : zpos];
         const PT Rt = Qr[e0 + RUN];
 #pragma unroll
         for (int j = 0; j < RUN; ++j) {
@@ -330,7 +393,7 @@ __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restr
 template <typename PT, int RUN, bool FIRST, bool P0>
 __device__ __forceinline__ void tbr_orders(PT* plane0, PT* plane1, PT (&X)[RUN], PT (&P)[RUN],
                                            const float (&d)[RUN], const float (&bh)[RUN],
-                                           const int (&vidx)[RUN],
+                                           const int (&vidx)[RUN], int zpos,
                                            unsigned interm, int e0, int rl, int ka, int ke,
                                            const float2* __restrict__ qc,
                                            float2 (&acc)[RUN][TBRPlane<PT>::PER],
@@ -341,41 +404,54 @@ __device__ __forceinline__ void tbr_orders(PT* plane0, PT* plane1, PT (&X)[RUN],
     for (;;) {
         float2 qk = qn;
         if (k < ke) qn = qc[k + 1];
-        tbr_order<PT, RUN, FIRST, P0>(plane0, plane1, X, P, d, bh, vidx, interm, e0,
+        tbr_order<PT, RUN, FIRST, P0>(plane0, plane1, X, P, d, bh, vidx, zpos, interm, e0,
                                       rl >= k - ka + 1, qk, k, acc, part);
         if (k == ke) break;
         ++k;
         qk = qn;
         if (k < ke) qn = qc[k + 1];
-        tbr_order<PT, RUN, FIRST, !P0>(plane1, plane0, P, X, d, bh, vidx, interm, e0,
+        tbr_order<PT, RUN, FIRST, !P0>(plane1, plane0, P, X, d, bh, vidx, zpos, interm, e0,
                                        rl >= k - ka + 1, qk, k, acc, part);
         if (k == ke) break;
         ++k;
     }
 }
 
+// Dynamic shared memory: two planes of NPOS + 1 elements (positions and the trailing zero),
+// staging for T_{ka-1}, T_{ka-2}, the accumulator and d of the next tile; each part starts on a
+// 128-byte boundary (the boxes' destinations).
+template <typename PT, int RUN, int TPB> struct TBRLayout {
+    static constexpr size_t NPOS = (size_t)RUN * TPB, E = sizeof(PT);
+    static constexpr size_t up(size_t x) { return (x + 127) & ~(size_t)127; }
+    static constexpr size_t plane1 = up((NPOS + 1) * E);
+    static constexpr size_t stX = up(plane1 + (NPOS + 1) * E);
+    static constexpr size_t stP = up(stX + NPOS * E);
+    static constexpr size_t stA = up(stP + NPOS * E);
+    static constexpr size_t stD = up(stA + NPOS * E);
+    static constexpr size_t bytes = stD + NPOS * sizeof(float);
+};
 template <typename PT, int RUN, int TPB>
 __host__ __device__ constexpr size_t tbr_smem_layout()
 {
-    // two planes of NPOS + 1, staging for T_{ka-1}, T_{ka-2}, the accumulator, and d
-    return (2 * ((size_t)RUN * TPB + 1) + 3 * (size_t)RUN * TPB) * sizeof(PT) +
-           (size_t)RUN * TPB * sizeof(float);
+    return TBRLayout<PT, RUN, TPB>::bytes;
 }
 
-template <typename PT, int RUN, int TPB, bool FIRST>
+template <typename PT, int RUN, int TPB, bool FIRST, bool BOX>
 __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
 {
+    static_assert(!BOX || sizeof(PT) == 16, "boxes carry pairs of vectors");
     constexpr int PER = TBRPlane<PT>::PER;
-    constexpr int ALIGN = TBRPlane<PT>::A;
     constexpr int NPOS = RUN * TPB;
-    constexpr int PS = NPOS + 1;  // plane size: positions and the trailing zero
-    extern __shared__ float4 tbr_smem_raw[];
+    using LY = TBRLayout<PT, RUN, TPB>;
+    extern __shared__ __align__(128) unsigned char tbr_smem_raw[];
     PT* const plane0 = reinterpret_cast<PT*>(tbr_smem_raw);
-    PT* const plane1 = plane0 + PS;
-    PT* const stX = plane1 + PS;
-    PT* const stP = stX + NPOS;
-    PT* const stA = stP + NPOS;
-    float* const stD = reinterpret_cast<float*>(stA + NPOS);
+    PT* const plane1 = reinterpret_cast<PT*>(tbr_smem_raw + LY::plane1);
+    PT* const stX = reinterpret_cast<PT*>(tbr_smem_raw + LY::stX);
+    PT* const stP = reinterpret_cast<PT*>(tbr_smem_raw + LY::stP);
+    PT* const stA = reinterpret_cast<PT*>(tbr_smem_raw + LY::stA);
+    float* const stD = reinterpret_cast<float*>(tbr_smem_raw + LY::stD);
+    // the boxes' destinations must start on 128-byte boundaries (else per-thread copies)
+    const bool box_ok = (tbr_smem_u32(tbr_smem_raw) & 127u) == 0u;
     __shared__ double s_red[(TPB / 32) * 2 * PER];
     const PT zero = tbr_zero((PT*)nullptr);
     const int tid = threadIdx.x;
@@ -389,27 +465,31 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
     PT* __restrict__ tail = static_cast<PT*>(a.tail);
     PT* __restrict__ psi = static_cast<PT*>(a.psi);
     const float2* __restrict__ qc = static_cast<const float2*>(a.qcoef);
+    __shared__ __align__(8) uint64_t s_bar;  // completion of the next tile's boxes
+    unsigned bar_parity = 0;                  // parity of the next phase to wait for
     if (tid == 0) {
         plane0[NPOS] = zero;
         plane1[NPOS] = zero;
+        if constexpr (BOX) tbr_mbar_init(&s_bar);
     }
 
     __shared__ __align__(16) int s_meta[2][TBR_META_WORDS];  // descriptors of items it, it + 1
     const int nwork = a.ntiles * npairs;
     int w = blockIdx.x;
     const bool any = w < nwork;  // a CTA without an item still counts in the finalize below
-    if (any && tid < 27) s_meta[0][tid] = tbr_meta_load(a, w, npairs, tid);
+    if (any && tid < TBR_META_USED) s_meta[0][tid] = tbr_meta_load(a, w, npairs, tid);
     __syncthreads();
     TBRTile t;
+    bool boxed = false;  // the fetched item's inputs come (partly) by boxes
     if (any) {
-        t = tbr_tile(s_meta[0], w, a.ka, npairs, ALIGN);
-        tbr_fetch<PT, RUN, FIRST>(a, t, e0, npairs, stX, stP, stA, stD);
+        t = tbr_tile(s_meta[0], w, a.ka, npairs);
+        boxed = tbr_fetch<PT, RUN, FIRST, BOX>(a, t, e0, npairs, stX, stP, stA, stD, &s_bar, box_ok);
     }
     for (int it = 0; w < nwork; w += gridDim.x, ++it) {
         // the next item's descriptors: loads in flight during this item's start
         const int wn = w + (int)gridDim.x;
         int meta_word = 0;
-        if (tid < 27 && wn < nwork) meta_word = tbr_meta_load(a, wn, npairs, tid);
+        if (tid < TBR_META_USED && wn < nwork) meta_word = tbr_meta_load(a, wn, npairs, tid);
         float part[FIRST ? 2 * PER : 1];
 #pragma unroll
         for (int q = 0; q < (FIRST ? 2 * PER : 1); ++q) part[q] = 0.f;
@@ -418,6 +498,13 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
         const DevBlock& B = cur.B;
         // this work item's inputs, copied during the previous item's orders
         tbr_cp_wait();
+        if (BOX && boxed) {
+            if (!tbr_mbar_wait(&s_bar, bar_parity)) {
+                atomicOr(a.errflag, 2);
+                tbr_mbar_wait(&s_bar, bar_parity);  // once more for the boxes in flight
+            }
+            bar_parity ^= 1u;
+        }
         PT X[RUN], P[RUN];
         float d[RUN], bh[RUN];
         int vidx[RUN];
@@ -442,14 +529,14 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
                 P[j] = zero;
                 d[j] = 0.f;
                 bh[j] = 0.f;
-                vidx[j] = 0;
+                vidx[j] = NPOS;
                 PT ea = zero;
                 if (wk.site(cur)) {
                     const int r = T.R0 + rr;
                     const bool up = (r + T.C0 + cc) & 1;  // vertical neighbour r - 1 (else r + 1)
                     rl = max(rl, tbr_limit(rr, cc, RH, RW, up, open_t, open_b, open_l, open_r));
-                    vidx[j] = up ? ((rr > 0 && r > 0) ? e - cur.S : 0)
-                                 : ((rr + 1 < RH && r + 1 < B.W) ? e + cur.S : 0);
+                    vidx[j] = up ? ((rr > 0 && r > 0) ? e - cur.S : NPOS)
+                                 : ((rr + 1 < RH && r + 1 < B.W) ? e + cur.S : NPOS);
                     X[j] = stX[e];
                     if (!FIRST) P[j] = stP[e];
                     d[j] = stD[e];
@@ -489,19 +576,20 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
         // plane 0 complete; the barrier also orders this tile's reads of the staging buffers
         // before the copies of the next item below overwrite them, and publishes the next
         // item's descriptors (slot (it + 1) & 1 was last read two items ago)
-        if (tid < 27) s_meta[(it + 1) & 1][tid] = meta_word;
+        if (tid < TBR_META_USED) s_meta[(it + 1) & 1][tid] = meta_word;
         __syncthreads();
         // the next work item's inputs stream in while this one runs its orders
+        boxed = false;
         if (wn < nwork) {
-            t = tbr_tile(s_meta[(it + 1) & 1], wn, a.ka, npairs, ALIGN);
-            tbr_fetch<PT, RUN, FIRST>(a, t, e0, npairs, stX, stP, stA, stD);
+            t = tbr_tile(s_meta[(it + 1) & 1], wn, a.ka, npairs);
+            boxed = tbr_fetch<PT, RUN, FIRST, BOX>(a, t, e0, npairs, stX, stP, stA, stD, &s_bar, box_ok);
         }
         if (cur.live) {
             if (a.ka & 1)
-                tbr_orders<PT, RUN, FIRST, true>(plane0, plane1, X, P, d, bh, vidx, interm, e0,
+                tbr_orders<PT, RUN, FIRST, true>(plane0, plane1, X, P, d, bh, vidx, NPOS, interm, e0,
                                                  rl, a.ka, ke, qc + B.coef_off, acc, part);
             else
-                tbr_orders<PT, RUN, FIRST, false>(plane0, plane1, X, P, d, bh, vidx, interm,
+                tbr_orders<PT, RUN, FIRST, false>(plane0, plane1, X, P, d, bh, vidx, NPOS, interm,
                                                   e0, rl, a.ka, ke, qc + B.coef_off, acc, part);
             // T_ke is in P when ke - ka is even (the last order ran the first half), else in X
             const bool last_in_p = ((ke - a.ka) & 1) == 0;
@@ -626,14 +714,25 @@ size_t tbr_smem_bytes(int nv, int run, int tpb)
     return 0;
 }
 
+// the variant with boxes exists for pairs of vectors only
+template <typename PT> struct TBRBox {
+    static constexpr bool value = sizeof(PT) == 16;
+};
+
 template <typename PT, int RUN, int TPB>
 static int tbr_attr_t()
 {
     const int smem = (int)tbr_smem_layout<PT, RUN, TPB>();
-    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tbr<PT, RUN, TPB, true>,
+    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tbr<PT, RUN, TPB, true, false>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tbr<PT, RUN, TPB, false>,
+    CHEB_CUDA(cudaFuncSetAttribute(k_rec_tbr<PT, RUN, TPB, false, false>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if constexpr (TBRBox<PT>::value) {
+        CHEB_CUDA(cudaFuncSetAttribute(k_rec_tbr<PT, RUN, TPB, true, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        CHEB_CUDA(cudaFuncSetAttribute(k_rec_tbr<PT, RUN, TPB, false, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    }
     return CHEB_OK;
 }
 
@@ -648,11 +747,18 @@ int tbr_configure(int nv, int run, int tpb)
 }
 
 template <typename PT, int RUN, int TPB>
-static void tbr_launch_t(const TBArgs& a, int grid, cudaStream_t s)
+static void tbr_launch_t(const TBArgs& a, int grid, cudaStream_t s, bool box)
 {
     const size_t smem = tbr_smem_layout<PT, RUN, TPB>();
-    if (a.ka == 1) k_rec_tbr<PT, RUN, TPB, true><<<grid, TPB, smem, s>>>(a);
-    else k_rec_tbr<PT, RUN, TPB, false><<<grid, TPB, smem, s>>>(a);
+    if constexpr (TBRBox<PT>::value) {
+        if (box) {
+            if (a.ka == 1) k_rec_tbr<PT, RUN, TPB, true, true><<<grid, TPB, smem, s>>>(a);
+            else k_rec_tbr<PT, RUN, TPB, false, true><<<grid, TPB, smem, s>>>(a);
+            return;
+        }
+    }
+    if (a.ka == 1) k_rec_tbr<PT, RUN, TPB, true, false><<<grid, TPB, smem, s>>>(a);
+    else k_rec_tbr<PT, RUN, TPB, false, false><<<grid, TPB, smem, s>>>(a);
 }
 
 int tbr_launch(Plan* p, const TBArgs& a, cudaStream_t s)
@@ -662,10 +768,12 @@ int tbr_launch(Plan* p, const TBArgs& a, cudaStream_t s)
     if (p->tb_grid_cap > 0 && grid > p->tb_grid_cap) grid = p->tb_grid_cap;
     if (grid < 1) return CHEB_OK;
     const int eb = tbr_elem_bytes(p->nvec), run = p->tb_spt, tpb = p->tb_tpb;
+    // the variant with boxes when some ribbon of this launch has tensor maps
+    const bool box = p->tb_kernel == CHEB_TB_RUNS_TMA && (a.tm_cur || a.tm_prev);
     bool ok = false;
 #define CHEB_TBR_GO(PT, RUN, TPB)                                     \
     if (!ok && (int)sizeof(PT) == eb && run == RUN && tpb == TPB) {   \
-        tbr_launch_t<PT, RUN, TPB>(a, grid, s);                       \
+        tbr_launch_t<PT, RUN, TPB>(a, grid, s, box);                  \
         ok = true;                                                    \
     }
     CHEB_TBR_SHAPES(CHEB_TBR_GO)
@@ -676,12 +784,132 @@ int tbr_launch(Plan* p, const TBArgs& a, cudaStream_t s)
     return CHEB_OK;
 }
 
+// ---- tensor maps (host) ---------------------------------------------------------------------
+// The driver's encoder, looked up once through the runtime (no link to the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tbr_encoder()
+{
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+bool tbr_tma_available() { return tbr_encoder() != nullptr; }
+
+// Maps of one buffer (base: element 0 of the plan's [site][vec] complex64 vector) for the
+// ribbons of a tile set: out[q * pairs + pr] views ribbon q's plane element pr as a 3-D tensor
+// (4 floats, L columns of pairs * 16 bytes, W rows of L pairs * 16 bytes) with a box of
+// (4, S, BH); columns and rows beyond the ribbon read as zero.  Ribbons without boxes keep a
+// zeroed map that the kernel never uses.
+static bool tbr_encode_buffer(const Plan* p, const TBSet& set, const void* base, CUtensorMap* out)
+{
+    const auto enc = tbr_encoder();
+    const int npairs = p->nvec / 2;
+    for (int q = 0; q < p->nblocks; ++q) {
+        const TBTile& t = set.first[(size_t)q];
+        const DevBlock& B = p->hblocks[q];
+        for (int pr = 0; pr < npairs; ++pr) {
+            CUtensorMap& m = out[(size_t)q * npairs + pr];
+            std::memset(&m, 0, sizeof(m));
+            if (!t.tma) continue;
+            char* g = static_cast<char*>(const_cast<void*>(base)) +
+                      ((size_t)B.offset * npairs + pr) * 16;
+            const cuuint64_t dims[3] = {4, (cuuint64_t)B.L, (cuuint64_t)B.W};
+            const cuuint64_t strides[2] = {(cuuint64_t)npairs * 16, (cuuint64_t)B.L * npairs * 16};
+            const cuuint32_t box[3] = {4, (cuuint32_t)t.S, (cuuint32_t)t.BH};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+                CUDA_SUCCESS)
+                return false;
+        }
+    }
+    return true;
+}
+
+static bool tbr_boxes(const Plan* p)
+{
+    return p->tb_kernel == CHEB_TB_RUNS_TMA && p->nvec >= 2 && !p->tb_sched.empty() &&
+           tbr_tma_available();
+}
+
+// Maps of the buffers of launches 1.. of the step (the two recurrence pairs; launch 0 reads
+// psi, whose maps are made per psi pointer); psi slots invalidated.
+int tbr_maps_prepare(Plan* p)
+{
+    for (Plan::TMPsi& t : p->tm_psi) t = Plan::TMPsi{};
+    if (!tbr_boxes(p)) return CHEB_OK;
+    const size_t nmap = (size_t)p->nblocks * (p->nvec / 2);
+    p->tmap_array = nmap * sizeof(CUtensorMap);
+    const size_t narrays = 2 * p->tb_sched.size() + Plan::kGraphSlots + 1;
+    const size_t need = narrays * p->tmap_array;
+    if (p->tmaps_cap < need) {
+        if (p->d_tmaps) cudaFree(p->d_tmaps);
+        p->d_tmaps = nullptr;
+        p->tmaps_cap = 0;
+        if (cudaMalloc(&p->d_tmaps, need) != cudaSuccess) return fail(CHEB_ERR_NOMEM, "tensor maps");
+        p->tmaps_cap = need;
+    }
+    std::vector<CUtensorMap> h(narrays * nmap);
+    std::memset(h.data(), 0, h.size() * sizeof(CUtensorMap));
+    void* pairs[2][2] = {{p->d_A, p->d_B}, {p->d_C, p->d_D}};
+    for (size_t i = 1; i < p->tb_sched.size(); ++i) {
+        const TBSet& set = p->tb_sets[p->tb_sched[i].set];
+        if (!tbr_encode_buffer(p, set, pairs[(i - 1) & 1][1], &h[(2 * i + 0) * nmap]) ||
+            !tbr_encode_buffer(p, set, pairs[(i - 1) & 1][0], &h[(2 * i + 1) * nmap]))
+            return fail(CHEB_ERR_CUDA, "tensor map encoding");
+    }
+    CHEB_CUDA(cudaMemcpy(p->d_tmaps, h.data(), need, cudaMemcpyHostToDevice));
+    return CHEB_OK;
+}
+
+// psi's maps for launch 0 into psi slot `slot`, ordered on stream s (outside any capture)
+int tbr_maps_psi(Plan* p, const void* psi, int slot, cudaStream_t s)
+{
+    if (!tbr_boxes(p) || !p->d_tmaps) return CHEB_OK;
+    Plan::TMPsi& key = p->tm_psi[slot];
+    if (key.psi == psi && key.epoch == p->shape_epoch) return CHEB_OK;
+    const size_t nmap = (size_t)p->nblocks * (p->nvec / 2);
+    std::vector<CUtensorMap> h(nmap);
+    if (!tbr_encode_buffer(p, p->tb_sets[p->tb_sched[0].set], psi, h.data()))
+        return fail(CHEB_ERR_CUDA, "tensor map encoding");
+    char* dst = static_cast<char*>(p->d_tmaps) + (2 * p->tb_sched.size() + slot) * p->tmap_array;
+    // pageable source: the call returns once the data is staged, and the copy is ordered on s
+    CHEB_CUDA(cudaMemcpyAsync(dst, h.data(), p->tmap_array, cudaMemcpyHostToDevice, s));
+    key.psi = psi;
+    key.epoch = p->shape_epoch;
+    return CHEB_OK;
+}
+
+// The map array a launch uses (which: 0 = T_{ka-1}, 1 = T_{ka-2}), or NULL for per-thread copies.
+const void* tbr_maps_for(const Plan* p, int launch, int which, const void* psi, int slot)
+{
+    if (!tbr_boxes(p) || !p->d_tmaps) return nullptr;
+    const char* base = static_cast<const char*>(p->d_tmaps);
+    if (launch == 0) {
+        if (slot < 0) return nullptr;
+        const Plan::TMPsi& key = p->tm_psi[slot];
+        if (which != 0 || key.psi != psi || key.epoch != p->shape_epoch) return nullptr;
+        return base + (2 * p->tb_sched.size() + slot) * p->tmap_array;
+    }
+    return base + (2 * (size_t)launch + which) * p->tmap_array;
+}
+
 // Host work model of one launch of this kernel (cheb_plan_step_model)
 void tbr_model_launch(const Plan* p, const std::vector<TBTile>& tiles, int ka, int kb,
                       int prev_ka, TBModel& m)
 {
     const int nv = p->nvec;
-    const int per = nv >= 2 ? 2 : 1, align = nv >= 2 ? 4 : 8;
+    const int per = nv >= 2 ? 2 : 1;
     const double eb = tbr_elem_bytes(nv);
     const double nel = nv / per;  // plane elements per site (CTAs per tile)
     const int run = p->tb_spt, npos = p->tb_spt * p->tb_tpb;
@@ -691,7 +919,7 @@ void tbr_model_launch(const Plan* p, const std::vector<TBTile>& tiles, int ka, i
         if (ka > B.M) continue;
         const int ke = std::min(kb, (int)B.M), ns = ke - ka + 1;
         const bool done = ke == B.M;
-        const int RW = T.C1 - T.C0, RH = T.R1 - T.R0, S = tbr_stride(RW, align);
+        const int RW = T.C1 - T.C0, RH = T.R1 - T.R0, S = T.S;  // the ribbon's stride
         const double inter = (double)(T.r1 - T.r0) * (T.c1 - T.c0);
         const bool ot = T.R0 > 0, ob = T.R1 < B.W, ol = T.C0 > 0, orr = T.C1 < B.L;
         // runs: positions t run .. t run + run - 1; a run is formed while any site is valid;
@@ -700,8 +928,7 @@ void tbr_model_launch(const Plan* p, const std::vector<TBTile>& tiles, int ka, i
         for (int t = 0; t * run < npos; ++t) {
             int rl = -1, sites = 0;
             for (int j = 0; j < run; ++j) {
-                const int q = t * run + j - 1;
-                if (q < 0) continue;
+                const int q = t * run + j;
                 const int rr = q / S, cc = q - rr * S;
                 if (rr >= RH || cc >= RW) continue;
                 ++sites;
@@ -716,16 +943,19 @@ void tbr_model_launch(const Plan* p, const std::vector<TBTile>& tiles, int ka, i
         m.computed += formed;
         // per formed run-order: RUN vertical loads, two run-end loads and RUN stores (pads
         // included); per tile: both planes written over all positions, and the staging copies of
-        // the sites' inputs (T_{ka-1}, T_{ka-2}, d, the interior's accumulator), written by
-        // cp.async and read back once; all times the CTAs of the tile (one per plane element)
+        // the inputs (T_{ka-1}, T_{ka-2}: the sites, or S x BH box elements; d and the interior's
+        // accumulator), written once and read back once at the sites; all times the CTAs of the
+        // tile (one per plane element)
         const double vin = first ? 1.0 : 2.0;
+        const double staged = T.tma ? (double)T.S * T.BH : (double)RH * RW;
         const bool to_main = first || ka <= B.ksplit;
         const bool read_e = !first && (to_main || done);
         const bool read_t = !first && !to_main && prev_ka > B.ksplit;
         const double acc_in = (read_e ? 1.0 : 0.0) + (read_t ? 1.0 : 0.0);
         const double sites = (double)RH * RW;
         m.smem += nel * (eb * run_orders * (2.0 * run + 2.0) + 2.0 * eb * npos +
-                         2.0 * (sites * (vin * eb + 4.0) + inter * eb * (acc_in > 0 ? 1.0 : 0.0)));
+                         vin * eb * (staged + sites) + 2.0 * sites * 4.0 +
+                         2.0 * inter * eb * (acc_in > 0 ? 1.0 : 0.0));
         const double outs = done ? 1.0 : 3.0;
         m.l2 += sites * (vin * nel * eb + 4.0 * nel) + inter * nel * eb * (acc_in + outs);
     }

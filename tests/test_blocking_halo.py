@@ -174,19 +174,31 @@ def test_tiles_span_row_bands_and_column_tiles():
 
 
 # ---- padded regions of the register-run kernel -----------------------------------------------
-def _check_tiles_padded(W, L, s, positions, align):
+def _check_tiles_padded(W, L, s, positions, align, boxes):
     import numpy as np
 
     import paper_0907_3022_gb300 as cb
 
-    tiles = cb.cheb_tb_tiles_padded(W, L, s, positions, align)
+    tiles = cb.cheb_tb_tiles_padded(W, L, s, positions, align, boxes)
     hr = (s + 1) // 2
     cover = np.zeros((W, L), dtype=np.int32)
-    for R0, R1, C0, C1, r0, r1, c0, c1 in tiles.tolist():
+    if boxes:
+        # one row stride and one box height for the whole ribbon: the widest tile's stride, the
+        # tallest tile's rows, and together they fit the CTA's positions
+        S_all, BH_all = set(tiles[:, 8].tolist()), set(tiles[:, 9].tolist())
+        assert len(S_all) == 1 and len(BH_all) == 1
+        S, BH = S_all.pop(), BH_all.pop()
+        assert S % align == 0 and BH == max(tiles[:, 1] - tiles[:, 0])
+        assert S == max((c1_ - c0_ + align) // align * align
+                        for c0_, c1_ in zip(tiles[:, 2], tiles[:, 3]))
+        assert 1 + BH * S <= positions
+    for R0, R1, C0, C1, r0, r1, c0, c1, S, BH in tiles.tolist():
         assert 0 <= R0 <= r0 < r1 <= R1 <= W and 0 <= C0 <= c0 < c1 <= C1 <= L
         stride = (C1 - C0 + align) // align * align
-        # at least one zero pad after every row, stride a multiple of align, and the leading
-        # zero position plus all rows fit the CTA's positions
+        if not boxes:  # the tile's own stride and rows
+            assert S == stride and BH == R1 - R0
+        # at least one zero pad after every row, stride a multiple of align, and all rows plus
+        # the trailing zero position fit the CTA's positions
         assert stride >= C1 - C0 + 1 and stride % align == 0 and stride - (C1 - C0) <= align
         assert 1 + (R1 - R0) * stride <= positions
         assert r0 - R0 == min(hr, r0) and R1 - r1 == min(hr, W - r1)
@@ -204,7 +216,8 @@ def test_padded_tiles_partition_the_ribbon_with_valid_interiors():
                  (160, 400), (40, 500)]:
         for s in (1, 3, 8, 10):
             for positions, align in ((1536, 4), (2304, 4), (2560, 4), (3072, 4), (5120, 8)):
-                _check_tiles_padded(W, L, s, positions, align)
+                for boxes in (False, True):
+                    _check_tiles_padded(W, L, s, positions, align, boxes)
 
 
 def test_padded_tiles_rejected_when_one_column_does_not_fit():

@@ -1,5 +1,6 @@
 """The temporally blocked recurrence at the launch shapes the ensemble benchmark runs (8 to 12
-orders per launch; both blocked kernels at their tuned CTA shapes), element by
+orders per launch; the blocked kernels at their tuned CTA shapes, the register-run one with
+per-thread copies and with tensor-memory-access boxes), element by
 element against the FP64 oracle, on ribbons whose tiles need several row bands and several
 column tiles, so that the row halo (ceil(s/2) rows), the column halo (s columns), ragged last
 bands and columns and the merged last launch of a step are all exercised.
@@ -23,12 +24,13 @@ pytestmark = pytest.mark.gpu
 SIZES = [(158, 3177), (154, 3426), (131, 1999), (1, 300), (3, 5), (97, 41), (7, 230), (130, 30),
          (2, 3), (1, 1)]
 NSTEPS = 10
-SITES, RUNS = 0, 1
+SITES, RUNS, RUNS_TMA = 0, 1, 2
 # (orders per launch, sites per thread, threads, kernel): the strided-site kernel's tuned
-# shapes and the register-run kernel's
+# shapes and the register-run kernel's, with per-thread copies and with boxes
 SHAPES = [(8, 6, 512, SITES), (10, 6, 512, SITES), (8, 3, 1024, SITES), (10, 3, 1024, SITES),
           (8, 7, 384, RUNS), (10, 7, 384, RUNS), (10, 9, 256, RUNS), (12, 9, 256, RUNS),
-          (10, 3, 768, RUNS)]
+          (10, 3, 768, RUNS), (10, 7, 384, RUNS_TMA), (12, 9, 256, RUNS_TMA),
+          (10, 5, 512, RUNS_TMA)]
 
 _cache = {}
 

@@ -1,8 +1,12 @@
-"""The register-run blocked kernel (CHEB_TB_RUNS) against the FP64 oracle and against
-single-order launches, at every compiled shape, on ensembles with edge shapes: 1D chains
-(W = 1), a single site, ribbons shorter than the halo, and widths and lengths that leave
-ragged last bands, columns and runs.  Interior sites of every tile keep all orders of a launch
-valid; halo sites, pads and runs that straddle rows must never leak into them."""
+"""The register-run blocked kernel (CHEB_TB_RUNS, and CHEB_TB_RUNS_TMA with its inputs staged
+by tensor-memory-access boxes) against the FP64 oracle and against single-order launches, at
+every compiled shape, on ensembles with edge shapes: 1D chains (W = 1), a single site, ribbons
+shorter than the halo, and widths and lengths that leave ragged last bands, columns and runs.
+Interior sites of every tile keep all orders of a launch valid; halo sites, pads and runs that
+straddle rows must never leak into them.
+
+The two variants form every interior site's T_k from the same neighbour values in the same
+order, whatever the tiles, so their results must be equal bit for bit."""
 import numpy as np
 import pytest
 
@@ -28,15 +32,16 @@ def _cases():
     out = []
     for nvec in (4, 2):
         for run, tpb in PAIR_SHAPES:
-            out.append((nvec, run, tpb))
+            out.append((nvec, run, tpb, 1))
+            out.append((nvec, run, tpb, 2))
     for run, tpb in SINGLE_SHAPES:
-        out.append((1, run, tpb))
+        out.append((1, run, tpb, 1))
     return out
 
 
 @pytest.mark.parametrize("s", [3, 6, 10])
-@pytest.mark.parametrize("nvec,run,tpb", _cases())
-def test_runs_match_oracle_and_single_order(nvec, run, tpb, s):
+@pytest.mark.parametrize("nvec,run,tpb,kernel", _cases())
+def test_runs_match_oracle_and_single_order(nvec, run, tpb, kernel, s):
     import paper_0907_3022_gb300 as cb
 
     ens = wl.RibbonEnsemble(n_ribbons=len(SIZES), sizes=list(SIZES), sigma=4.0,
@@ -53,12 +58,17 @@ def test_runs_match_oracle_and_single_order(nvec, run, tpb, s):
     ref_plan.evolve(a, ens.dt, nsteps)
     plan = _plan(cb, ens, nvec)
     plan.evolve(x0, ens.dt, 0)
-    plan.set_blocking_kernel(s, run, tpb, cb.CHEB_TB_RUNS)
-    assert plan.blocking_shape() == (s, run, tpb) and plan.blocking_kernel() == cb.CHEB_TB_RUNS
+    plan.set_blocking_kernel(s, run, tpb, kernel)
+    assert plan.blocking_shape() == (s, run, tpb) and plan.blocking_kernel() == kernel
     b = x0.clone()
     plan.evolve(b, ens.dt, nsteps)
     out_a, out_b = host(a), host(b)
     assert rel(out_b, out_a) <= 2e-6
+    if kernel == cb.CHEB_TB_RUNS_TMA:  # the same results as the per-thread copies, bit for bit
+        plan.set_blocking_kernel(s, run, tpb, cb.CHEB_TB_RUNS)
+        c = x0.clone()
+        plan.evolve(c, ens.dt, nsteps)
+        assert np.array_equal(host(c), out_b)
     import oracle
 
     for r in range(ens.n_ribbons):
@@ -128,3 +138,43 @@ def test_runs_shape_errors():
         plan.set_blocking_kernel(4, 3, 768, 7)
     assert e.value.status == cb.CHEB_ERR_INVALID
     plan.close()
+    one = _plan(cb, ens, 1)
+    with pytest.raises(cb.ChebError) as e:  # boxes carry pairs of vectors only
+        one.set_blocking_kernel(4, 7, 512, cb.CHEB_TB_RUNS_TMA)
+    assert e.value.status == cb.CHEB_ERR_UNSUPPORTED
+    one.close()
+
+
+def test_runs_tma_boxes_follow_the_state_vector():
+    """The first launch of a step reads psi through tensor maps made for psi's address: direct
+    steps (one map slot, rewritten when psi changes) and graph-replayed evolve calls on six
+    vectors (more than the plan's four graph slots, so slots are evicted and their maps
+    rewritten), interleaved, against the per-thread-copy kernel doing the same calls."""
+    import paper_0907_3022_gb300 as cb
+
+    ens = wl.RibbonEnsemble(n_ribbons=len(SIZES), sizes=list(SIZES), sigma=4.0,
+                            k0s=wl.ENSEMBLE_K0[:4])
+    off = ens.offsets()
+    xs = []
+    for j in range(6):
+        x = ens.packets()
+        for r in range(ens.n_ribbons):
+            x[off[r]:off[r + 1], j % 4] = wl.random_state(int(off[r + 1] - off[r]), 500 + j, r)
+        xs.append(x)
+    calls = [(0, "e", 2), (1, "s", 1), (2, "e", 1), (0, "s", 1), (3, "e", 2), (4, "e", 1),
+             (5, "e", 1), (1, "e", 2), (0, "e", 1), (2, "s", 1), (5, "s", 1), (3, "e", 1)]
+    outs = {}
+    for kernel in (cb.CHEB_TB_RUNS, cb.CHEB_TB_RUNS_TMA):
+        plan = _plan(cb, ens, 4)
+        psis = [dev_vec(x, C64) for x in xs]
+        plan.evolve(psis[0], ens.dt, 0)
+        plan.set_blocking_kernel(10, 7, 384, kernel)
+        for j, kind, n in calls:
+            if kind == "s":
+                plan.step(psis[j], ens.dt)
+            else:
+                plan.evolve(psis[j], ens.dt, n)
+        outs[kernel] = [host(p) for p in psis]
+        plan.close()
+    for j in range(6):
+        assert np.array_equal(outs[cb.CHEB_TB_RUNS_TMA][j], outs[cb.CHEB_TB_RUNS][j]), j
