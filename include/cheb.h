@@ -320,8 +320,9 @@ int cheb_plan_set_blocking(cheb_plan* plan, int orders_per_launch, int sites_per
                     once.  Region rows are padded to a multiple of 4 (pairs of vectors) or 8
                     (one vector) positions with at least one zero pad.  A CTA holds one pair of
                     vectors (nvec 2 and 4: the two pairs of a tile go to two CTAs) or one vector
-                    (nvec 1).  Each thread prefetches its positions of the next tile while
-                    the current one runs.  Compiled (run x threads): pairs 3 x 768, 3 x 512,
+                    (nvec 1).  The launch keeps its CTAs resident (one per SM), each working
+                    through tiles; each thread prefetches its positions of the CTA's next
+                    tile while the current one runs.  Compiled (run x threads): pairs 3 x 768, 3 x 512,
                     5 x 512, 7 x 384, 9 x 256; single vectors 3 x 1024, 5 x 512, 7 x 512;
      CHEB_TB_RUNS_TMA  CHEB_TB_RUNS with the next tile's T_{k-1} and T_{k-2} staged by
                     tensor-memory-access boxes (one box per vector pair and buffer, completion
@@ -338,6 +339,12 @@ typedef enum { CHEB_TB_SITES = 0, CHEB_TB_RUNS = 1, CHEB_TB_RUNS_TMA = 2 } cheb_
 int cheb_plan_set_blocking_kernel(cheb_plan* plan, int orders_per_launch, int sites_per_thread,
                                   int threads, int kernel);
 int cheb_plan_blocking_kernel(const cheb_plan* plan, int* kernel);
+/* CTAs of each blocked launch: at most `ctas`, every CTA working through the tiles (and vector
+   pairs) i, i + ctas, ...; 0 (the default) means the strided-site kernel's one CTA per tile
+   and the register-run kernel's resident CTAs (SMs x CTAs per SM), whose CTAs copy their next
+   tile's inputs while the current one runs its orders.  Results do not depend on it.
+   CHEB_ERR_INVALID for ctas < 0. */
+int cheb_plan_set_blocking_grid(cheb_plan* plan, int ctas);
 
 /* Whole steps on a thread-block cluster (1D grid plans, CHEB_LAT1D with nvec 1, a shared
    potential and at most 32768 points): ctas = 8 or 16 runs all M orders of a step in one

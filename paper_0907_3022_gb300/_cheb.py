@@ -115,6 +115,7 @@ _SIGS = {
                               _c.POINTER(_c.c_int32), _c.c_int64, _i64p], _c.c_int),
     "cheb_plan_set_blocking_kernel": ([_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int], _c.c_int),
     "cheb_plan_blocking_kernel": ([_vp, _ip], _c.c_int),
+    "cheb_plan_set_blocking_grid": ([_vp, _c.c_int], _c.c_int),
     "cheb_autotune": ([_vp], _c.c_int),
     "cheb_plan_launch": ([_vp, _ip, _ip, _ip, _ip], _c.c_int),
     "cheb_plan_set_blocking": ([_vp, _c.c_int, _c.c_int, _c.c_int], _c.c_int),
@@ -402,6 +403,10 @@ class Plan:
                             kernel: int):
         check(lib().cheb_plan_set_blocking_kernel(self.handle, orders_per_launch, sites_per_thread,
                                                   threads, kernel), "cheb_plan_set_blocking_kernel")
+
+    def set_blocking_grid(self, ctas: int):
+        """CTAs of each blocked launch (0: the kernel's default)."""
+        check(lib().cheb_plan_set_blocking_grid(self.handle, ctas), "cheb_plan_set_blocking_grid")
 
     def blocking_kernel(self) -> int:
         """CHEB_TB_SITES, CHEB_TB_RUNS or CHEB_TB_RUNS_TMA (CHEB_TB_SITES when blocking is off)."""

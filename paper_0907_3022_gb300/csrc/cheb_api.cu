@@ -295,6 +295,9 @@ static int tb_prepare(Plan* p)
         p->tb_s = 0;
         return rc0;
     }
+    p->tbr_resident = tb_runs(p->tb_kernel)
+                          ? tbr_blocks_per_sm(p->nvec, p->tb_spt, p->tb_tpb) * p->num_sms
+                          : 0;
     const int s0 = std::max(1, std::min(p->tb_s, minM - 1));
     // order ranges [ka, kb] of the launches; a last range shorter than half a block is merged
     // into the one before (a launch costs its region loads and stores however few orders it
@@ -1582,6 +1585,16 @@ extern "C" int cheb_plan_set_blocking_kernel(cheb_plan* plan, int s, int spt, in
     if (rc) return rc;
     if (s > 0 && p->have_dt && p->tb_sched.empty())
         return fail(CHEB_ERR_INVALID, "temporal blocking: a ribbon does not fit the tile budget");
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_set_blocking_grid(cheb_plan* plan, int ctas)
+{
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p) return fail(CHEB_ERR_INVALID, "NULL plan");
+    if (ctas < 0) return fail(CHEB_ERR_INVALID, "cheb_plan_set_blocking_grid: ctas < 0");
+    p->tb_grid_cap = ctas;
+    p->shape_epoch++;  // the step graphs hold the launch shape
     return CHEB_OK;
 }
 

@@ -191,6 +191,7 @@ const void* tbr_maps_for(const Plan* p, int launch, int which, const void* psi, 
 bool tbr_supported(int nv, int run, int tpb);
 size_t tbr_smem_bytes(int nv, int run, int tpb);
 int tbr_configure(int nv, int run, int tpb);
+int tbr_blocks_per_sm(int nv, int run, int tpb);  // resident CTAs per SM (0 on error)
 int tbr_launch(Plan* p, const TBArgs& a, cudaStream_t s);
 void tbr_model_launch(const Plan* p, const std::vector<TBTile>& tiles, int ka, int kb,
                       int prev_ka, TBModel& m);
@@ -325,7 +326,8 @@ struct Plan {
     int tb_spt = 4;           // sites per thread (CHEB_TB_RUNS: the run length)
     int tb_tpb = 256;         // threads per CTA of the blocked kernel
     int tb_kernel = CHEB_TB_SITES;  // blocked kernel: strided sites or register runs (+ boxes)
-    int tb_grid_cap = 0;
+    int tb_grid_cap = 0;      // CTAs of a blocked launch (cheb_plan_set_blocking_grid; 0: default)
+    int tbr_resident = 0;     // resident CTAs of the register-run kernel's shape (SMs x per SM)
     void* d_C = nullptr;      // second recurrence pair and the main accumulator
     void* d_D = nullptr;
     void* d_E = nullptr;

@@ -736,6 +736,40 @@ static int tbr_attr_t()
     return CHEB_OK;
 }
 
+// resident CTAs per SM of a shape: the fewest over its variants (FIRST and not, with and
+// without boxes)
+template <typename PT, int RUN, int TPB>
+static int tbr_occ_t()
+{
+    const size_t smem = tbr_smem_layout<PT, RUN, TPB>();
+    int o[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], k_rec_tbr<PT, RUN, TPB, true, false>, TPB, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], k_rec_tbr<PT, RUN, TPB, false, false>, TPB, smem);
+    o[2] = o[3] = o[1];
+    if constexpr (TBRBox<PT>::value) {
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[2], k_rec_tbr<PT, RUN, TPB, true, true>, TPB, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], k_rec_tbr<PT, RUN, TPB, false, true>, TPB, smem);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return std::min(std::min(o[0], o[1]), std::min(o[2], o[3]));
+}
+
+int tbr_blocks_per_sm(int nv, int run, int tpb)
+{
+    const int eb = tbr_elem_bytes(nv);
+#define CHEB_TBR_OCC(PT, RUN, TPB) \
+    if ((int)sizeof(PT) == eb && run == RUN && tpb == TPB) return tbr_occ_t<PT, RUN, TPB>();
+    CHEB_TBR_SHAPES(CHEB_TBR_OCC)
+#undef CHEB_TBR_OCC
+    return 0;
+}
+
 int tbr_configure(int nv, int run, int tpb)
 {
     const int eb = tbr_elem_bytes(nv);
@@ -764,8 +798,11 @@ static void tbr_launch_t(const TBArgs& a, int grid, cudaStream_t s, bool box)
 int tbr_launch(Plan* p, const TBArgs& a, cudaStream_t s)
 {
     const int per = p->nvec >= 2 ? 2 : 1;
+    // persistent: as many CTAs as are resident (the caller's count if set), each looping over
+    // work items, so that the copies of a CTA's next item overlap the orders of its current one
     int grid = a.ntiles * (p->nvec / per);
-    if (p->tb_grid_cap > 0 && grid > p->tb_grid_cap) grid = p->tb_grid_cap;
+    const int cap = p->tb_grid_cap > 0 ? p->tb_grid_cap : p->tbr_resident;
+    if (cap > 0 && grid > cap) grid = cap;
     if (grid < 1) return CHEB_OK;
     const int eb = tbr_elem_bytes(p->nvec), run = p->tb_spt, tpb = p->tb_tpb;
     // the variant with boxes when some ribbon of this launch has tensor maps

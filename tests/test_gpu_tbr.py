@@ -85,6 +85,38 @@ def test_runs_match_oracle_and_single_order(nvec, run, tpb, kernel, s):
     ref_plan.close()
 
 
+@pytest.mark.parametrize("kernel,run,tpb", [(1, 7, 384), (2, 7, 384), (1, 3, 768), (0, 6, 512)])
+def test_blocked_grid_does_not_change_results(kernel, run, tpb):
+    """Every CTA of a blocked launch works through tiles i, i + grid, ...; with 1, 3 and 7
+    CTAs each CTA runs many tiles in a row (the register-run kernel copying each next tile's
+    inputs during the current one's orders), with the default grid the results must be the
+    same bit for bit: a tile's arithmetic does not depend on which CTA runs it."""
+    import paper_0907_3022_gb300 as cb
+
+    ens = wl.RibbonEnsemble(n_ribbons=len(SIZES), sizes=list(SIZES), sigma=4.0,
+                            k0s=wl.ENSEMBLE_K0[:4])
+    x = ens.packets()
+    off = ens.offsets()
+    for r in range(ens.n_ribbons):
+        x[off[r]:off[r + 1], 3] = wl.random_state(int(off[r + 1] - off[r]), 31, r)
+    x0 = dev_vec(x, C64)
+    plan = _plan(cb, ens, 4)
+    plan.evolve(x0, ens.dt, 0)
+    plan.set_blocking_kernel(6, run, tpb, kernel)
+    outs = []
+    for ctas in (0, 1, 3, 7):
+        plan.set_blocking_grid(ctas)
+        b = x0.clone()
+        plan.evolve(b, ens.dt, 4)
+        outs.append(host(b))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    with pytest.raises(cb.ChebError) as e:
+        plan.set_blocking_grid(-1)
+    assert e.value.status == cb.CHEB_ERR_INVALID
+    plan.close()
+
+
 def test_runs_small_orders_records_and_growth_check():
     """dt = 0.001 (M of about 5): the first launch is cut below min M and every ribbon ends
     inside the second; records every 10 steps; then bounds far too tight must trip the
