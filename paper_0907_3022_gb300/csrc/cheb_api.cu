@@ -437,6 +437,10 @@ static int enqueue_step_tb(Plan* p, void* psi, cudaStream_t st)
     } else if (slot == Plan::kGraphSlots) {
         slot = -1;
     }
+    // the register-run kernel adds its first launch's ||psi||^2 into the (ribbon, vector)
+    // slots of the growth check
+    if (tb_runs(p->tb_kernel))
+        CHEB_CUDA(cudaMemsetAsync(p->d_red, 0, (size_t)p->nblocks * p->nvec * 2 * sizeof(double), st));
     for (size_t i = 0; i < p->tb_sched.size(); ++i) {
         const Plan::TBLaunch& L = p->tb_sched[i];
         const TBSet& set = p->tb_sets[L.set];

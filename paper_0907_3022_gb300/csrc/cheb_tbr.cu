@@ -345,17 +345,16 @@ __device__ __forceinline__ bool tbr_fetch(const TBArgs& a, const TBRTile& t, int
 
 // One order k of parity ODD for the thread's run: dst <- 2 H~ src - dst at every position
 // (src = T_{k-1}, dst = T_{k-2} in, T_k out), T_k stored to Pw, q_k T_k added to every
-// position's accumulator (only interior ones are written out).  Pads carry zero coupling,
-// diagonal and values, so they stay exactly zero (every value read is finite: both planes are
-// zeroed at each tile start).  Reads Qr (T_{k-1}).
-template <typename PT, int RUN, bool FIRST, bool ODD>
+// position's accumulator (only interior ones are written out); HALF: the first order,
+// T_1 = H~ T_0 (dst holds zeros).  Pads carry zero coupling, diagonal and values, so they
+// stay exactly zero (every value read is finite: both planes are zeroed at each tile start).
+// Reads Qr (T_{k-1}).
+template <typename PT, int RUN, bool HALF, bool ODD>
 __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restrict__ Pw,
                                           const PT (&src)[RUN], PT (&dst)[RUN],
                                           const float (&d)[RUN], const float (&bh)[RUN],
-                                          const int (&vidx)[RUN], int zpos,
-                                          unsigned interm, int e0, bool active, float2 qk, int k,
-                                          float2 (&acc)[RUN][TBRPlane<PT>::PER],
-                                          float (&part)[FIRST ? 2 * TBRPlane<PT>::PER : 1])
+                                          const int (&vidx)[RUN], int zpos, int e0, bool active,
+                                          float2 qk, float2 (&acc)[RUN][TBRPlane<PT>::PER])
 {
     constexpr int PER = TBRPlane<PT>::PER;
     if (active) {
@@ -368,20 +367,9 @@ __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restr
         for (int j = 0; j < RUN; ++j) {
             const PT l = j > 0 ? src[j - 1] : Lf;
             const PT r = j < RUN - 1 ? src[j + 1] : Rt;
-            const PT h = tbr_h(l, r, V[j], dst[j], src[j], d[j], bh[j], FIRST && ODD && k == 1);
+            const PT h = tbr_h(l, r, V[j], dst[j], src[j], d[j], bh[j], HALF);
 #pragma unroll
-            for (int c = 0; c < PER; ++c) {
-                const float2 hv = tbr_get(h, c);
-                tbr_accum<ODD>(acc[j][c], qk, hv);
-                if constexpr (FIRST && ODD) {
-                    if (k == 1 && ((interm >> j) & 1u)) {
-                        // ||T_0||^2, <T_0|H~ T_0> (FP32: feeds only the divergence check)
-                        const float2 x = tbr_get(src[j], c);
-                        part[2 * c + 0] = fmaf(x.x, x.x, fmaf(x.y, x.y, part[2 * c + 0]));
-                        part[2 * c + 1] = fmaf(x.x, hv.x, fmaf(x.y, hv.y, part[2 * c + 1]));
-                    }
-                }
-            }
+            for (int c = 0; c < PER; ++c) tbr_accum<ODD>(acc[j][c], qk, tbr_get(h, c));
             dst[j] = h;
             Pw[e0 + j] = h;
         }
@@ -389,31 +377,52 @@ __device__ __forceinline__ void tbr_order(const PT* __restrict__ Qr, PT* __restr
     __syncthreads();
 }
 
-// orders ka..ke, two per iteration (P <- 2 H~ X - P, then X <- 2 H~ P - X); P0 = parity of ka
-template <typename PT, int RUN, bool FIRST, bool P0>
-__device__ __forceinline__ void tbr_orders(PT* plane0, PT* plane1, PT (&X)[RUN], PT (&P)[RUN],
-                                           const float (&d)[RUN], const float (&bh)[RUN],
-                                           const int (&vidx)[RUN], int zpos,
-                                           unsigned interm, int e0, int rl, int ka, int ke,
-                                           const float2* __restrict__ qc,
-                                           float2 (&acc)[RUN][TBRPlane<PT>::PER],
-                                           float (&part)[FIRST ? 2 * TBRPlane<PT>::PER : 1])
+// orders k..ke, two per iteration (B <- 2 H~ A - B from plane qa into plane qb, then
+// A <- 2 H~ B - A back); P0 = parity of k; a run is formed while rl >= (order - ka + 1)
+template <typename PT, int RUN, bool P0>
+__device__ __forceinline__ void tbr_orders_from(PT* qa, PT* qb, PT (&A)[RUN], PT (&Bv)[RUN],
+                                                const float (&d)[RUN], const float (&bh)[RUN],
+                                                const int (&vidx)[RUN], int zpos, int e0, int rl,
+                                                int ka, int k, int ke,
+                                                const float2* __restrict__ qc,
+                                                float2 (&acc)[RUN][TBRPlane<PT>::PER])
 {
-    float2 qn = qc[ka];
-    int k = ka;
+    float2 qn = qc[k];
     for (;;) {
         float2 qk = qn;
         if (k < ke) qn = qc[k + 1];
-        tbr_order<PT, RUN, FIRST, P0>(plane0, plane1, X, P, d, bh, vidx, zpos, interm, e0,
-                                      rl >= k - ka + 1, qk, k, acc, part);
+        tbr_order<PT, RUN, false, P0>(qa, qb, A, Bv, d, bh, vidx, zpos, e0, rl >= k - ka + 1, qk,
+                                      acc);
         if (k == ke) break;
         ++k;
         qk = qn;
         if (k < ke) qn = qc[k + 1];
-        tbr_order<PT, RUN, FIRST, !P0>(plane1, plane0, P, X, d, bh, vidx, zpos, interm, e0,
-                                       rl >= k - ka + 1, qk, k, acc, part);
+        tbr_order<PT, RUN, false, !P0>(qb, qa, Bv, A, d, bh, vidx, zpos, e0, rl >= k - ka + 1, qk,
+                                       acc);
         if (k == ke) break;
         ++k;
+    }
+}
+
+// orders ka..ke: P <- 2 H~ X - P, then X <- 2 H~ P - X, ...; in the first launch (ka = 1)
+// order 1 is peeled off (T_1 = H~ T_0, a compile-time halving) and the loop goes on from
+// order 2 with the roles swapped
+template <typename PT, int RUN, bool FIRST, bool P0>
+__device__ __forceinline__ void tbr_orders(PT* plane0, PT* plane1, PT (&X)[RUN], PT (&P)[RUN],
+                                           const float (&d)[RUN], const float (&bh)[RUN],
+                                           const int (&vidx)[RUN], int zpos, int e0, int rl,
+                                           int ka, int ke, const float2* __restrict__ qc,
+                                           float2 (&acc)[RUN][TBRPlane<PT>::PER])
+{
+    if constexpr (FIRST) {
+        tbr_order<PT, RUN, true, true>(plane0, plane1, X, P, d, bh, vidx, zpos, e0, rl >= 1,
+                                       qc[ka], acc);
+        if (ka < ke)
+            tbr_orders_from<PT, RUN, false>(plane1, plane0, P, X, d, bh, vidx, zpos, e0, rl, ka,
+                                            ka + 1, ke, qc, acc);
+    } else {
+        tbr_orders_from<PT, RUN, P0>(plane0, plane1, X, P, d, bh, vidx, zpos, e0, rl, ka, ka, ke,
+                                     qc, acc);
     }
 }
 
@@ -452,7 +461,6 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
     float* const stD = reinterpret_cast<float*>(tbr_smem_raw + LY::stD);
     // the boxes' destinations must start on 128-byte boundaries (else per-thread copies)
     const bool box_ok = (tbr_smem_u32(tbr_smem_raw) & 127u) == 0u;
-    __shared__ double s_red[(TPB / 32) * 2 * PER];
     const PT zero = tbr_zero((PT*)nullptr);
     const int tid = threadIdx.x;
     const int e0 = tid * RUN;
@@ -476,8 +484,13 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
     __shared__ __align__(16) int s_meta[2][TBR_META_WORDS];  // descriptors of items it, it + 1
     const int nwork = a.ntiles * npairs;
     int w = blockIdx.x;
-    const bool any = w < nwork;  // a CTA without an item still counts in the finalize below
+    const bool any = w < nwork;
     if (any && tid < TBR_META_USED) s_meta[0][tid] = tbr_meta_load(a, w, npairs, tid);
+    // the descriptors of the CTA's next item, loaded one item ahead (two dependent loads: the
+    // tile, then its ribbon) so that later items find them arrived during the orders
+    int meta_next = 0;
+    if (tid < TBR_META_USED && w + (int)gridDim.x < nwork)
+        meta_next = tbr_meta_load(a, w + (int)gridDim.x, npairs, tid);
     __syncthreads();
     TBRTile t;
     bool boxed = false;  // the fetched item's inputs come (partly) by boxes
@@ -486,13 +499,10 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
         boxed = tbr_fetch<PT, RUN, FIRST, BOX>(a, t, e0, npairs, stX, stP, stA, stD, &s_bar, box_ok);
     }
     for (int it = 0; w < nwork; w += gridDim.x, ++it) {
-        // the next item's descriptors: loads in flight during this item's start
         const int wn = w + (int)gridDim.x;
-        int meta_word = 0;
-        if (tid < TBR_META_USED && wn < nwork) meta_word = tbr_meta_load(a, wn, npairs, tid);
-        float part[FIRST ? 2 * PER : 1];
+        float n2[FIRST ? PER : 1];  // ||T_0||^2 of the interior (first launch)
 #pragma unroll
-        for (int q = 0; q < (FIRST ? 2 * PER : 1); ++q) part[q] = 0.f;
+        for (int q = 0; q < (FIRST ? PER : 1); ++q) n2[q] = 0.f;
         const TBRTile cur = t;
         const TBTile& T = cur.T;
         const DevBlock& B = cur.B;
@@ -543,6 +553,13 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
                     bh[j] = bhi;
                     if (wk.interior(cur)) {
                         interm |= 1u << j;
+                        if constexpr (FIRST) {  // FP32: feeds only the divergence check
+#pragma unroll
+                            for (int q = 0; q < PER; ++q) {
+                                const float2 x = tbr_get(X[j], q);
+                                n2[q] = fmaf(x.x, x.x, fmaf(x.y, x.y, n2[q]));
+                            }
+                        }
                         if (read_e || read_t) ea = stA[e];
                         if (read_e && read_t) {  // E + tail at the ribbon's last order
                             const int64_t gi = (B.offset + wk.rg) * npairs + cur.pr;
@@ -576,8 +593,12 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
         // plane 0 complete; the barrier also orders this tile's reads of the staging buffers
         // before the copies of the next item below overwrite them, and publishes the next
         // item's descriptors (slot (it + 1) & 1 was last read two items ago)
-        if (tid < TBR_META_USED) s_meta[(it + 1) & 1][tid] = meta_word;
+        if (tid < TBR_META_USED) s_meta[(it + 1) & 1][tid] = meta_next;
         __syncthreads();
+        // the descriptors of the item after the next: loads in flight during this item's orders
+        meta_next = 0;
+        if (tid < TBR_META_USED && wn + (int)gridDim.x < nwork)
+            meta_next = tbr_meta_load(a, wn + (int)gridDim.x, npairs, tid);
         // the next work item's inputs stream in while this one runs its orders
         boxed = false;
         if (wn < nwork) {
@@ -586,11 +607,11 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
         }
         if (cur.live) {
             if (a.ka & 1)
-                tbr_orders<PT, RUN, FIRST, true>(plane0, plane1, X, P, d, bh, vidx, NPOS, interm, e0,
-                                                 rl, a.ka, ke, qc + B.coef_off, acc, part);
+                tbr_orders<PT, RUN, FIRST, true>(plane0, plane1, X, P, d, bh, vidx, NPOS, e0, rl,
+                                                 a.ka, ke, qc + B.coef_off, acc);
             else
-                tbr_orders<PT, RUN, FIRST, false>(plane0, plane1, X, P, d, bh, vidx, NPOS, interm,
-                                                  e0, rl, a.ka, ke, qc + B.coef_off, acc, part);
+                tbr_orders<PT, RUN, FIRST, false>(plane0, plane1, X, P, d, bh, vidx, NPOS, e0, rl,
+                                                  a.ka, ke, qc + B.coef_off, acc);
             // T_ke is in P when ke - ka is even (the last order ran the first half), else in X
             const bool last_in_p = ((ke - a.ka) & 1) == 0;
             float lim[PER];
@@ -632,57 +653,22 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
             }
         }
         if constexpr (FIRST) {
-            // per (tile, vector) partials: FP32 warp tree, FP64 across the warps
-            const int lane = tid & 31, warp = tid >> 5;
+            // ||psi||^2 per (ribbon, vector) for the growth check of the ribbon's last order:
+            // FP32 warp sums added to the slot, which the step zeroes before its first launch
+            // (summation order free: the check compares against 4 ||psi||^2)
+            if (cur.live) {
+                const int lane = tid & 31;
 #pragma unroll
-            for (int q = 0; q < 2 * PER; ++q) {
-                float xs = part[q];
-                for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
-                if (lane == 0) s_red[warp * 2 * PER + q] = (double)xs;
+                for (int q = 0; q < PER; ++q) {
+                    float xs = n2[q];
+                    for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
+                    if (lane == 0 && xs != 0.f)
+                        atomicAdd(a.red_out + ((size_t)T.block * nvec + cur.pr * PER + q) * 2, (double)xs);
+                }
             }
-            __syncthreads();
-            if (tid < 2 * PER) {
-                double tt = 0.0;
-                for (int q = 0; q < TPB / 32; ++q) tt += s_red[q * 2 * PER + tid];
-                // vector pr * PER + tid / 2, component tid % 2
-                const int ti = w / npairs;
-                a.partials[((size_t)ti * nvec + cur.pr * PER) * 2 + tid] = tt;
-            }
-            __syncthreads();
         }
     }
     tbr_cp_wait();  // no copy may be left in flight when the CTA exits
-    if constexpr (FIRST) {
-        __shared__ unsigned int s_last;
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) s_last = (atomicAdd(a.done_counter, 1u) == gridDim.x - 1) ? 1u : 0u;
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            // one warp per (ribbon, vector) slot, lane-strided over the tiles, fixed xor tree
-            const int lane = tid & 31, warp = tid >> 5;
-            for (int slot = warp; slot < a.nblocks * nvec; slot += TPB / 32) {
-                const int q = slot / nvec, v = slot % nvec;
-                const int it1 = a.block_tile_begin[q + 1];
-                double n2 = 0.0, eh = 0.0;
-                for (int it = a.block_tile_begin[q] + lane; it < it1; it += 32) {
-                    n2 += __ldcg(a.partials + ((size_t)it * nvec + v) * 2 + 0);
-                    eh += __ldcg(a.partials + ((size_t)it * nvec + v) * 2 + 1);
-                }
-                for (int off = 16; off > 0; off >>= 1) {
-                    n2 += __shfl_xor_sync(0xffffffffu, n2, off);
-                    eh += __shfl_xor_sync(0xffffffffu, eh, off);
-                }
-                if (lane == 0) {
-                    const DevBlock Bq = a.blocks[q];
-                    a.red_out[(size_t)slot * 2 + 0] = n2;
-                    a.red_out[(size_t)slot * 2 + 1] = Bq.a * eh + Bq.b * n2;
-                }
-            }
-            if (tid == 0) *a.done_counter = 0u;
-        }
-    }
 }
 
 // ---- dispatch ---------------------------------------------------------------------------
