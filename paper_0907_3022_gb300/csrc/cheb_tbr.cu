@@ -35,8 +35,10 @@
 //   tile start is hidden.  With pairs of vectors, T_{ka-1} and T_{ka-2} come as two tensor-memory-
 //   access boxes of S x BH elements (BH = the ribbon's tallest region) whose shared-memory image
 //   is exactly the plane layout above (box row rr, column cc at rr S + cc; columns and rows beyond
-//   the ribbon read as zero); d, the accumulator and single-vector planes are copied per thread
-//   with cp.async, each thread its own positions.
+//   the ribbon read as zero); d, the accumulator and single-vector planes are copied with
+//   cp.async, consecutive lanes on consecutive positions, published by a barrier after the
+//   wait.  A launch keeps its CTAs resident (one per SM), each working through tiles, so that
+//   a tile's copies overlap the previous tile's orders.
 //
 // Per formed site-order and plane element: one vertical load, 2 / RUN run-end loads, one store
 // (k_rec_tb: own, three neighbours, T_{k-2} and the store).
@@ -147,8 +149,8 @@ __device__ __forceinline__ float2 tbr_phase(const float2 a, const float2 ph, con
     return make_float2(rx, ry);
 }
 
-// asynchronous global -> shared copies of the next tile's inputs (each thread copies, and later
-// reads back, only its own positions)
+// asynchronous global -> shared copies of the next tile's inputs (all threads copy, with
+// consecutive lanes on consecutive positions; a barrier after the wait publishes them)
 __device__ __forceinline__ void tbr_cp16(void* sdst, const void* gsrc)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
@@ -287,11 +289,12 @@ struct TBRWalk {
     }
 };
 
-// Issue the copies of a work item's inputs for this thread's positions: T_{ka-1}, T_{ka-2}
-// (not in the first launch), d, and for interior sites the accumulator the launch continues
-// (E, or the tail when only the tail is read; when both are read the tail is loaded directly).
-template <typename PT, int RUN, bool FIRST, bool BOX>
-__device__ __forceinline__ bool tbr_fetch(const TBArgs& a, const TBRTile& t, int e0, int npairs,
+// Issue the copies of a work item's inputs: T_{ka-1}, T_{ka-2} (not in the first launch), d,
+// and for interior sites the accumulator the launch continues (E, or the tail when only the
+// tail is read; when both are read the tail is loaded directly).  Thread tid copies positions
+// tid, tid + TPB, ...
+template <typename PT, int RUN, int TPB, bool FIRST, bool BOX>
+__device__ __forceinline__ bool tbr_fetch(const TBArgs& a, const TBRTile& t, int npairs,
                                           PT* stX, PT* stP, PT* stA, float* stD, uint64_t* bar,
                                           bool box_ok)
 {
@@ -327,17 +330,26 @@ __device__ __forceinline__ bool tbr_fetch(const TBArgs& a, const TBRTile& t, int
     // the ribbon's first element of this plane index; sites at + rg * npairs
     const int64_t base = t.B.offset * npairs + t.pr;
     const PT* const accsrc = read_e ? accE : tail;
-    TBRWalk wk(t, e0);
+    // consecutive lanes on consecutive positions (position p = tid + k TPB): a warp's copies
+    // cover a few contiguous lines of a region row, not 32 lines RUN sites apart
+    const int RW = t.T.C1 - t.T.C0, RH = t.T.R1 - t.T.R0;
+    const int ir0 = t.T.r0 - t.T.R0, ir1 = t.T.r1 - t.T.R0;
+    const int ic0 = t.T.c0 - t.T.C0, ic1 = t.T.c1 - t.T.C0;
+    const int rg0 = t.T.R0 * t.B.L + t.T.C0;
+    const float* const dg = diag + t.B.offset;
 #pragma unroll
-    for (int j = 0; j < RUN; ++j) {
-        if (wk.site(t)) {
-            const int64_t gi = base + (int64_t)wk.rg * npairs;
-            if (!boxX) tbr_cp(stX + e0 + j, in_cur + gi);
-            if (!FIRST && !boxP) tbr_cp(stP + e0 + j, in_prev + gi);
-            tbr_cp4(stD + e0 + j, diag + t.B.offset + wk.rg);
-            if ((read_e || read_t) && wk.interior(t)) tbr_cp(stA + e0 + j, accsrc + gi);
+    for (int k = 0; k < RUN; ++k) {
+        const int p = (int)threadIdx.x + k * TPB;
+        const int rr = (int)(((unsigned long long)p * t.invS) >> 32), cc = p - rr * t.S;
+        if (rr < RH && cc < RW) {
+            const int rg = rg0 + rr * t.B.L + cc;
+            const int64_t gi = base + (int64_t)rg * npairs;
+            if (!boxX) tbr_cp(stX + p, in_cur + gi);
+            if (!FIRST && !boxP) tbr_cp(stP + p, in_prev + gi);
+            tbr_cp4(stD + p, dg + rg);
+            if ((read_e || read_t) && rr >= ir0 && rr < ir1 && cc >= ic0 && cc < ic1)
+                tbr_cp(stA + p, accsrc + gi);
         }
-        wk.next(t);
     }
     tbr_cp_commit();
     return boxX || boxP;
@@ -496,7 +508,7 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
     bool boxed = false;  // the fetched item's inputs come (partly) by boxes
     if (any) {
         t = tbr_tile(s_meta[0], w, a.ka, npairs);
-        boxed = tbr_fetch<PT, RUN, FIRST, BOX>(a, t, e0, npairs, stX, stP, stA, stD, &s_bar, box_ok);
+        boxed = tbr_fetch<PT, RUN, TPB, FIRST, BOX>(a, t, npairs, stX, stP, stA, stD, &s_bar, box_ok);
     }
     for (int it = 0; w < nwork; w += gridDim.x, ++it) {
         const int wn = w + (int)gridDim.x;
@@ -506,7 +518,8 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
         const TBRTile cur = t;
         const TBTile& T = cur.T;
         const DevBlock& B = cur.B;
-        // this work item's inputs, copied during the previous item's orders
+        // this work item's inputs, copied during the previous item's orders by all threads;
+        // the barrier also ends the previous item's reads of the planes
         tbr_cp_wait();
         if (BOX && boxed) {
             if (!tbr_mbar_wait(&s_bar, bar_parity)) {
@@ -515,6 +528,7 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
             }
             bar_parity ^= 1u;
         }
+        __syncthreads();
         PT X[RUN], P[RUN];
         float d[RUN], bh[RUN];
         int vidx[RUN];
@@ -530,51 +544,58 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
             const int RW = T.C1 - T.C0, RH = T.R1 - T.R0;
             const bool open_t = T.R0 > 0, open_b = T.R1 < B.W, open_l = T.C0 > 0, open_r = T.C1 < B.L;
             const float bhi = (float)B.beta;  // exact: the plan chooses a so
-            TBRWalk wk(cur, e0);
+            const int ir0 = T.r0 - T.R0, ir1 = T.r1 - T.R0, ic0 = T.c0 - T.C0, ic1 = T.c1 - T.C0;
+            const bool ld_a = read_e || read_t;
+            // Every position's staged inputs are loaded without conditions (all indexes lie in
+            // the buffers) and kept only at sites, so the loads do not wait behind per-position
+            // branches.  The vertical neighbour r +- 1 of a region row exists in the region
+            // exactly when it exists in the ribbon, since the region never leaves the ribbon.
+            int rr = (int)(((unsigned long long)e0 * cur.invS) >> 32), cc = e0 - rr * cur.S;
 #pragma unroll
             for (int j = 0; j < RUN; ++j) {
                 const int e = e0 + j;
-                const int rr = wk.rr, cc = wk.cc;
-                X[j] = zero;
-                P[j] = zero;
-                d[j] = 0.f;
-                bh[j] = 0.f;
-                vidx[j] = NPOS;
-                PT ea = zero;
-                if (wk.site(cur)) {
-                    const int r = T.R0 + rr;
-                    const bool up = (r + T.C0 + cc) & 1;  // vertical neighbour r - 1 (else r + 1)
-                    rl = max(rl, tbr_limit(rr, cc, RH, RW, up, open_t, open_b, open_l, open_r));
-                    vidx[j] = up ? ((rr > 0 && r > 0) ? e - cur.S : NPOS)
-                                 : ((rr + 1 < RH && r + 1 < B.W) ? e + cur.S : NPOS);
-                    X[j] = stX[e];
-                    if (!FIRST) P[j] = stP[e];
-                    d[j] = stD[e];
-                    bh[j] = bhi;
-                    if (wk.interior(cur)) {
-                        interm |= 1u << j;
-                        if constexpr (FIRST) {  // FP32: feeds only the divergence check
+                const PT xs = stX[e];
+                const PT ps = FIRST ? zero : stP[e];
+                const float ds = stD[e];
+                const PT as = ld_a ? stA[e] : zero;
+                const bool site = cc < RW && rr < RH;
+                const bool inter = rr >= ir0 && rr < ir1 && cc >= ic0 && cc < ic1;  // a site
+                const bool up = (T.R0 + rr + T.C0 + cc) & 1;  // vertical neighbour r - 1 (else r + 1)
+                const int lim = tbr_limit(rr, cc, RH, RW, up, open_t, open_b, open_l, open_r);
+                rl = site ? max(rl, lim) : rl;
+                vidx[j] = !site ? NPOS : up ? (rr > 0 ? e - cur.S : NPOS) : (rr + 1 < RH ? e + cur.S : NPOS);
+                X[j] = site ? xs : zero;
+                P[j] = site ? ps : zero;
+                d[j] = site ? ds : 0.f;
+                bh[j] = site ? bhi : 0.f;
+                interm |= inter ? (1u << j) : 0u;
+                const PT ea = inter ? as : zero;
 #pragma unroll
-                            for (int q = 0; q < PER; ++q) {
-                                const float2 x = tbr_get(X[j], q);
-                                n2[q] = fmaf(x.x, x.x, fmaf(x.y, x.y, n2[q]));
-                            }
-                        }
-                        if (read_e || read_t) ea = stA[e];
-                        if (read_e && read_t) {  // E + tail at the ribbon's last order
-                            const int64_t gi = (B.offset + wk.rg) * npairs + cur.pr;
-                            const PT tv = tail[gi];
-#pragma unroll
-                            for (int q = 0; q < PER; ++q) {
-                                const float2 x = tbr_get(ea, q), y = tbr_get(tv, q);
-                                tbr_put(ea, q, make_float2(x.x + y.x, x.y + y.y));
-                            }
-                        }
+                for (int q = 0; q < PER; ++q) {
+                    acc[j][q] = tbr_get(ea, q);
+                    if constexpr (FIRST) {  // ||T_0||^2 in FP32: feeds only the divergence check
+                        const float2 x = tbr_get(inter ? xs : zero, q);
+                        n2[q] = fmaf(x.x, x.x, fmaf(x.y, x.y, n2[q]));
                     }
                 }
+                if (++cc == cur.S) {
+                    cc = 0;
+                    ++rr;
+                }
+            }
+            if (read_e && read_t) {  // E + tail at the ribbon's last order (the tail from global)
+                TBRWalk wk(cur, e0);
 #pragma unroll
-                for (int q = 0; q < PER; ++q) acc[j][q] = tbr_get(ea, q);
-                wk.next(cur);
+                for (int j = 0; j < RUN; ++j, wk.next(cur)) {
+                    if (!((interm >> j) & 1u)) continue;
+                    const PT tv = tail[(B.offset + wk.rg) * npairs + cur.pr];
+#pragma unroll
+                    for (int q = 0; q < PER; ++q) {
+                        const float2 y = tbr_get(tv, q);
+                        acc[j][q].x += y.x;
+                        acc[j][q].y += y.y;
+                    }
+                }
             }
             // T_{ka-1} of every position into plane 0, plane 1 zeroed (pads and all)
 #pragma unroll
@@ -603,7 +624,7 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
         boxed = false;
         if (wn < nwork) {
             t = tbr_tile(s_meta[(it + 1) & 1], wn, a.ka, npairs);
-            boxed = tbr_fetch<PT, RUN, FIRST, BOX>(a, t, e0, npairs, stX, stP, stA, stD, &s_bar, box_ok);
+            boxed = tbr_fetch<PT, RUN, TPB, FIRST, BOX>(a, t, npairs, stX, stP, stA, stD, &s_bar, box_ok);
         }
         if (cur.live) {
             if (a.ka & 1)
@@ -623,22 +644,40 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
             pl.x = (float)(B.ph_re - (double)ph.x);
             ph.y = (float)B.ph_im;
             pl.y = (float)(B.ph_im - (double)ph.y);
+            if (!done) {
+                // T_ke and T_{ke-1} of the interior straight from the planes (the last order's
+                // barrier completed them; the next item's barrier ends these reads), consecutive
+                // lanes on consecutive positions
+                const PT* const planeK = last_in_p ? plane1 : plane0;
+                const PT* const planeK1 = last_in_p ? plane0 : plane1;
+                const int ir0 = T.r0 - T.R0, ir1 = T.r1 - T.R0;
+                const int ic0 = T.c0 - T.C0, ic1 = T.c1 - T.C0;
+                const int64_t gb = (int64_t)B.offset + (int64_t)T.R0 * B.L + T.C0;
+#pragma unroll
+                for (int k = 0; k < RUN; ++k) {
+                    const int p = tid + k * TPB;
+                    const int rr = (int)(((unsigned long long)p * cur.invS) >> 32);
+                    const int cc = p - rr * cur.S;
+                    if (rr >= ir0 && rr < ir1 && cc >= ic0 && cc < ic1) {
+                        const int64_t g = (gb + (int64_t)rr * B.L + cc) * npairs + cur.pr;
+                        out_cur[g] = planeK[p];
+                        out_prev[g] = planeK1[p];
+                    }
+                }
+            }
             TBRWalk wk(cur, e0);
 #pragma unroll
             for (int j = 0; j < RUN; ++j, wk.next(cur)) {
                 if (!((interm >> j) & 1u)) continue;
                 const int64_t g = (B.offset + wk.rg) * npairs + cur.pr;
-                const PT tk = last_in_p ? P[j] : X[j];
-                const PT tk1 = last_in_p ? X[j] : P[j];
                 PT aP;
 #pragma unroll
                 for (int c = 0; c < PER; ++c) tbr_put(aP, c, acc[j][c]);
                 if (!done) {
-                    out_cur[g] = tk;
-                    out_prev[g] = tk1;
                     if (to_main) accE[g] = aP;
                     else tail[g] = aP;
                 } else {
+                    const PT tk = last_in_p ? P[j] : X[j];
                     PT oP;
 #pragma unroll
                     for (int c = 0; c < PER; ++c) {
