@@ -476,6 +476,7 @@ static int enqueue_step_tb(Plan* p, void* psi, cudaStream_t st)
         a.errflag = p->d_err;
         a.tm_cur = tbr_maps_for(p, (int)i, 0, psi, slot);
         a.tm_prev = tbr_maps_for(p, (int)i, 1, psi, slot);
+        a.nsites = p->n_sites;
         if (p->timing) {
             if (p->ev_used + 2 > p->ev_pool.size()) {
                 for (int e = 0; e < 64; ++e) {

@@ -152,6 +152,10 @@ struct TBArgs {
     // the ribbons whose tiles are copied by boxes (NULL: per-thread copies)
     const void* tm_cur;
     const void* tm_prev;
+    // register-run kernel: sites of the plan; its step-internal vectors (T pairs, E, tail) are
+    // stored pair-planar, element (site, pair) at pair * nsites + site (psi keeps
+    // [site][vector])
+    int64_t nsites;
 };
 
 struct TBSet {

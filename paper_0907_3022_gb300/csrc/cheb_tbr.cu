@@ -327,8 +327,10 @@ __device__ __forceinline__ bool tbr_fetch(const TBArgs& a, const TBRTile& t, int
     const bool to_main = FIRST || (a.ka <= t.B.ksplit);
     const bool read_e = !FIRST && (to_main || done);
     const bool read_t = !FIRST && !to_main && a.prev_ka > t.B.ksplit;
-    // the ribbon's first element of this plane index; sites at + rg * npairs
-    const int64_t base = t.B.offset * npairs + t.pr;
+    // this plane index of the ribbon's first site: psi [site][vector] (T_0 in the first
+    // launch), the step's own vectors pair-planar
+    const int64_t base_psi = t.B.offset * npairs + t.pr;
+    const int64_t base_own = (int64_t)t.pr * a.nsites + t.B.offset;
     const PT* const accsrc = read_e ? accE : tail;
     // consecutive lanes on consecutive positions (position p = tid + k TPB): a warp's copies
     // cover a few contiguous lines of a region row, not 32 lines RUN sites apart
@@ -343,12 +345,13 @@ __device__ __forceinline__ bool tbr_fetch(const TBArgs& a, const TBRTile& t, int
         const int rr = (int)(((unsigned long long)p * t.invS) >> 32), cc = p - rr * t.S;
         if (rr < RH && cc < RW) {
             const int rg = rg0 + rr * t.B.L + cc;
-            const int64_t gi = base + (int64_t)rg * npairs;
-            if (!boxX) tbr_cp(stX + p, in_cur + gi);
-            if (!FIRST && !boxP) tbr_cp(stP + p, in_prev + gi);
+            const int64_t go = base_own + rg;
+            const int64_t gx = FIRST ? base_psi + (int64_t)rg * npairs : go;
+            if (!boxX) tbr_cp(stX + p, in_cur + gx);
+            if (!FIRST && !boxP) tbr_cp(stP + p, in_prev + go);
             tbr_cp4(stD + p, dg + rg);
             if ((read_e || read_t) && rr >= ir0 && rr < ir1 && cc >= ic0 && cc < ic1)
-                tbr_cp(stA + p, accsrc + gi);
+                tbr_cp(stA + p, accsrc + go);
         }
     }
     tbr_cp_commit();
@@ -588,7 +591,7 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
 #pragma unroll
                 for (int j = 0; j < RUN; ++j, wk.next(cur)) {
                     if (!((interm >> j) & 1u)) continue;
-                    const PT tv = tail[(B.offset + wk.rg) * npairs + cur.pr];
+                    const PT tv = tail[(int64_t)cur.pr * a.nsites + B.offset + wk.rg];
 #pragma unroll
                     for (int q = 0; q < PER; ++q) {
                         const float2 y = tbr_get(tv, q);
@@ -659,7 +662,7 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
                     const int rr = (int)(((unsigned long long)p * cur.invS) >> 32);
                     const int cc = p - rr * cur.S;
                     if (rr >= ir0 && rr < ir1 && cc >= ic0 && cc < ic1) {
-                        const int64_t g = (gb + (int64_t)rr * B.L + cc) * npairs + cur.pr;
+                        const int64_t g = (int64_t)cur.pr * a.nsites + gb + (int64_t)rr * B.L + cc;
                         out_cur[g] = planeK[p];
                         out_prev[g] = planeK1[p];
                     }
@@ -669,11 +672,11 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
 #pragma unroll
             for (int j = 0; j < RUN; ++j, wk.next(cur)) {
                 if (!((interm >> j) & 1u)) continue;
-                const int64_t g = (B.offset + wk.rg) * npairs + cur.pr;
                 PT aP;
 #pragma unroll
                 for (int c = 0; c < PER; ++c) tbr_put(aP, c, acc[j][c]);
                 if (!done) {
+                    const int64_t g = (int64_t)cur.pr * a.nsites + B.offset + wk.rg;
                     if (to_main) accE[g] = aP;
                     else tail[g] = aP;
                 } else {
@@ -687,7 +690,7 @@ __global__ void __launch_bounds__(TPB, 1) k_rec_tbr(TBArgs a)
                         const float t2 = fmaf(tv.x, tv.x, tv.y * tv.y);
                         if (!(t2 <= lim[c])) atomicOr(a.errflag, 1);
                     }
-                    psi[g] = oP;
+                    psi[(B.offset + wk.rg) * npairs + cur.pr] = oP;
                 }
             }
         }
@@ -871,7 +874,8 @@ bool tbr_tma_available() { return tbr_encoder() != nullptr; }
 // (4 floats, L columns of pairs * 16 bytes, W rows of L pairs * 16 bytes) with a box of
 // (4, S, BH); columns and rows beyond the ribbon read as zero.  Ribbons without boxes keep a
 // zeroed map that the kernel never uses.
-static bool tbr_encode_buffer(const Plan* p, const TBSet& set, const void* base, CUtensorMap* out)
+static bool tbr_encode_buffer(const Plan* p, const TBSet& set, const void* base, bool planar,
+                              CUtensorMap* out)
 {
     const auto enc = tbr_encoder();
     const int npairs = p->nvec / 2;
@@ -882,10 +886,14 @@ static bool tbr_encode_buffer(const Plan* p, const TBSet& set, const void* base,
             CUtensorMap& m = out[(size_t)q * npairs + pr];
             std::memset(&m, 0, sizeof(m));
             if (!t.tma) continue;
-            char* g = static_cast<char*>(const_cast<void*>(base)) +
-                      ((size_t)B.offset * npairs + pr) * 16;
+            // psi: [site][vector], pair pr at 16 bytes per pair; the step's own vectors:
+            // pair-planar, pair pr's sites contiguous
+            const size_t first = planar ? (size_t)pr * p->n_sites + B.offset
+                                        : (size_t)B.offset * npairs + pr;
+            const size_t col = planar ? 16 : (size_t)npairs * 16;
+            char* g = static_cast<char*>(const_cast<void*>(base)) + first * 16;
             const cuuint64_t dims[3] = {4, (cuuint64_t)B.L, (cuuint64_t)B.W};
-            const cuuint64_t strides[2] = {(cuuint64_t)npairs * 16, (cuuint64_t)B.L * npairs * 16};
+            const cuuint64_t strides[2] = {(cuuint64_t)col, (cuuint64_t)B.L * col};
             const cuuint32_t box[3] = {4, (cuuint32_t)t.S, (cuuint32_t)t.BH};
             const cuuint32_t estr[3] = {1, 1, 1};
             if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g, dims, strides, box, estr,
@@ -926,8 +934,8 @@ int tbr_maps_prepare(Plan* p)
     void* pairs[2][2] = {{p->d_A, p->d_B}, {p->d_C, p->d_D}};
     for (size_t i = 1; i < p->tb_sched.size(); ++i) {
         const TBSet& set = p->tb_sets[p->tb_sched[i].set];
-        if (!tbr_encode_buffer(p, set, pairs[(i - 1) & 1][1], &h[(2 * i + 0) * nmap]) ||
-            !tbr_encode_buffer(p, set, pairs[(i - 1) & 1][0], &h[(2 * i + 1) * nmap]))
+        if (!tbr_encode_buffer(p, set, pairs[(i - 1) & 1][1], true, &h[(2 * i + 0) * nmap]) ||
+            !tbr_encode_buffer(p, set, pairs[(i - 1) & 1][0], true, &h[(2 * i + 1) * nmap]))
             return fail(CHEB_ERR_CUDA, "tensor map encoding");
     }
     CHEB_CUDA(cudaMemcpy(p->d_tmaps, h.data(), need, cudaMemcpyHostToDevice));
@@ -942,7 +950,7 @@ int tbr_maps_psi(Plan* p, const void* psi, int slot, cudaStream_t s)
     if (key.psi == psi && key.epoch == p->shape_epoch) return CHEB_OK;
     const size_t nmap = (size_t)p->nblocks * (p->nvec / 2);
     std::vector<CUtensorMap> h(nmap);
-    if (!tbr_encode_buffer(p, p->tb_sets[p->tb_sched[0].set], psi, h.data()))
+    if (!tbr_encode_buffer(p, p->tb_sets[p->tb_sched[0].set], psi, false, h.data()))
         return fail(CHEB_ERR_CUDA, "tensor map encoding");
     char* dst = static_cast<char*>(p->d_tmaps) + (2 * p->tb_sched.size() + slot) * p->tmap_array;
     // pageable source: the call returns once the data is staged, and the copy is ordered on s
