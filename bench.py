@@ -773,6 +773,9 @@ def run_single(args, world, rank, local):
         if cfg["kind"] == "ribbon" and plan.blocking()[0]:
             roofline = blocked_roofline(cb, plan, kms, kcount, min(args.steps, 5), per_unit,
                                         "one site and one Chebyshev order")
+        if cfg["kind"] == "doublewell" and plan.cluster():
+            roofline = cluster_roofline(cb, plan, cfg["sites"] * M * min(args.steps, 5), kms,
+                                        prec == cb.CHEB_C128, local, roofline)
         # accuracy: against the oracle after min(steps done, config) steps from the packet
         nacc = {"holstein": 2, "ribbon": 50}.get(cfg["kind"], cfg["nsteps"])
         if args.lean:
@@ -842,6 +845,34 @@ def run_single(args, world, rank, local):
         print(json.dumps(line), flush=True)
     plan.close()
     return 0
+
+
+def cluster_roofline(cb, plan, site_orders, kms, fp64, local, hbm):
+    """The cluster step runs on the cluster's SMs only (8 or 16), a chunk of the chain each, and
+    is bound by their arithmetic (complex128: FP64) or by its barriers (complex64).  Counted per
+    useful site-order from the kernel: complex128 8 FP64 pipe instructions (2 DADD neighbour
+    sums, 4 DFMA for beta and d, 2 for the accumulation), complex64 12 FP32 (2 FADD, 4 FFMA for
+    beta as a float pair, 2 for d, 4 for the accumulation as a float pair); the super-steps'
+    recomputed edge sites are not counted.  Peak: the library's probe of the whole GPU's FMA
+    rate, times the cluster's CTAs over the SMs."""
+    import torch
+
+    ctas = plan.cluster()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    per = 8 if fp64 else 12
+    probe = cb.cheb_measure_peak(cb.CHEB_PEAK_FP64_GFLOPS if fp64 else cb.CHEB_PEAK_FP32_GFLOPS)
+    peak = probe / 2.0 * ctas / sms  # G FMA instructions/s of the cluster's SMs
+    achieved = per * site_orders / (kms / 1e3) / 1e9
+    return {"bound": "fp64" if fp64 else "latency", "achieved": achieved, "peak": peak,
+            "unit": "G %s pipe instructions/s" % ("FP64" if fp64 else "FP32"),
+            "frac": achieved / peak, "traffic": None, "kernel": hbm["kernel"],
+            "peak_kind": "FMA rate measured in this run by the library's probe, x %d CTAs / %d SMs"
+                         % (ctas, sms),
+            "per_unit": "%d %s instructions per useful site-order" % (per, "FP64" if fp64 else "FP32"),
+            "note": None if fp64 else "complex64: the cluster barriers between super-steps, not "
+                                      "FP32, bound the step; the FP32 fraction is for reference",
+            "hbm_reference": {"achieved": hbm["achieved"], "peak": hbm["peak"], "unit": "GB/s",
+                              "frac": hbm["frac"], "alg_bytes_per_unit": hbm["alg_bytes_per_unit"]}}
 
 
 def adjoint_roofline(cb, M, T, sites, ms_per_gradient, fp64):
