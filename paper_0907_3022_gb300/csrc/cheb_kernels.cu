@@ -127,15 +127,43 @@ struct SellOp {
         const int64_t chunk = pos >> 5;
         const int64_t off = a.sell_chunk_off[chunk] + (pos & 31);
         const int len = a.sell_chunk_len[chunk];
-        for (int e = 0; e < len; ++e) {
-            const int col = a.sell_col[off + (int64_t)e * 32];
-            const R val = sval[off + (int64_t)e * 32];
-            C y[VPT];
-            IO::load(cur + (int64_t)col * nv + (int64_t)g * VPT, y);
+        // complex128: the first EU entries (every Holstein row has 2 to 4) with all column
+        // indices and values first, then all gathers, so that a row's dependent loads overlap
+        // (10 % faster); complex64 keeps one entry at a time, whose fewer registers leave more
+        // warps to hide the gathers (the batched form was 20 % slower there)
+        constexpr int EU = sizeof(R) == 8 ? 4 : 0;
+        if constexpr (EU > 0) {
+            int col[EU];
+            R val[EU];
+#pragma unroll
+            for (int e = 0; e < EU; ++e) {
+                col[e] = e < len ? a.sell_col[off + (int64_t)e * 32] : 0;
+                val[e] = e < len ? sval[off + (int64_t)e * 32] : (R)0;
+            }
+            C y[EU][VPT];
+#pragma unroll
+            for (int e = 0; e < EU; ++e)
+                if (e < len) IO::load(cur + (int64_t)col[e] * nv + (int64_t)g * VPT, y[e]);
+#pragma unroll
+            for (int e = 0; e < EU; ++e) {
+                if (e < len) {
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) {
+                        acc[v].x = fma(val[e], y[e][v].x, acc[v].x);
+                        acc[v].y = fma(val[e], y[e][v].y, acc[v].y);
+                    }
+                }
+            }
+        }
+        for (int e = EU; e < len; ++e) {
+            const int c = a.sell_col[off + (int64_t)e * 32];
+            const R v0 = sval[off + (int64_t)e * 32];
+            C z[VPT];
+            IO::load(cur + (int64_t)c * nv + (int64_t)g * VPT, z);
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
-                acc[v].x = fma(val, y[v].x, acc[v].x);
-                acc[v].y = fma(val, y[v].y, acc[v].y);
+                acc[v].x = fma(v0, z[v].x, acc[v].x);
+                acc[v].y = fma(v0, z[v].y, acc[v].y);
             }
         }
     }
