@@ -321,8 +321,8 @@ int cheb_plan_set_blocking(cheb_plan* plan, int orders_per_launch, int sites_per
                     (one vector) positions with at least one zero pad.  A CTA holds one pair of
                     vectors (nvec 2 and 4: the two pairs of a tile go to two CTAs) or one vector
                     (nvec 1).  The launch keeps its CTAs resident (one per SM), each working
-                    through tiles; each thread prefetches its positions of the CTA's next
-                    tile while the current one runs.  Compiled (run x threads): pairs 3 x 768, 3 x 512,
+                    through tiles, and copies its next tile's inputs into shared memory
+                    while the current one runs.  Compiled (run x threads): pairs 3 x 768, 3 x 512,
                     5 x 512, 7 x 384, 9 x 256; single vectors 3 x 1024, 5 x 512, 7 x 512;
      CHEB_TB_RUNS_TMA  CHEB_TB_RUNS with the next tile's T_{k-1} and T_{k-2} staged by
                     tensor-memory-access boxes (one box per vector pair and buffer, completion

@@ -14,10 +14,10 @@
 //   neighbours of the next order read it).  Only T_{k-1} has a shared-memory plane (two planes,
 //   read one / write the other).
 // * Layout of a plane: site (rr, cc) of the RH x RW region is at position rr S + cc, where the
-//   row stride S is the same for every tile of a ribbon (the tile builder takes the widest
-//   region row + 1 rounded up to A = 4 for float4, 8 for float2), so that the S - RW >= 1
-//   positions after every row are zero pads; one zero element follows the last position (index
-//   NPOS = RUN TPB).  The pads make the neighbour left of column 0 and right of column RW - 1 a
+//   row stride S (from the tile builder) is RW + 1 rounded up to A = 4 for float4, 8 for
+//   float2 (with boxes: the widest tile's, the same for every tile of a ribbon), so that the
+//   S - RW >= 1 positions after every row are zero pads; one zero element follows the last
+//   position (index NPOS = RUN TPB).  The pads make the neighbour left of column 0 and right of column RW - 1 a
 //   zero read, which is the ribbon's open edge where the region ends at the ribbon border (where
 //   it ends at an open side the site is outside the validity limit and its value unused).  A
 //   vertical neighbour outside the region or the ribbon, and the left neighbour of position 0,
@@ -30,15 +30,19 @@
 //   the order loop (both planes are zeroed at every tile start, so every value read is finite).
 //   The accumulation runs for every position and only interior sites are written out, and the
 //   parity of the order, which decides how (-i)^k enters, is a compile-time constant.
-// * The inputs of the next work item (T_{ka-1}, T_{ka-2}, d and the accumulator) stream into
-//   staging buffers while the current item runs its orders, so the global-memory latency of a
-//   tile start is hidden.  With pairs of vectors, T_{ka-1} and T_{ka-2} come as two tensor-memory-
-//   access boxes of S x BH elements (BH = the ribbon's tallest region) whose shared-memory image
-//   is exactly the plane layout above (box row rr, column cc at rr S + cc; columns and rows beyond
-//   the ribbon read as zero); d, the accumulator and single-vector planes are copied with
-//   cp.async, consecutive lanes on consecutive positions, published by a barrier after the
-//   wait.  A launch keeps its CTAs resident (one per SM), each working through tiles, so that
-//   a tile's copies overlap the previous tile's orders.
+// * A launch keeps its CTAs resident (one per SM), each working through tiles, and the inputs
+//   of a CTA's next work item (T_{ka-1}, T_{ka-2}, d and the accumulator) stream into staging
+//   buffers while the current item runs its orders, so the global-memory latency of a tile
+//   start is hidden.  They are copied with cp.async, consecutive lanes on consecutive
+//   positions, and published by a barrier after the wait; in the variant with boxes
+//   (CHEB_TB_RUNS_TMA, pairs of vectors) T_{ka-1} and T_{ka-2} come as two tensor-memory-access
+//   boxes of S x BH elements (BH = the ribbon's tallest region) whose shared-memory image is
+//   exactly the plane layout above (box row rr, column cc at rr S + cc; columns and rows beyond
+//   the ribbon read as zero).
+// * The step's own vectors (the T pairs passed between launches, E, tail) are stored
+//   pair-planar, element (site, pair) at pair x sites + site, so that a CTA, which owns one
+//   pair, moves whole sectors; psi, read by the first launch and written by the last, keeps
+//   its [site][vector] layout.
 //
 // Per formed site-order and plane element: one vertical load, 2 / RUN run-end loads, one store
 // (k_rec_tb: own, three neighbours, T_{k-2} and the store).
