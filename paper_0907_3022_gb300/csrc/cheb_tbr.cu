@@ -84,12 +84,40 @@ __host__ __device__ __forceinline__ int tbr_limit(int rr, int cc, int RH, int RW
 __device__ __forceinline__ float4 tbr_zero(float4*) { return make_float4(0.f, 0.f, 0.f, 0.f); }
 __device__ __forceinline__ float2 tbr_zero(float2*) { return make_float2(0.f, 0.f); }
 
+// Packed two-float arithmetic on a complex value's (re, im) pair: one instruction for both
+// components, each rounded as the scalar operation would be.
+__device__ __forceinline__ unsigned long long tbr_pk(float2 v)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 tbr_upk(unsigned long long r)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float2 tbr_add2(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(tbr_pk(a)), "l"(tbr_pk(b)));
+    return tbr_upk(d);
+}
+__device__ __forceinline__ float2 tbr_fma2(float2 a, float2 b, float2 c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(tbr_pk(a)), "l"(tbr_pk(b)), "l"(tbr_pk(c)));
+    return tbr_upk(d);
+}
+
 // h = beta (l + r + v) - p + d x, halved for T_1 = H~ T_0; beta is a float32 number in
 // complex64 lattice plans (the plan chooses a so), zero at pads
 __device__ __forceinline__ float2 tbr_h(float2 l, float2 r, float2 v, float2 p, float2 x, float d,
                                         float bh, bool half)
 {
-    const float sx = (l.x + r.x) + v.x, sy = (l.y + r.y) + v.y;
+    const float2 s2 = tbr_add2(tbr_add2(l, r), v);
+    const float sx = s2.x, sy = s2.y;
     float hx = fmaf(bh, sx, -p.x), hy = fmaf(bh, sy, -p.y);
     hx = fmaf(d, x.x, hx);
     hy = fmaf(d, x.y, hy);
@@ -132,10 +160,8 @@ template <bool ODD>
 __device__ __forceinline__ void tbr_accum(float2& acc, const float2 q, const float2 t)
 {
     if (!ODD) {
-        acc.x = fmaf(q.y, t.x, acc.x);
-        acc.y = fmaf(q.y, t.y, acc.y);
-        acc.x = fmaf(q.x, t.x, acc.x);
-        acc.y = fmaf(q.x, t.y, acc.y);
+        acc = tbr_fma2(make_float2(q.y, q.y), t, acc);
+        acc = tbr_fma2(make_float2(q.x, q.x), t, acc);
     } else {
         acc.x = fmaf(q.y, t.y, acc.x);
         acc.y = fmaf(-q.y, t.x, acc.y);
