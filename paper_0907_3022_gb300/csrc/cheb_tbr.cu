@@ -117,15 +117,13 @@ __device__ __forceinline__ float2 tbr_h(float2 l, float2 r, float2 v, float2 p, 
                                         float bh, bool half)
 {
     const float2 s2 = tbr_add2(tbr_add2(l, r), v);
-    const float sx = s2.x, sy = s2.y;
-    float hx = fmaf(bh, sx, -p.x), hy = fmaf(bh, sy, -p.y);
-    hx = fmaf(d, x.x, hx);
-    hy = fmaf(d, x.y, hy);
+    float2 h = tbr_fma2(make_float2(bh, bh), s2, make_float2(-p.x, -p.y));
+    h = tbr_fma2(make_float2(d, d), x, h);
     if (half) {
-        hx *= 0.5f;
-        hy *= 0.5f;
+        h.x *= 0.5f;
+        h.y *= 0.5f;
     }
-    return make_float2(hx, hy);
+    return h;
 }
 __device__ __forceinline__ float4 tbr_h(float4 l, float4 r, float4 v, float4 p, float4 x, float d,
                                         float bh, bool half)
