@@ -878,7 +878,8 @@ int tbr_launch(Plan* p, const TBArgs& a, cudaStream_t s)
 }
 
 // ---- tensor maps (host) ---------------------------------------------------------------------
-// The driver's encoder, looked up once through the runtime (no link to the driver library).
+// The CUDA driver API's tensor-map encoder, looked up once through the runtime (no link to
+// libcuda).
 static PFN_cuTensorMapEncodeTiled_v12000 tbr_encoder()
 {
     static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
